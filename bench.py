@@ -1,0 +1,286 @@
+"""Benchmark: cell x velocity updates per second of the RK-3 step.
+
+Workload (the metric's configuration, config C2): Maxwell molecules, Shakhov
+Pr = 2/3, mu ~ T; Kn = 1, u_w = 0.5, T_w = 1; Nz = 128 cells stretched toward the
+walls (A = 0.98); 8 x 8 full-range x 2 x 16 half-range = 2048 velocities,
+equilibrium order 4; f stored in FP32 with FP64 moment sums.  One step is one
+full RK-3 step (three stages: walls, WENO-5 advection, Shakhov relaxation,
+moments, residual) of a batch of B = 256 independent replicas of C2 on each GPU
+(256 MiB per state buffer, larger than the 129 MB L2, so no L2 flush is needed).
+
+Output: one JSON line (rank 0).  `value` is the whole-job rate (all ranks) from
+CUDA events on the solver's stream around exactly --steps steps after --warmup
+steps, max time over ranks.  `e2e` repeats the measurement through the public
+API with the state uploaded from pinned host memory and the profiles read back
+every step.  `roofline` relates the stage kernels' live event time to their
+algorithmic bytes (32 B per update and step in FP32) and the measured HBM copy
+bandwidth.  `cpu_baseline` times the FP64 CPU oracle on a bounded sample.
+
+--impl reference times that oracle (the only reference this method has) on the
+host cores instead, with the same metric.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+BATCH = 256
+BYTES_PER_UPDATE = {"f32": 32, "f64": 64}   # algorithmic HBM bytes per update per RK-3 step
+KERNELS_PER_STEP = 9                        # 3 x (stage, finalize_cells, finalize_inst)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="lbs", choices=["lbs", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.lines, self.proc = gpu, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _oracle_c2():
+    from oracle.oracle import Oracle
+    p = W.C2
+    return Oracle(p["Qx"], p["Qy"], p["Qz"], p["N_eq"], p["Nz"], A=p["A"], Kn=p["Kn"], uw=p["u_w"],
+                  Tw=p["T_w"], Pr=p["Pr"], visc_law=p["visc_law"], visc_param=p["visc_param"])
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle as it stands on the host cores: one C2 instance, whole RK-3 steps."""
+    o = _oracle_c2()
+    o.step(1)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        o.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    upd = W.C2["Nz"] * 2 * W.C2["Qx"] * W.C2["Qy"] * W.C2["Qz"] * n
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": upd / dt, "unit": "updates/s", "cores": cores, "kind": "oracle",
+            "sample": "one C2 instance (128 cells x 2048 velocities), %d full RK-3 steps, FP64, "
+                      "%.1f s" % (n, dt)}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    o = _oracle_c2()
+    for _ in range(a.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    upd = W.C2["Nz"] * 2 * W.C2["Qx"] * W.C2["Qy"] * W.C2["Qz"] * a.steps
+    v = upd / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    print(json.dumps({
+        "impl": "reference", "metric": "cell x velocity updates/s (RK-3 steps)", "value": v,
+        "unit": "updates/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "C2 Shakhov Maxwell molecules Kn=1 u_w=0.5 Nz=128 A=0.98 "
+                               "Q=8x8x(2x16)=2048 N_eq=4", "sample": "one instance per step"},
+        "cpu_baseline": {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                         "sample": "one C2 instance per step, %d RK-3 steps" % a.steps},
+        "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1702_01335_gb300 import LBS_FP32, LBS_FP64, Instance, Solver
+    prec = LBS_FP32 if a.precision == "f32" else LBS_FP64
+    inst = [Instance(**W.C2)] * a.batch
+    s = Solver(inst, precision=prec)
+    st = s.torch_stream()
+    upd_step = sum(i.Nz * i.Q for i in inst)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident throughput
+    s.step(a.warmup)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(st)
+        s.step(a.steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = upd_step * world * a.steps / (ms_max * 1e-3)
+
+    # ---- roofline of the stage kernels (live CUDA events, same stream)
+    nprof = max(3, min(200, a.steps // 10))
+    k_stage, k_fin, k_step = s.profile_steps(nprof)
+    bpu = BYTES_PER_UPDATE[a.precision]
+    achieved = upd_step * bpu * nprof / (k_stage * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+
+    # ---- end to end through the C ABI with host buffers
+    pinned = torch.empty(s.state_bytes(), dtype=torch.uint8, pin_memory=True)
+    s.get_state_all_ptr(pinned.data_ptr(), to_host=True)
+    nprof_rows = sum(8 * i.Nz for i in inst)
+    out_host = torch.empty(nprof_rows, dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(3, min(100, a.steps // 30))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state_all_ptr(pinned.data_ptr(), from_host=True)
+        s.step(1)
+        s.moments_all_ptr(out_host.data_ptr())
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_value = upd_step * world * e2e_steps / float(tt.item())
+
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    if os.path.exists(tpath):
+        d = json.load(open(tpath))
+        if d.get("kernel_hash") == kernel_hash() and d.get("precision") == a.precision:
+            traffic = d["bytes_per_step_per_update"] * upd_step / 3.0
+
+    if rank == 0:
+        line = {
+            "metric": "cell x velocity updates/s (RK-3 steps)",
+            "value": value, "unit": "updates/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": a.precision, "data": "synthetic",
+            "config": {"workload": "C2 Shakhov Maxwell molecules Kn=1 u_w=0.5 T_w=1 Pr=2/3 "
+                                   "Nz=128 A=0.98 Q=8x8x(2x16)=2048 N_eq=4",
+                       "batch_per_gpu": a.batch, "state_bytes_per_buffer": s.state_bytes(),
+                       "l2": "inputs larger than L2 (3 buffers of %d MiB)" % (s.state_bytes() >> 20),
+                       "parallelism": "replicas, independent batches per GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                         "kernel": "stage_kernel (3 launches per step)",
+                         "algorithmic_bytes_per_update_step": bpu,
+                         "stage_kernel_ms_per_step": k_stage / nprof,
+                         "finalize_ms_per_step": k_fin / nprof,
+                         "profiled_step_ms": k_step / nprof},
+            "e2e": {"value": e2e_value, "unit": "updates/s",
+                    "h2d_bytes_per_step": s.state_bytes(), "d2h_bytes_per_step": nprof_rows * 8,
+                    "what": "lbs_set_state(all, pinned host) + lbs_step(1) + lbs_moments(all, host) "
+                            "per step"},
+            "gpu_launches": KERNELS_PER_STEP * a.steps,
+            "clocks": clk.summary(),
+        }
+        if not a.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "lbs_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1702_01335_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

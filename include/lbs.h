@@ -1,0 +1,181 @@
+/*
+ * lbs.h - C ABI of the GB300 solver for the mixed-quadrature Shakhov lattice
+ * Boltzmann model of Couette flow (Ambrus & Sofonea, "Half-range lattice
+ * Boltzmann models for the simulation of Couette flow using the Shakhov
+ * collision term", arXiv:1702.01335).
+ *
+ * Geometry and axes.  Two parallel plates at z = -L/2 and z = +L/2 (L = 1)
+ * move along x with -u_w and +u_w and are held at T_w (Sec. III; the paper
+ * calls the wall-normal axis x and the flow axis y).  The velocity set is the
+ * direct product of full-range Gauss-Hermite rules with Qx nodes on x and Qy
+ * nodes on y, and a half-range Gauss-Hermite rule with Qz_half nodes on each
+ * semi-axis of z: Q = 2 * Qx * Qy * Qz_half velocities (Sec. III).
+ *
+ * Scheme (one time step = lbs_step(h, 1)): the RK-3 TVD stages of Eq. (rk3)
+ * applied to L[F] of Eq. (L_def): WENO-5 advection along z (Eqs. flux,
+ * weno5_flux, weno5_omega, weno_sigma, Table weno), relaxation to the
+ * truncated-Hermite Shakhov target n G_x G_y G_z (1 + S) (Eqs. boltz, sdef,
+ * fyz, Fmn_def), diffuse reflection at both walls with three ghost nodes,
+ * quadratic extrapolation and the wall density n_w (Appendix, "Boundary
+ * conditions"), re-imposed at every RK stage.
+ *
+ * Conventions.
+ *  - Every function returns an lbs_status; nothing aborts.  On failure
+ *    lbs_last_error() returns a message (thread-local storage).
+ *  - The library owns all device memory of a handle.  Output buffers passed
+ *    in are owned by the caller.
+ *  - Work is queued on the CUDA stream given at creation; when NULL is given
+ *    the library creates (and later destroys) a non-blocking stream of its
+ *    own, see lbs_get_stream.  Functions that return host data synchronise it.
+ *  - Profiles are FP64, laid out [profile][cell] with cells ordered from the
+ *    bottom wall (z = -L/2) to the top wall.
+ *  - A handle holds a batch of independent instances (one Couette problem
+ *    each, possibly of different sizes); they advance together and are
+ *    addressed by index 0 .. n-1.
+ */
+#ifndef LBS_H
+#define LBS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbs_solver* lbs_handle;
+
+typedef enum {
+    LBS_OK = 0,
+    LBS_ERR_ARG = 1,              /* invalid argument or size                  */
+    LBS_ERR_CUDA = 2,             /* a CUDA runtime call failed                */
+    LBS_ERR_NONFINITE = 3,        /* NaN/Inf or n <= 0 / T <= 0 in a state      */
+    LBS_ERR_NO_CONVERGENCE = 4,   /* residual target not met within max_steps  */
+    LBS_ERR_QUADRATURE = 5        /* quadrature construction failed            */
+} lbs_status;
+
+typedef enum { LBS_VISC_POWER = 0, LBS_VISC_SUTHERLAND = 1 } lbs_visc_law;
+
+/* Storage/arithmetic precision of the distribution.  FP32 stores and relaxes f
+ * in FP32; moment sums across warps, the wall flux balance, the profiles and
+ * the residual are FP64 in both modes. */
+typedef enum { LBS_FP64 = 0, LBS_FP32_STORE_FP64_ACC = 1 } lbs_precision;
+
+/* Velocity-set orders.  N_eq is the order of the truncated Hermite expansion
+ * of the equilibrium; each axis uses min(N_eq, Q_a - 1) (Sec. III; Q_a = Qz_half
+ * on the wall-normal axis).  Limits: 1 <= Qx, Qy <= 64, 1 <= Qz_half <= 64,
+ * 0 <= N_eq <= 8, Q <= 32768. */
+typedef struct { int Qx, Qy, Qz_half, N_eq; } lbs_orders;
+
+/* Grid: Nz cells (6 <= Nz <= 4096).  A = 0: uniform cells.  0 < A < 1: the
+ * tanh stretching of Eqs. (stretch), (etas) mirrored onto the full channel,
+ * eta_s = -atanh(A) + (s - 1/2) d_eta, d_eta = 2 atanh(A)/Nz, x = L tanh(eta)/(2A). */
+typedef struct { int Nz; double A; } lbs_grid;
+
+/* Viscosity law.  POWER: mu ~ T^omega_or_S, tau = Kn T^(omega-1) / n
+ * (Eq. mw_tau for omega = 1).  SUTHERLAND: Eq. (sutherland_tau) with
+ * delta = 1/(Kn sqrt 2): tau = Kn sqrt(T) (1 + S) / (n (T + S)), S = omega_or_S. */
+typedef struct { lbs_visc_law law; double omega_or_S; } lbs_visc;
+
+/* One Couette instance.  dt > 0 is used as given; dt <= 0 selects
+ * dt = cfl * min(dz) / max|p_z|, capped at tau(n = 2, T = T_w) / 2. */
+typedef struct {
+    lbs_orders orders;
+    lbs_grid grid;
+    double Kn, u_w, T_w, Pr;
+    lbs_visc visc;
+    double dt, cfl;
+} lbs_instance_desc;
+
+/* Create a single-instance solver (Sec. III model, Appendix scheme) with the
+ * CFL time step.  The state starts at the rest Maxwellian n = 1, T = 1 (the
+ * weights w_k).  cuda_stream is a cudaStream_t or NULL.  Errors: LBS_ERR_ARG on
+ * out-of-range orders/sizes, Kn <= 0, T_w <= 0, Pr <= 0 or cfl <= 0;
+ * LBS_ERR_CUDA when device memory cannot be allocated. */
+lbs_status lbs_create(lbs_handle* out, lbs_orders ord, lbs_grid grid, double Kn, double u_w,
+                      double T_w, double Pr, lbs_visc visc, lbs_precision prec, double cfl,
+                      void* cuda_stream);
+
+/* Create a batch of n >= 1 independent instances that advance together in
+ * the same launches (shared precision and stream).  desc[n] is read only
+ * during the call. */
+lbs_status lbs_batch_create(lbs_handle* out, const lbs_instance_desc* desc, int n,
+                            lbs_precision prec, void* cuda_stream);
+
+/* Release every resource of the handle (synchronises its stream). */
+lbs_status lbs_destroy(lbs_handle h);
+
+/* Queue nsteps >= 0 full RK-3 steps (Eq. rk3) of every active instance on the
+ * stream; returns without waiting.  The residual of each step is kept. */
+lbs_status lbs_step(lbs_handle h, long nsteps);
+
+/* March until every instance has residual R < tol or has taken max_steps steps.
+ * Each instance stops (retires) in the step where its R first drops below tol;
+ * steps_out[n] (may be NULL) receives the steps each instance took.  R is
+ * checked on the device every step; the host polls every check_every steps
+ * (CUDA-graph launches of check_every steps).  Returns LBS_ERR_NO_CONVERGENCE
+ * if some instance did not converge. */
+lbs_status lbs_run_to_steady(lbs_handle h, double tol, long max_steps, int check_every,
+                             long* steps_out);
+
+/* Profiles of instance inst, host_out[8][Nz]: n, u_x, T, q_x, q_z, P_xx,
+ * P_xz, P_zz (Eq. qdef, pressure tensor P_ij = sum xi_i xi_j f with xi = p - u).
+ * inst = -1: every instance, concatenated in instance order ([8][Nz_b] each). */
+lbs_status lbs_moments(lbs_handle h, int inst, double* host_out);
+
+/* All 14 profiles of instance inst, host_out[14][Nz]: n, u_x, u_y, u_z, T,
+ * q_x, q_y, q_z, P_xx, P_yy, P_zz, P_xy, P_xz, P_yz. */
+lbs_status lbs_profiles(lbs_handle h, int inst, double* host_out);
+
+/* Residual of the last step of instance inst:
+ * R = max over W in {n, u_x, T} of ||W_new - W_old||_2 / max(||W_old||_2, 1e-30)
+ * over the interior cells (the paper states no criterion; this is the solver's). */
+lbs_status lbs_residual(lbs_handle h, int inst, double* out);
+
+/* Number of steps instance inst has taken. */
+lbs_status lbs_steps_taken(lbs_handle h, int inst, long* out);
+
+/* Sizes of instance inst: out[0..3] = Q, Nz, Qx*Qy, element size in bytes of
+ * the stored distribution; dt_out (may be NULL) receives the time step. */
+lbs_status lbs_info(lbs_handle h, int inst, long* out, double* dt_out);
+
+/* Checkpoint: copy the distribution of instance inst, [Nz][Q] in the velocity
+ * order k = ((sg * Qz_half + m) * Qx + i) * Qy + j (sg = 0: p_z > 0), as
+ * normalised populations f_k / w_k in the stored precision, to dst (host if
+ * to_host, else device).  inst = -1: every instance, concatenated in order. */
+lbs_status lbs_get_state(lbs_handle h, int inst, void* dst, int to_host);
+
+/* Resume / warm start: set the distribution of instance inst from src (layout
+ * and precision of lbs_get_state; host if from_host, else device) and
+ * recompute its moments and wall densities.  inst = -1: every instance from
+ * one concatenated buffer.  LBS_ERR_NONFINITE if the state has non-finite
+ * values or n <= 0 or T <= 0 in a cell. */
+lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host);
+
+/* Warm start: seed instance inst with the discrete Shakhov target of the given
+ * profiles in every cell.  prof[8][Nz] has the layout of lbs_moments (the P_ij
+ * rows are not used: the seed is n G_x G_y G_z (1 + S) of n, u_x, T, q_x, q_z).
+ * LBS_ERR_NONFINITE if a value is not finite or n <= 0 or T <= 0. */
+lbs_status lbs_init_from_profiles(lbs_handle h, int inst, const double* prof);
+
+/* Run nsteps steps launching every kernel directly with CUDA events around
+ * each on the handle's stream, and return summed device times in ms:
+ * out_ms[0] the stage kernels (WENO advection, collision, RK combine, moment
+ * and wall-flux partials), out_ms[1] the per-cell and per-instance finalise
+ * kernels, out_ms[2] the whole steps.  Synchronises.  For measurement only;
+ * the arithmetic is that of lbs_step. */
+lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms);
+
+/* The CUDA stream (cudaStream_t) the handle queues its work on: the one given at
+ * creation, or the stream the library created when NULL was given. */
+lbs_status lbs_get_stream(lbs_handle h, void** out);
+
+/* Host-only: the solver's Q-point Gauss rule for omega(p) = exp(-p^2/2)/sqrt(2 pi),
+ * kind 0 = full range (sum w = 1), kind 1 = half range on (0, inf) (sum w = 1/2).
+ * Needs no GPU.  LBS_ERR_ARG for Q outside 1..64. */
+lbs_status lbs_quadrature(int kind, int Q, double* nodes, double* weights);
+
+/* Message of the last error of the calling thread ("" if none). */
+const char* lbs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBS_H */

@@ -1,0 +1,726 @@
+// C ABI of the solver (include/lbs.h): host set-up of each Couette instance
+// (velocity set, Hermite bases, grid, wall equilibria, time step), one device
+// memory pool per handle, and the launch sequence of a time step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbs.h"
+#include "lbs_internal.h"
+
+namespace lbs {
+cudaError_t launch_stage(int fp32, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
+                         int ntiles, size_t smem, cudaStream_t st);
+cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int ninst, int maxNz,
+                            cudaStream_t st);
+cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,
+                        cudaStream_t st);
+}  // namespace lbs
+
+using namespace lbs;
+
+static thread_local std::string g_err;
+
+static lbs_status fail(lbs_status s, const std::string& m)
+{
+    g_err = m;
+    return s;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(LBS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+namespace {
+
+struct InstHost {
+    lbs_instance_desc d;
+    int Nz, Q, Qx, Qy, Qz, Nx, Ny, Nzq, nchunks, rec_stride, nzm_max;
+    double dt;
+    std::vector<double> xc, xf;  // cell centres (s = -3..Nz+2, 0-based), interfaces
+};
+
+struct Pool {  // bump allocator over one device allocation
+    size_t bytes = 0;
+    size_t take(size_t n)
+    {
+        size_t o = (bytes + 255) & ~size_t(255);
+        bytes = o + n;
+        return o;
+    }
+};
+
+}  // namespace
+
+struct lbs_solver {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int fp32 = 0, esize = 8, V = 1, ZT = 16, ninst = 0, maxNz = 0;
+    std::vector<InstHost> ih;
+    std::vector<InstDev> idev;
+    InstDev* d_inst = nullptr;
+    Tile* d_tiles = nullptr;
+    int ntiles = 0;
+    size_t smem = 0;
+    unsigned char* pool = nullptr;
+    double* d_macro = nullptr;  // [8][maxNz] staging for warm starts
+    cudaGraphExec_t gexec = nullptr;
+    int gsteps = 0;
+};
+
+// ---------------------------------------------------------------- set-up ----
+static lbs_status validate(const lbs_instance_desc& d)
+{
+    const lbs_orders& o = d.orders;
+    if (o.Qx < 1 || o.Qx > kMaxQ1D || o.Qy < 1 || o.Qy > kMaxQ1D || o.Qz_half < 1 ||
+        o.Qz_half > kMaxQ1D)
+        return fail(LBS_ERR_ARG, "velocity orders must lie in 1..64");
+    if (o.N_eq < 0 || o.N_eq > kMaxN) return fail(LBS_ERR_ARG, "N_eq must lie in 0..8");
+    if ((long)2 * o.Qx * o.Qy * o.Qz_half > 32768) return fail(LBS_ERR_ARG, "Q = 2 Qx Qy Qz_half exceeds 32768");
+    if (d.grid.Nz < 6 || d.grid.Nz > 4096) return fail(LBS_ERR_ARG, "Nz must lie in 6..4096");
+    if (!(d.grid.A >= 0.0 && d.grid.A < 1.0)) return fail(LBS_ERR_ARG, "grid stretching A must lie in [0, 1)");
+    if (!(d.Kn > 0.0) || !(d.T_w > 0.0) || !(d.Pr > 0.0) || !std::isfinite(d.u_w))
+        return fail(LBS_ERR_ARG, "Kn, T_w and Pr must be positive and u_w finite");
+    if (d.visc.law != LBS_VISC_POWER && d.visc.law != LBS_VISC_SUTHERLAND)
+        return fail(LBS_ERR_ARG, "unknown viscosity law");
+    if (d.visc.law == LBS_VISC_SUTHERLAND && !(d.visc.omega_or_S > 0.0))
+        return fail(LBS_ERR_ARG, "Sutherland constant must be positive");
+    if (!(d.dt > 0.0) && !(d.cfl > 0.0)) return fail(LBS_ERR_ARG, "either dt or cfl must be positive");
+    return LBS_OK;
+}
+
+// cell centre / interface positions; Eqs. (stretch), (etas) on the full channel
+static double xpos(int Nz, double A, double s)  // s in cell units from the bottom wall
+{
+    if (A == 0.0) return -0.5 + s / Nz;
+    const double E = std::atanh(A);
+    return std::tanh(-E + s * 2.0 * E / Nz) / (2.0 * A);
+}
+
+static void lagrange3(double x, double a, double b, double c, double* w)
+{
+    w[0] = (x - b) * (x - c) / ((a - b) * (a - c));
+    w[1] = (x - a) * (x - c) / ((b - a) * (b - c));
+    w[2] = (x - a) * (x - b) / ((c - a) * (c - b));
+}
+
+template <typename T>
+static void put(std::vector<unsigned char>& host, size_t off, const std::vector<double>& v)
+{
+    T* p = reinterpret_cast<T*>(host.data() + off);
+    for (size_t i = 0; i < v.size(); ++i) p[i] = T(v[i]);
+}
+
+template <typename T>
+static std::vector<double> rounded(const std::vector<double>& v)
+{
+    std::vector<double> r(v.size());
+    for (size_t i = 0; i < v.size(); ++i) r[i] = double(T(v[i]));
+    return r;
+}
+
+static void build_tiles(lbs_solver* h, std::vector<Tile>& tiles)
+{
+    tiles.clear();
+    const int KC = kThreads * h->V;
+    size_t smem = 0;
+    for (int b = 0; b < h->ninst; ++b) {
+        InstHost& I = h->ih[b];
+        I.nchunks = (I.Q + KC - 1) / KC;
+        int nzt = std::min((I.Nz + h->ZT - 1) / h->ZT, I.Nz / 3);
+        nzt = std::max(nzt, 1);
+        const int base = I.Nz / nzt, rem = I.Nz % nzt;
+        int nzm_max = 0;
+        for (int c = 0; c < I.nchunks; ++c) {
+            const int k0 = c * KC, k1 = std::min(I.Q, k0 + KC) - 1;
+            nzm_max = std::max(nzm_max, k1 / (I.Qx * I.Qy) - k0 / (I.Qx * I.Qy) + 1);
+        }
+        I.nzm_max = nzm_max;
+        const int zmax = base + (rem ? 1 : 0);
+        const size_t RS = kRecHead + I.Qx + I.Qy + nzm_max;
+        smem = std::max(smem, (size_t)zmax * (kThreads / 32) * kNMom * 8 + (size_t)zmax * RS * h->esize);
+        for (int c = 0; c < I.nchunks; ++c) {
+            int z0 = 0;
+            for (int t = 0; t < nzt; ++t) {
+                const int zn = base + (t < rem ? 1 : 0);
+                tiles.push_back(Tile{b, z0, zn, c});
+                z0 += zn;
+            }
+        }
+    }
+    h->smem = smem;
+}
+
+template <typename T>
+static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
+{
+    // ---- per-instance host tables
+    std::vector<std::vector<double>> tabs_d;  // per instance, concatenated later
+    Pool pool;
+    struct Off {
+        size_t Hx, Hy, Pz, alpha, beta, px, py, xi, wx, wy, wz, gxt, gxb, gwy, gwz, idz;
+        size_t F0, F1, F2, rec, partial, flux, nw, prof, Wold, Wnew, res, steps, active, status;
+    };
+    std::vector<Off> off(h->ninst);
+    struct Tables {
+        std::vector<double> Hx, Hy, Pz, alpha, beta, px, wx, py, wy, xi, wz, gxt, gxb, gwy, gwz, idz;
+    };
+    std::vector<Tables> tb(h->ninst);
+    h->idev.assign(h->ninst, InstDev());
+    std::vector<Tile> tiles;
+    // first pass: sizes that do not depend on the tiling
+    for (int b = 0; b < h->ninst; ++b) {
+        const lbs_instance_desc& d = desc[b];
+        InstHost& I = h->ih[b];
+        I.d = d;
+        I.Nz = d.grid.Nz;
+        I.Qx = d.orders.Qx;
+        I.Qy = d.orders.Qy;
+        I.Qz = d.orders.Qz_half;
+        I.Q = 2 * I.Qx * I.Qy * I.Qz;
+        I.Nx = std::min(d.orders.N_eq, I.Qx - 1);
+        I.Ny = std::min(d.orders.N_eq, I.Qy - 1);
+        I.Nzq = std::min(d.orders.N_eq, I.Qz - 1);
+        I.rec_stride = kRecHead + I.Qx + I.Qy + 2 * I.Qz;
+        h->maxNz = std::max(h->maxNz, I.Nz);
+    }
+    build_tiles(h, tiles);
+    for (int b = 0; b < h->ninst; ++b) {
+        InstHost& I = h->ih[b];
+        Tables& t = tb[b];
+        const lbs_instance_desc& d = I.d;
+        // quadratures
+        t.px.resize(I.Qx); t.wx.resize(I.Qx); t.py.resize(I.Qy); t.wy.resize(I.Qy);
+        t.xi.resize(I.Qz); t.wz.resize(I.Qz);
+        if (gauss_rule(QUAD_FULL, I.Qx, t.px.data(), t.wx.data()) ||
+            gauss_rule(QUAD_FULL, I.Qy, t.py.data(), t.wy.data()) ||
+            gauss_rule(QUAD_HALF, I.Qz, t.xi.data(), t.wz.data()))
+            return fail(LBS_ERR_QUADRATURE, "Gauss rule construction failed");
+        for (double v : t.wz)
+            if (!(v > 0.0) || !std::isfinite(v)) return fail(LBS_ERR_QUADRATURE, "non-positive half-range weight");
+        recurrence(QUAD_HALF, kMaxN + 2, t.alpha, t.beta);
+        t.Hx.resize(I.Qx * (I.Nx + 1)); t.Hy.resize(I.Qy * (I.Ny + 1)); t.Pz.resize(I.Qz * (I.Nzq + 1));
+        hermite_basis(t.px.data(), I.Qx, I.Nx, t.Hx.data());
+        hermite_basis(t.py.data(), I.Qy, I.Ny, t.Hy.data());
+        half_basis(t.xi.data(), I.Qz, I.Nzq, t.alpha, t.beta, t.Pz.data());
+        // wall equilibria per axis (n = 1, T = T_w, u = +-u_w along x, q = 0)
+        double a[kMaxN + 1], bb[kMaxN + 1];
+        t.gxt.assign(I.Qx, 0.0); t.gxb.assign(I.Qx, 0.0); t.gwy.assign(I.Qy, 0.0); t.gwz.assign(2 * I.Qz, 0.0);
+        full_coeffs(d.u_w, d.T_w, I.Nx, a);
+        for (int i = 0; i < I.Qx; ++i)
+            for (int l = 0; l <= I.Nx; ++l) t.gxt[i] += a[l] * t.Hx[i * (I.Nx + 1) + l];
+        full_coeffs(-d.u_w, d.T_w, I.Nx, a);
+        for (int i = 0; i < I.Qx; ++i)
+            for (int l = 0; l <= I.Nx; ++l) t.gxb[i] += a[l] * t.Hx[i * (I.Nx + 1) + l];
+        full_coeffs(0.0, d.T_w, I.Ny, a);
+        for (int j = 0; j < I.Qy; ++j)
+            for (int l = 0; l <= I.Ny; ++l) t.gwy[j] += a[l] * t.Hy[j * (I.Ny + 1) + l];
+        half_coeffs(0.0, d.T_w, I.Nzq, t.alpha.data(), t.beta.data(), bb);
+        for (int m = 0; m < I.Qz; ++m)
+            for (int l = 0; l <= I.Nzq; ++l) {
+                t.gwz[m] += bb[l] * t.Pz[m * (I.Nzq + 1) + l];
+                t.gwz[I.Qz + m] += bb[l] * t.Pz[m * (I.Nzq + 1) + l];
+            }
+        // grid
+        const int Nz = I.Nz;
+        I.xc.resize(Nz + 6);
+        for (int s = -3; s <= Nz + 2; ++s) I.xc[s + 3] = xpos(Nz, d.grid.A, s + 0.5);
+        I.xf.resize(Nz + 1);
+        for (int s = 0; s <= Nz; ++s) I.xf[s] = xpos(Nz, d.grid.A, s);
+        t.idz.resize(Nz);
+        double dzmin = 1e300;
+        for (int s = 0; s < Nz; ++s) {
+            t.idz[s] = 1.0 / (I.xf[s + 1] - I.xf[s]);
+            dzmin = std::min(dzmin, I.xf[s + 1] - I.xf[s]);
+        }
+        // time step
+        if (d.dt > 0.0) {
+            I.dt = d.dt;
+        } else {
+            const double pmax = *std::max_element(t.xi.begin(), t.xi.end());
+            const double cap = 0.5 * relax_time(d.visc.law, d.Kn, d.visc.omega_or_S, 2.0, d.T_w);
+            I.dt = std::min(d.cfl * dzmin / pmax, cap);
+        }
+        // device descriptor (pointers filled after allocation)
+        InstDev& D = h->idev[b];
+        D.Nz = Nz; D.Qx = I.Qx; D.Qy = I.Qy; D.Qz = I.Qz; D.Q = I.Q; D.QxQy = I.Qx * I.Qy;
+        D.Nx = I.Nx; D.Ny = I.Ny; D.Nzq = I.Nzq;
+        D.nchunks = I.nchunks; D.rec_stride = I.rec_stride;
+        D.visc_law = d.visc.law; D.Kn = d.Kn; D.visc_param = d.visc.omega_or_S; D.Pr = d.Pr;
+        D.dt = I.dt; D.tol = 0.0;
+        const std::vector<double>& xc = I.xc;  // xc[s + 3]
+        lagrange3(xc[Nz + 3], xc[Nz + 2], xc[Nz + 1], xc[Nz], D.ext_top[0]);
+        lagrange3(xc[Nz + 4], xc[Nz + 3], xc[Nz + 2], xc[Nz + 1], D.ext_top[1]);
+        lagrange3(xc[2], xc[3], xc[4], xc[5], D.ext_bot[0]);
+        lagrange3(xc[1], xc[2], xc[3], xc[4], D.ext_bot[1]);
+        // D = sum over incoming velocities of w p_z Gw, from the stored (rounded) tables
+        const std::vector<double> wx = rounded<T>(t.wx), wy = rounded<T>(t.wy), wz = rounded<T>(t.wz);
+        const std::vector<double> xi = rounded<T>(t.xi), gxt = rounded<T>(t.gxt), gxb = rounded<T>(t.gxb);
+        const std::vector<double> gwy = rounded<T>(t.gwy), gwz = rounded<T>(t.gwz);
+        double sxt = 0, sxb = 0, sy = 0, szp = 0, szm = 0;
+        for (int i = 0; i < I.Qx; ++i) { sxt += wx[i] * gxt[i]; sxb += wx[i] * gxb[i]; }
+        for (int j = 0; j < I.Qy; ++j) sy += wy[j] * gwy[j];
+        for (int m = 0; m < I.Qz; ++m) {
+            szp += wz[m] * xi[m] * gwz[m];
+            szm += wz[m] * (-xi[m]) * gwz[I.Qz + m];
+        }
+        D.Dtop = sxt * sy * szm;
+        D.Dbot = sxb * sy * szp;
+        // memory layout
+        Off& o = off[b];
+        const size_t es = sizeof(T);
+        o.Hx = pool.take(t.Hx.size() * 8); o.Hy = pool.take(t.Hy.size() * 8); o.Pz = pool.take(t.Pz.size() * 8);
+        o.alpha = pool.take(t.alpha.size() * 8); o.beta = pool.take(t.beta.size() * 8);
+        o.px = pool.take(I.Qx * es); o.py = pool.take(I.Qy * es); o.xi = pool.take(I.Qz * es);
+        o.wx = pool.take(I.Qx * es); o.wy = pool.take(I.Qy * es); o.wz = pool.take(I.Qz * es);
+        o.gxt = pool.take(I.Qx * es); o.gxb = pool.take(I.Qx * es); o.gwy = pool.take(I.Qy * es);
+        o.gwz = pool.take(2 * I.Qz * es); o.idz = pool.take(Nz * es);
+        const size_t nf = (size_t)Nz * I.Q;
+        o.F0 = pool.take(nf * es); o.F1 = pool.take(nf * es); o.F2 = pool.take(nf * es);
+        o.rec = pool.take((size_t)Nz * I.rec_stride * es);
+        o.partial = pool.take((size_t)I.nchunks * Nz * kNMom * 8);
+        o.flux = pool.take((size_t)I.nchunks * 2 * 8);
+        o.nw = pool.take(2 * 8); o.prof = pool.take(14 * (size_t)Nz * 8);
+        o.Wold = pool.take(3 * (size_t)Nz * 8); o.Wnew = pool.take(3 * (size_t)Nz * 8);
+        o.res = pool.take(8); o.steps = pool.take(8); o.active = pool.take(4); o.status = pool.take(4);
+    }
+    const size_t inst_off = pool.take(sizeof(InstDev) * h->ninst);
+    const size_t tile_off = pool.take(sizeof(Tile) * tiles.size());
+    const size_t macro_off = pool.take(8 * (size_t)h->maxNz * 8);
+    void* mem = nullptr;
+    CK(cudaMalloc(&mem, pool.bytes));
+    h->pool = static_cast<unsigned char*>(mem);
+    unsigned char* P = h->pool;
+    // host image of the constant tables, descriptors and tiles; state set below
+    std::vector<unsigned char> img(pool.bytes, 0);
+    for (int b = 0; b < h->ninst; ++b) {
+        const Off& o = off[b];
+        const Tables& t = tb[b];
+        const InstHost& I = h->ih[b];
+        put<double>(img, o.Hx, t.Hx); put<double>(img, o.Hy, t.Hy); put<double>(img, o.Pz, t.Pz);
+        put<double>(img, o.alpha, t.alpha); put<double>(img, o.beta, t.beta);
+        put<T>(img, o.px, t.px); put<T>(img, o.py, t.py); put<T>(img, o.xi, t.xi);
+        put<T>(img, o.wx, t.wx); put<T>(img, o.wy, t.wy); put<T>(img, o.wz, t.wz);
+        put<T>(img, o.gxt, t.gxt); put<T>(img, o.gxb, t.gxb); put<T>(img, o.gwy, t.gwy);
+        put<T>(img, o.gwz, t.gwz); put<T>(img, o.idz, t.idz);
+        const size_t nf = (size_t)I.Nz * I.Q;
+        T* F0 = reinterpret_cast<T*>(img.data() + o.F0);
+        for (size_t e = 0; e < nf; ++e) F0[e] = T(1);  // rest Maxwellian n = 1, T = 1: f_k = w_k
+        *reinterpret_cast<int*>(img.data() + o.active) = 1;
+        InstDev& D = h->idev[b];
+        D.Hx = reinterpret_cast<const double*>(P + o.Hx);
+        D.Hy = reinterpret_cast<const double*>(P + o.Hy);
+        D.Pz = reinterpret_cast<const double*>(P + o.Pz);
+        D.alpha = reinterpret_cast<const double*>(P + o.alpha);
+        D.beta = reinterpret_cast<const double*>(P + o.beta);
+        D.px = P + o.px; D.py = P + o.py; D.xi = P + o.xi; D.wx = P + o.wx; D.wy = P + o.wy; D.wz = P + o.wz;
+        D.gwx_top = P + o.gxt; D.gwx_bot = P + o.gxb; D.gwy = P + o.gwy; D.gwz = P + o.gwz;
+        D.inv_dz = P + o.idz;
+        D.F0 = P + o.F0; D.F1 = P + o.F1; D.F2 = P + o.F2; D.rec = P + o.rec;
+        D.partial = reinterpret_cast<double*>(P + o.partial);
+        D.flux_part = reinterpret_cast<double*>(P + o.flux);
+        D.nw = reinterpret_cast<double*>(P + o.nw);
+        D.prof = reinterpret_cast<double*>(P + o.prof);
+        D.Wold = reinterpret_cast<double*>(P + o.Wold);
+        D.Wnew = reinterpret_cast<double*>(P + o.Wnew);
+        D.res = reinterpret_cast<double*>(P + o.res);
+        D.steps = reinterpret_cast<long long*>(P + o.steps);
+        D.active = reinterpret_cast<int*>(P + o.active);
+        D.status = reinterpret_cast<int*>(P + o.status);
+    }
+    std::memcpy(img.data() + inst_off, h->idev.data(), sizeof(InstDev) * h->ninst);
+    std::memcpy(img.data() + tile_off, tiles.data(), sizeof(Tile) * tiles.size());
+    h->d_inst = reinterpret_cast<InstDev*>(P + inst_off);
+    h->d_tiles = reinterpret_cast<Tile*>(P + tile_off);
+    h->d_macro = reinterpret_cast<double*>(P + macro_off);
+    h->ntiles = (int)tiles.size();
+    CK(cudaMemcpyAsync(P, img.data(), pool.bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBS_OK;
+}
+
+// moments, records, wall densities and W_old of the current F0 (every active instance)
+static lbs_status analyse(lbs_solver* h)
+{
+    CK(launch_stage(h->fp32, h->V, 0, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->stream));
+    CK(launch_finalize(h->fp32, 0, h->d_inst, h->ninst, h->maxNz, h->stream));
+    return LBS_OK;
+}
+
+static lbs_status enqueue_step(lbs_solver* h)
+{
+    for (int s = 1; s <= 3; ++s) {
+        CK(launch_stage(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->stream));
+        CK(launch_finalize(h->fp32, s, h->d_inst, h->ninst, h->maxNz, h->stream));
+    }
+    return LBS_OK;
+}
+
+static void drop_graph(lbs_solver* h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->gsteps = 0;
+}
+
+static lbs_status get_graph(lbs_solver* h, int nsteps)
+{
+    if (h->gexec && h->gsteps == nsteps) return LBS_OK;
+    drop_graph(h);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    lbs_status st = LBS_OK;
+    for (int i = 0; i < nsteps && st == LBS_OK; ++i) st = enqueue_step(h);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (st != LBS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(LBS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(LBS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    h->gsteps = nsteps;
+    return LBS_OK;
+}
+
+static lbs_status check_status(lbs_solver* h)
+{
+    std::vector<int> st(h->ninst);
+    for (int b = 0; b < h->ninst; ++b)
+        CK(cudaMemcpyAsync(&st[b], h->idev[b].status, 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int b = 0; b < h->ninst; ++b)
+        if (st[b]) return fail(LBS_ERR_NONFINITE, "instance " + std::to_string(b) + " reached a non-finite or non-positive state");
+    return LBS_OK;
+}
+
+// ---------------------------------------------------------------- C ABI -----
+extern "C" {
+
+const char* lbs_last_error(void) { return g_err.c_str(); }
+
+lbs_status lbs_quadrature(int kind, int Q, double* nodes, double* weights)
+{
+    if ((kind != 0 && kind != 1) || Q < 1 || Q > kMaxQ1D || !nodes || !weights)
+        return fail(LBS_ERR_ARG, "kind must be 0 or 1 and Q in 1..64");
+    if (gauss_rule(kind == 0 ? QUAD_FULL : QUAD_HALF, Q, nodes, weights))
+        return fail(LBS_ERR_QUADRATURE, "Gauss rule construction failed");
+    return LBS_OK;
+}
+
+lbs_status lbs_batch_create(lbs_handle* out, const lbs_instance_desc* desc, int n, lbs_precision prec,
+                            void* cuda_stream)
+{
+    if (!out || !desc || n < 1) return fail(LBS_ERR_ARG, "need an output handle and n >= 1 descriptors");
+    if (prec != LBS_FP64 && prec != LBS_FP32_STORE_FP64_ACC) return fail(LBS_ERR_ARG, "unknown precision");
+    *out = nullptr;
+    for (int b = 0; b < n; ++b) {
+        lbs_status s = validate(desc[b]);
+        if (s != LBS_OK) return fail(s, "instance " + std::to_string(b) + ": " + g_err);
+    }
+    lbs_solver* h = new lbs_solver();
+    h->fp32 = prec == LBS_FP32_STORE_FP64_ACC;
+    h->esize = h->fp32 ? 4 : 8;
+    h->ninst = n;
+    h->ih.resize(n);
+    long work = 0;
+    for (int b = 0; b < n; ++b)
+        work += (long)desc[b].grid.Nz * 2 * desc[b].orders.Qx * desc[b].orders.Qy * desc[b].orders.Qz_half;
+    h->V = work >= (1L << 22) ? 2 : 1;
+    h->ZT = 16;
+    if (cuda_stream) {
+        h->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return fail(LBS_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+        }
+        h->own_stream = true;
+    }
+    lbs_status s = h->fp32 ? setup<float>(h, desc) : setup<double>(h, desc);
+    if (s == LBS_OK) s = analyse(h);
+    if (s == LBS_OK) s = check_status(h);
+    if (s != LBS_OK) {
+        std::string m = g_err;
+        lbs_destroy(h);
+        return fail(s, m);
+    }
+    *out = h;
+    return LBS_OK;
+}
+
+lbs_status lbs_create(lbs_handle* out, lbs_orders ord, lbs_grid grid, double Kn, double u_w, double T_w,
+                      double Pr, lbs_visc visc, lbs_precision prec, double cfl, void* cuda_stream)
+{
+    lbs_instance_desc d;
+    d.orders = ord;
+    d.grid = grid;
+    d.Kn = Kn; d.u_w = u_w; d.T_w = T_w; d.Pr = Pr;
+    d.visc = visc;
+    d.dt = 0.0;
+    d.cfl = cfl;
+    if (!(cfl > 0.0)) return fail(LBS_ERR_ARG, "cfl must be positive");
+    return lbs_batch_create(out, &d, 1, prec, cuda_stream);
+}
+
+lbs_status lbs_destroy(lbs_handle h)
+{
+    if (!h) return LBS_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    if (h->pool) cudaFree(h->pool);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return LBS_OK;
+}
+
+lbs_status lbs_step(lbs_handle h, long nsteps)
+{
+    if (!h || nsteps < 0) return fail(LBS_ERR_ARG, "invalid handle or negative step count");
+    const int G = 8;  // steps per CUDA-graph launch
+    const long full = nsteps / G, rest = nsteps % G;
+    if (full > 0) {
+        lbs_status s = get_graph(h, G);
+        if (s != LBS_OK) return s;
+        for (long i = 0; i < full; ++i) CK(cudaGraphLaunch(h->gexec, h->stream));
+    }
+    for (long i = 0; i < rest; ++i) {
+        lbs_status s = enqueue_step(h);
+        if (s != LBS_OK) return s;
+    }
+    return LBS_OK;
+}
+
+lbs_status lbs_run_to_steady(lbs_handle h, double tol, long max_steps, int check_every, long* steps_out)
+{
+    if (!h || !(tol > 0.0) || max_steps < 1 || check_every < 1)
+        return fail(LBS_ERR_ARG, "need tol > 0, max_steps >= 1, check_every >= 1");
+    // arm the device-side retirement test
+    for (int b = 0; b < h->ninst; ++b) h->idev[b].tol = tol;
+    CK(cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->ninst, cudaMemcpyHostToDevice, h->stream));
+    std::vector<long long> st0(h->ninst), st(h->ninst);
+    std::vector<int> act(h->ninst);
+    for (int b = 0; b < h->ninst; ++b)
+        CK(cudaMemcpyAsync(&st0[b], h->idev[b].steps, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    lbs_status s = get_graph(h, check_every);
+    long done = 0;
+    bool all = false;
+    while (s == LBS_OK && done < max_steps && !all) {
+        CK(cudaGraphLaunch(h->gexec, h->stream));
+        done += check_every;
+        all = true;
+        for (int b = 0; b < h->ninst; ++b)
+            CK(cudaMemcpyAsync(&act[b], h->idev[b].active, 4, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int b = 0; b < h->ninst; ++b) all &= act[b] == 0;
+    }
+    // disarm and reactivate every instance
+    for (int b = 0; b < h->ninst; ++b) h->idev[b].tol = 0.0;
+    CK(cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->ninst, cudaMemcpyHostToDevice, h->stream));
+    const int one = 1;
+    for (int b = 0; b < h->ninst; ++b) {
+        CK(cudaMemcpyAsync(&st[b], h->idev[b].steps, 8, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(h->idev[b].active, &one, 4, cudaMemcpyHostToDevice, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (s != LBS_OK) return s;
+    if (steps_out)
+        for (int b = 0; b < h->ninst; ++b) steps_out[b] = (long)(st[b] - st0[b]);
+    s = check_status(h);
+    if (s != LBS_OK) return s;
+    if (!all) return fail(LBS_ERR_NO_CONVERGENCE, "residual target not reached within max_steps");
+    return LBS_OK;
+}
+
+lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms)
+{
+    if (!h || nsteps < 1 || !out_ms) return fail(LBS_ERR_ARG, "need a handle, nsteps >= 1 and an output");
+    const int nev = 18;  // per step: 9 kernels, an event before and after each
+    std::vector<cudaEvent_t> ev(nev);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    double tstage = 0.0, tfin = 0.0, tstep = 0.0;
+    lbs_status st = LBS_OK;
+    for (long it = 0; it < nsteps && st == LBS_OK; ++it) {
+        for (int s = 1; s <= 3; ++s) {
+            CK(cudaEventRecord(ev[6 * (s - 1) + 0], h->stream));
+            CK(launch_stage(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->stream));
+            CK(cudaEventRecord(ev[6 * (s - 1) + 1], h->stream));
+            CK(launch_finalize(h->fp32, s, h->d_inst, h->ninst, h->maxNz, h->stream));
+            CK(cudaEventRecord(ev[6 * (s - 1) + 2], h->stream));
+        }
+        CK(cudaEventSynchronize(ev[6 * 2 + 2]));
+        for (int s = 0; s < 3; ++s) {
+            float a = 0.f, b = 0.f;
+            CK(cudaEventElapsedTime(&a, ev[6 * s + 0], ev[6 * s + 1]));
+            CK(cudaEventElapsedTime(&b, ev[6 * s + 1], ev[6 * s + 2]));
+            tstage += a;
+            tfin += b;
+        }
+        float w = 0.f;
+        CK(cudaEventElapsedTime(&w, ev[0], ev[6 * 2 + 2]));
+        tstep += w;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    out_ms[0] = tstage;
+    out_ms[1] = tfin;
+    out_ms[2] = tstep;
+    return check_status(h);
+}
+
+lbs_status lbs_get_stream(lbs_handle h, void** out)
+{
+    if (!h || !out) return fail(LBS_ERR_ARG, "invalid handle or null output");
+    *out = static_cast<void*>(h->stream);
+    return LBS_OK;
+}
+
+static lbs_status inst_ok(lbs_handle h, int inst)
+{
+    if (!h || inst < 0 || inst >= h->ninst) return fail(LBS_ERR_ARG, "invalid handle or instance index");
+    return LBS_OK;
+}
+
+static lbs_status copy_profiles(lbs_handle h, int inst, double* host_out)
+{
+    const int Nz = h->ih[inst].Nz;
+    CK(cudaMemcpyAsync(host_out, h->idev[inst].prof, 14 * (size_t)Nz * 8, cudaMemcpyDeviceToHost, h->stream));
+    return LBS_OK;
+}
+
+lbs_status lbs_profiles(lbs_handle h, int inst, double* host_out)
+{
+    lbs_status s = inst_ok(h, inst);
+    if (s != LBS_OK) return s;
+    if (!host_out) return fail(LBS_ERR_ARG, "null output");
+    s = copy_profiles(h, inst, host_out);
+    if (s != LBS_OK) return s;
+    CK(cudaStreamSynchronize(h->stream));
+    return check_status(h);
+}
+
+lbs_status lbs_moments(lbs_handle h, int inst, double* host_out)
+{
+    if (h && inst == -1 && host_out) {
+        size_t off = 0;
+        for (int b = 0; b < h->ninst; ++b) {
+            lbs_status s = lbs_moments(h, b, host_out + off);
+            if (s != LBS_OK) return s;
+            off += 8 * (size_t)h->ih[b].Nz;
+        }
+        return LBS_OK;
+    }
+    lbs_status s = inst_ok(h, inst);
+    if (s != LBS_OK) return s;
+    if (!host_out) return fail(LBS_ERR_ARG, "null output");
+    const int Nz = h->ih[inst].Nz;
+    std::vector<double> all(14 * (size_t)Nz);
+    s = copy_profiles(h, inst, all.data());
+    if (s != LBS_OK) return s;
+    CK(cudaStreamSynchronize(h->stream));
+    const int rows[8] = {0, 1, 4, 5, 7, 8, 12, 10};  // n, u_x, T, q_x, q_z, P_xx, P_xz, P_zz
+    for (int r = 0; r < 8; ++r) std::memcpy(host_out + (size_t)r * Nz, all.data() + (size_t)rows[r] * Nz, 8 * Nz);
+    return LBS_OK;
+}
+
+lbs_status lbs_residual(lbs_handle h, int inst, double* out)
+{
+    lbs_status s = inst_ok(h, inst);
+    if (s != LBS_OK) return s;
+    if (!out) return fail(LBS_ERR_ARG, "null output");
+    CK(cudaMemcpyAsync(out, h->idev[inst].res, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return check_status(h);
+}
+
+lbs_status lbs_steps_taken(lbs_handle h, int inst, long* out)
+{
+    lbs_status s = inst_ok(h, inst);
+    if (s != LBS_OK) return s;
+    if (!out) return fail(LBS_ERR_ARG, "null output");
+    long long v = 0;
+    CK(cudaMemcpyAsync(&v, h->idev[inst].steps, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *out = (long)v;
+    return LBS_OK;
+}
+
+lbs_status lbs_info(lbs_handle h, int inst, long* out, double* dt_out)
+{
+    lbs_status s = inst_ok(h, inst);
+    if (s != LBS_OK) return s;
+    if (!out) return fail(LBS_ERR_ARG, "null output");
+    const InstHost& I = h->ih[inst];
+    out[0] = I.Q;
+    out[1] = I.Nz;
+    out[2] = (long)I.Qx * I.Qy;
+    out[3] = h->esize;
+    if (dt_out) *dt_out = I.dt;
+    return LBS_OK;
+}
+
+lbs_status lbs_get_state(lbs_handle h, int inst, void* dst, int to_host)
+{
+    if (!h || inst < -1 || inst >= h->ninst) return fail(LBS_ERR_ARG, "invalid handle or instance index");
+    if (!dst) return fail(LBS_ERR_ARG, "null destination");
+    size_t off = 0;
+    for (int b = (inst < 0 ? 0 : inst); b < (inst < 0 ? h->ninst : inst + 1); ++b) {
+        const size_t bytes = (size_t)h->ih[b].Nz * h->ih[b].Q * h->esize;
+        CK(cudaMemcpyAsync(static_cast<unsigned char*>(dst) + off, h->idev[b].F0, bytes,
+                           to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
+        off += bytes;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return LBS_OK;
+}
+
+lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host)
+{
+    if (!h || inst < -1 || inst >= h->ninst) return fail(LBS_ERR_ARG, "invalid handle or instance index");
+    if (!src) return fail(LBS_ERR_ARG, "null source");
+    size_t off = 0;
+    for (int b = (inst < 0 ? 0 : inst); b < (inst < 0 ? h->ninst : inst + 1); ++b) {
+        const size_t bytes = (size_t)h->ih[b].Nz * h->ih[b].Q * h->esize;
+        CK(cudaMemcpyAsync(h->idev[b].F0, static_cast<const unsigned char*>(src) + off, bytes,
+                           from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
+        off += bytes;
+    }
+    lbs_status s = analyse(h);
+    if (s != LBS_OK) return s;
+    return check_status(h);
+}
+
+lbs_status lbs_init_from_profiles(lbs_handle h, int inst, const double* prof)
+{
+    lbs_status s = inst_ok(h, inst);
+    if (s != LBS_OK) return s;
+    if (!prof) return fail(LBS_ERR_ARG, "null profiles");
+    const int Nz = h->ih[inst].Nz;
+    // macro[8][Nz] = n, ux, uy, uz, T, qx, qy, qz from the 8 rows of lbs_moments
+    std::vector<double> macro(8 * (size_t)Nz, 0.0);
+    for (int c = 0; c < Nz; ++c) {
+        const double n = prof[c], ux = prof[Nz + c], T = prof[2 * Nz + c];
+        const double qx = prof[3 * Nz + c], qz = prof[4 * Nz + c];
+        if (!std::isfinite(n) || !std::isfinite(ux) || !std::isfinite(T) || !std::isfinite(qx) ||
+            !std::isfinite(qz) || !(n > 0.0) || !(T > 0.0))
+            return fail(LBS_ERR_NONFINITE, "profile value not finite or n, T not positive in cell " + std::to_string(c));
+        macro[c] = n; macro[Nz + c] = ux; macro[4 * Nz + c] = T; macro[5 * Nz + c] = qx; macro[7 * Nz + c] = qz;
+    }
+    CK(cudaMemcpyAsync(h->d_macro, macro.data(), macro.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(launch_seed(h->fp32, h->d_inst, inst, Nz, h->d_macro, h->stream));
+    s = analyse(h);
+    if (s != LBS_OK) return s;
+    return check_status(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Internal definitions shared by the host set-up and the CUDA kernels.
+#pragma once
+
+#include <cmath>
+#include <vector>
+
+#if defined(__CUDACC__)
+#define LBS_HD __host__ __device__ __forceinline__
+#else
+#define LBS_HD inline
+#endif
+
+namespace lbs {
+
+constexpr int kMaxQ1D = 64;     // nodes per axis (per sign on z)
+constexpr int kMaxN = 8;        // equilibrium expansion order
+constexpr int kNMom = 13;       // raw moments accumulated per cell
+constexpr int kRecHead = 12;    // scalars at the head of a cell record
+constexpr int kThreads = 128;   // threads of a stage CTA
+constexpr int kMaxZT = 64;      // cells of a z-tile
+
+enum { QUAD_FULL = 0, QUAD_HALF = 1 };
+
+// Cell record head (storage type): n, ux, uy, uz, T, qx, qy, qz, 1/tau,
+// (1 - Pr)/(n T^2), 1/(5T), unused; then n*Gx[Qx], Gy[Qy], Gz[2 Qz].
+enum { R_N = 0, R_UX, R_UY, R_UZ, R_T, R_QX, R_QY, R_QZ, R_ITAU, R_CS, R_I5T };
+
+// Everything a kernel needs to know about one instance (lives in device memory).
+struct InstDev {
+    int Nz, Qx, Qy, Qz, Q, QxQy;
+    int Nx, Ny, Nzq;              // per-axis expansion orders
+    int nchunks, rec_stride;
+    int visc_law;
+    double Kn, visc_param, Pr, dt, tol;
+    double Dtop, Dbot;            // sum over incoming velocities of w p_z Gw (n_w = 1)
+    double ext_top[2][3];         // ghost Nz+1 <- (Nz, Nz-1, Nz-2); Nz+2 <- (Nz+1, Nz, Nz-1)
+    double ext_bot[2][3];         // ghost 0 <- (1, 2, 3); ghost -1 <- (0, 1, 2)
+    // FP64 tables
+    const double *Hx, *Hy, *Pz;   // [Q_a][N_a + 1] basis values
+    const double *alpha, *beta;   // half-range recurrence, [kMaxN + 2]
+    // storage-typed tables (float or double)
+    const void *px, *py, *xi, *wx, *wy, *wz;
+    const void *gwx_top, *gwx_bot, *gwy, *gwz;  // wall equilibria per axis (Q_x, Q_x, Q_y, 2Q_z)
+    const void *inv_dz;                          // [Nz]
+    // state and work
+    void *F0, *F1, *F2;           // [Nz][Q] normalised populations f / w
+    void *rec;                    // [Nz][rec_stride]
+    double *partial;              // [nchunks][Nz][kNMom]
+    double *flux_part;            // [nchunks][2]: bottom, top outgoing flux
+    double *nw;                   // [2]: bottom, top wall density
+    double *prof;                 // [14][Nz]
+    double *Wold, *Wnew;          // [3][Nz]: n, u_x, T
+    double *res;                  // [1]
+    long long *steps;             // [1]
+    int *active;                  // [1]
+    int *status;                  // [1]: bit 0 non-finite / non-positive n, T
+};
+
+struct Tile { int inst, z0, zn, chunk; };
+
+// ---- equilibrium coefficients (shared by host set-up and device finalise) ----
+
+// a_l = int g(p; u, T) He_l(p) dp: a_0 = 1, a_1 = u, a_{l+1} = u a_l + l (T - 1) a_{l-1}
+// (from int g p He_l = u a_l + T l a_{l-1} and He_{l+1} = p He_l - l He_{l-1}).
+LBS_HD void full_coeffs(double u, double T, int N, double* a)
+{
+    a[0] = 1.0;
+    if (N >= 1) a[1] = u;
+    for (int l = 1; l < N; ++l) a[l + 1] = u * a[l] + l * (T - 1.0) * a[l - 1];
+}
+
+// b_l = int_0^inf g(p; u, T) pi_l(p) dp for the monic half-range polynomials,
+// by the modified-moment recurrence J_{l+1,k} = J_{l,k+1} - alpha_l J_{l,k} -
+// beta_l J_{l-1,k} started from the half-line Gaussian moments
+// J_{0,k} = M_k: M_0 = erfc(-u/sqrt(2T))/2, M_1 = u M_0 + T g(0),
+// M_{k+1} = u M_k + k T M_{k-1}.
+LBS_HD void half_coeffs(double u, double T, int N, const double* alpha, const double* beta,
+                        double* b)
+{
+    double J[kMaxN + 1][kMaxN + 1];  // J[l][k] is needed for k <= N - l only
+    const int K = N;
+    const double g0 = exp(-u * u / (2.0 * T)) * (1.0 / sqrt(2.0 * M_PI * T));
+    J[0][0] = 0.5 * erfc(-u / sqrt(2.0 * T));
+    if (K >= 1) J[0][1] = u * J[0][0] + T * g0;
+    for (int k = 1; k < K; ++k) J[0][k + 1] = u * J[0][k] + k * T * J[0][k - 1];
+    for (int l = 0; l < N; ++l)
+        for (int k = 0; k + l + 1 <= K; ++k)
+            J[l + 1][k] = J[l][k + 1] - alpha[l] * J[l][k] - (l > 0 ? beta[l] * J[l - 1][k] : 0.0);
+    for (int l = 0; l <= N; ++l) b[l] = J[l][0];
+}
+
+// relaxation time: power law tau = Kn T^(omega-1)/n, Sutherland tau = Kn sqrt(T)(1+S)/(n(T+S))
+LBS_HD double relax_time(int law, double Kn, double param, double n, double T)
+{
+    if (law == 0) return Kn * pow(T, param - 1.0) / n;
+    return Kn * sqrt(T) * (1.0 + param) / (n * (T + param));
+}
+
+// ---- host helpers (quadrature.cpp) ----
+void recurrence(int kind, int n, std::vector<double>& alpha, std::vector<double>& beta);
+int gauss_rule(int kind, int Q, double* nodes, double* weights);
+void hermite_basis(const double* p, int Q, int N, double* out);
+void half_basis(const double* xi, int Q, int N, const std::vector<double>& a,
+                const std::vector<double>& b, double* out);
+
+}  // namespace lbs

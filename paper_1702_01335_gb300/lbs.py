@@ -1,0 +1,276 @@
+"""Python binding of the C ABI in include/lbs.h (ctypes; argument marshalling only).
+
+Every step of the solver runs in the CUDA kernels of liblbs.so.  There is no
+CPU fallback: if the shared library is missing or cannot be loaded, `load()`
+raises.  PyTorch is used only to hand the library a CUDA stream and, for
+device-side checkpoints, device memory.
+"""
+import ctypes as C
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LBS_FP64 = 0
+LBS_FP32 = 1
+VISC_POWER = 0
+VISC_SUTHERLAND = 1
+MOMENT_NAMES = ("n", "ux", "T", "qx", "qz", "Pxx", "Pxz", "Pzz")
+PROFILE_NAMES = ("n", "ux", "uy", "uz", "T", "qx", "qy", "qz",
+                 "Pxx", "Pyy", "Pzz", "Pxy", "Pxz", "Pyz")
+STATUS = {0: "LBS_OK", 1: "LBS_ERR_ARG", 2: "LBS_ERR_CUDA", 3: "LBS_ERR_NONFINITE",
+          4: "LBS_ERR_NO_CONVERGENCE", 5: "LBS_ERR_QUADRATURE"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LbsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class _Orders(C.Structure):
+    _fields_ = [("Qx", C.c_int), ("Qy", C.c_int), ("Qz_half", C.c_int), ("N_eq", C.c_int)]
+
+
+class _Grid(C.Structure):
+    _fields_ = [("Nz", C.c_int), ("A", C.c_double)]
+
+
+class _Visc(C.Structure):
+    _fields_ = [("law", C.c_int), ("omega_or_S", C.c_double)]
+
+
+class _Desc(C.Structure):
+    _fields_ = [("orders", _Orders), ("grid", _Grid), ("Kn", C.c_double), ("u_w", C.c_double),
+                ("T_w", C.c_double), ("Pr", C.c_double), ("visc", _Visc), ("dt", C.c_double),
+                ("cfl", C.c_double)]
+
+
+EXPORTS = ("lbs_create", "lbs_batch_create", "lbs_destroy", "lbs_step", "lbs_run_to_steady",
+           "lbs_moments", "lbs_profiles", "lbs_residual", "lbs_steps_taken", "lbs_info",
+           "lbs_get_state", "lbs_set_state", "lbs_init_from_profiles", "lbs_quadrature",
+           "lbs_get_stream", "lbs_profile_steps", "lbs_last_error")
+
+
+def load(build_if_missing=True):
+    """Load liblbs.so (building it in-tree first if needed); raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and _build._stale():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("liblbs.so not built (run paper_1702_01335_gb300.build.build())")
+        lib = C.CDLL(path)
+        P, D, L = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_long)
+        H = C.POINTER(C.c_void_p)
+        lib.lbs_create.argtypes = [H, _Orders, _Grid, C.c_double, C.c_double, C.c_double, C.c_double,
+                                   _Visc, C.c_int, C.c_double, P]
+        lib.lbs_batch_create.argtypes = [H, C.POINTER(_Desc), C.c_int, C.c_int, P]
+        lib.lbs_destroy.argtypes = [P]
+        lib.lbs_step.argtypes = [P, C.c_long]
+        lib.lbs_run_to_steady.argtypes = [P, C.c_double, C.c_long, C.c_int, L]
+        lib.lbs_moments.argtypes = [P, C.c_int, D]
+        lib.lbs_profiles.argtypes = [P, C.c_int, D]
+        lib.lbs_residual.argtypes = [P, C.c_int, D]
+        lib.lbs_steps_taken.argtypes = [P, C.c_int, L]
+        lib.lbs_info.argtypes = [P, C.c_int, L, D]
+        lib.lbs_get_state.argtypes = [P, C.c_int, P, C.c_int]
+        lib.lbs_set_state.argtypes = [P, C.c_int, P, C.c_int]
+        lib.lbs_init_from_profiles.argtypes = [P, C.c_int, D]
+        lib.lbs_quadrature.argtypes = [C.c_int, C.c_int, D, D]
+        lib.lbs_get_stream.argtypes = [P, H]
+        lib.lbs_profile_steps.argtypes = [P, C.c_long, D]
+        lib.lbs_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name != "lbs_last_error":
+                getattr(lib, name).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _check(st):
+    if st != 0:
+        raise LbsError(st, _lib.lbs_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def quadrature(kind, Q):
+    """The solver's Gauss rule (host only): kind 0 full range, 1 half range."""
+    lib = load()
+    x, w = np.zeros(Q), np.zeros(Q)
+    _check(lib.lbs_quadrature(kind, Q, _dptr(x), _dptr(w)))
+    return x, w
+
+
+@dataclasses.dataclass
+class Instance:
+    """One Couette problem (see lbs_instance_desc in include/lbs.h)."""
+    Qx: int = 4
+    Qy: int = 4
+    Qz: int = 4
+    N_eq: int = 3
+    Nz: int = 32
+    A: float = 0.0
+    Kn: float = 0.1
+    u_w: float = 0.1
+    T_w: float = 1.0
+    Pr: float = 1.0
+    visc_law: int = VISC_POWER
+    visc_param: float = 1.0
+    dt: float = 0.0
+    cfl: float = 0.5
+
+    def desc(self):
+        return _Desc(_Orders(self.Qx, self.Qy, self.Qz, self.N_eq), _Grid(self.Nz, self.A),
+                     self.Kn, self.u_w, self.T_w, self.Pr, _Visc(self.visc_law, self.visc_param),
+                     self.dt, self.cfl)
+
+    @property
+    def Q(self):
+        return 2 * self.Qx * self.Qy * self.Qz
+
+
+def _torch_stream():
+    """torch's current CUDA stream if it is a created stream (the legacy default
+    stream cannot be captured into CUDA graphs; then the library makes its own)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            h = torch.cuda.current_stream().cuda_stream
+            return C.c_void_p(h) if h else None
+    except Exception:
+        pass
+    return None
+
+
+class Solver:
+    """A batch of Couette instances advanced together on one GPU stream."""
+
+    def __init__(self, instances, precision=LBS_FP64, stream=None):
+        if isinstance(instances, Instance):
+            instances = [instances]
+        self.instances = list(instances)
+        self.lib = load()
+        arr = (_Desc * len(self.instances))(*[i.desc() for i in self.instances])
+        self.h = C.c_void_p()
+        st = _torch_stream() if stream is None else C.c_void_p(stream)
+        _check(self.lib.lbs_batch_create(C.byref(self.h), arr, len(self.instances), precision, st))
+        self.precision = precision
+        self.dtype = np.float32 if precision == LBS_FP32 else np.float64
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream_handle(self):
+        """cudaStream_t (as an int) the solver queues its work on."""
+        out = C.c_void_p()
+        _check(self.lib.lbs_get_stream(self.h, C.byref(out)))
+        return out.value or 0
+
+    def torch_stream(self):
+        """The solver's stream as a torch.cuda.ExternalStream (for events and ordering)."""
+        import torch
+        return torch.cuda.ExternalStream(self.stream_handle)
+
+    def step(self, nsteps=1):
+        _check(self.lib.lbs_step(self.h, int(nsteps)))
+
+    def profile_steps(self, nsteps):
+        """Event-timed steps: (stage-kernel ms, finalise-kernel ms, whole-step ms), summed."""
+        out = np.zeros(3)
+        _check(self.lib.lbs_profile_steps(self.h, int(nsteps), _dptr(out)))
+        return tuple(out)
+
+    def state_bytes(self):
+        esize = 4 if self.precision == LBS_FP32 else 8
+        return sum(i.Nz * i.Q for i in self.instances) * esize
+
+    def get_state_all_ptr(self, ptr, to_host=True):
+        """Copy every instance's state, concatenated, to the buffer at address ptr."""
+        _check(self.lib.lbs_get_state(self.h, -1, C.c_void_p(ptr), int(to_host)))
+
+    def set_state_all_ptr(self, ptr, from_host=True):
+        """Set every instance's state from one concatenated buffer at address ptr."""
+        _check(self.lib.lbs_set_state(self.h, -1, C.c_void_p(ptr), int(from_host)))
+
+    def moments_all_ptr(self, ptr):
+        """Profiles of every instance ([8][Nz] each, concatenated) into host memory at ptr."""
+        _check(self.lib.lbs_moments(self.h, -1, C.cast(C.c_void_p(ptr), C.POINTER(C.c_double))))
+
+    def run_to_steady(self, tol=1e-8, max_steps=1_000_000, check_every=100, raise_on_fail=True):
+        out = (C.c_long * len(self.instances))()
+        st = self.lib.lbs_run_to_steady(self.h, tol, int(max_steps), int(check_every), out)
+        if st != 0 and (raise_on_fail or st != 4):
+            _check(st)
+        return np.array(out[:], dtype=np.int64)
+
+    def info(self, inst=0):
+        out = (C.c_long * 4)()
+        dt = C.c_double()
+        _check(self.lib.lbs_info(self.h, inst, out, C.byref(dt)))
+        return {"Q": out[0], "Nz": out[1], "QxQy": out[2], "esize": out[3], "dt": dt.value}
+
+    def moments(self, inst=0):
+        Nz = self.instances[inst].Nz
+        a = np.zeros((8, Nz))
+        _check(self.lib.lbs_moments(self.h, inst, _dptr(a)))
+        return dict(zip(MOMENT_NAMES, a))
+
+    def profiles(self, inst=0):
+        Nz = self.instances[inst].Nz
+        a = np.zeros((14, Nz))
+        _check(self.lib.lbs_profiles(self.h, inst, _dptr(a)))
+        return dict(zip(PROFILE_NAMES, a))
+
+    def residual(self, inst=0):
+        r = C.c_double()
+        _check(self.lib.lbs_residual(self.h, inst, C.byref(r)))
+        return r.value
+
+    def steps_taken(self, inst=0):
+        r = C.c_long()
+        _check(self.lib.lbs_steps_taken(self.h, inst, C.byref(r)))
+        return r.value
+
+    def get_state(self, inst=0):
+        """Normalised populations f_k / w_k, [Nz, Q], as a host array."""
+        I = self.instances[inst]
+        a = np.zeros((I.Nz, I.Q), dtype=self.dtype)
+        _check(self.lib.lbs_get_state(self.h, inst, a.ctypes.data_as(C.c_void_p), 1))
+        return a
+
+    def get_state_device(self, inst, out_ptr):
+        _check(self.lib.lbs_get_state(self.h, inst, C.c_void_p(out_ptr), 0))
+
+    def set_state(self, inst, a):
+        a = np.ascontiguousarray(a, dtype=self.dtype)
+        _check(self.lib.lbs_set_state(self.h, inst, a.ctypes.data_as(C.c_void_p), 1))
+
+    def set_state_device(self, inst, ptr):
+        _check(self.lib.lbs_set_state(self.h, inst, C.c_void_p(ptr), 0))
+
+    def init_from_profiles(self, inst, prof):
+        """prof: [8, Nz] in the order of MOMENT_NAMES (P rows unused)."""
+        prof = np.ascontiguousarray(prof, dtype=np.float64)
+        _check(self.lib.lbs_init_from_profiles(self.h, inst, _dptr(prof)))

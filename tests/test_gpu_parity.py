@@ -1,0 +1,176 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same
+seeded inputs, element by element (FP64 storage) and profile by profile (FP32
+storage), at sizes that span several z-tiles, several velocity chunks and ragged
+tails, plus the edge cases of the method."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._pair import gpu_f, oracle_of, profile_errors, rel_err, solver_of
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12     # relative, element-wise after tens of steps
+FP32_TOL = 2e-5      # relative per profile after tens of steps (FP32 storage)
+
+
+def _lbs():
+    import paper_1702_01335_gb300 as P
+    return P
+
+
+RAGGED = dict(Qx=6, Qy=5, Qz=7, N_eq=4, Nz=37, A=0.9, Kn=0.3, u_w=0.4, T_w=1.0, Pr=2.0 / 3.0,
+              visc_law=1, visc_param=0.5239)
+
+
+@pytest.mark.parametrize("params,steps", [(W.C1, 40), (RAGGED, 25)])
+def test_fp64_state_matches_oracle(params, steps):
+    P = _lbs()
+    o = oracle_of(params, dt=None)
+    s = solver_of(params, o.dt, P.LBS_FP64)
+    o.step(steps)
+    s.step(steps)
+    f_gpu = gpu_f(s, o)
+    f_ora = o.f[3:3 + o.Nz]
+    assert rel_err(f_gpu, f_ora) < FP64_TOL
+    errs = profile_errors(s.profiles(), o.profiles())
+    assert max(errs.values()) < FP64_TOL, "profile errors: " + repr(sorted(errs.items(), key=lambda kv: -kv[1]))
+    assert s.steps_taken() == steps
+
+
+def test_fp64_residual_sequence_matches_oracle():
+    P = _lbs()
+    o = oracle_of(RAGGED, dt=None)
+    s = solver_of(RAGGED, o.dt, P.LBS_FP64)
+    r = o.step(12, residuals=True)
+    # the first step divides by ||u_x|| of the rest state (zero up to rounding), so its
+    # residual is not comparable; every later one is
+    s.step(1)
+    for it in range(1, 12):
+        s.step(1)
+        assert abs(s.residual() / r[it] - 1) < 1e-9, (it, s.residual(), r[it])
+    assert r[-1] > 0
+
+
+def test_fp32_profiles_match_oracle():
+    P = _lbs()
+    o = oracle_of(RAGGED, dt=None)
+    s = solver_of(RAGGED, o.dt, P.LBS_FP32)
+    o.step(30)
+    s.step(30)
+    errs = profile_errors(s.profiles(), o.profiles())
+    assert max(errs.values()) < FP32_TOL, "profile errors: " + repr(sorted(errs.items(), key=lambda kv: -kv[1]))
+
+
+def test_batch_of_uneven_instances_matches_single_runs():
+    """A batch of instances of different Nz, Q and gas laws equals each run alone."""
+    P = _lbs()
+    ps = W.sweep(5, seed=11, nz_set=(6, 17, 24), qx_set=(3, 4, 6), qz_set=(2, 4, 5))
+    dts = [oracle_of(p, None).dt for p in ps]
+    dt = min(dts)
+    s = solver_of(ps, dt, P.LBS_FP64)
+    s.step(15)
+    for b, p in enumerate(ps):
+        o = oracle_of(p, dt)
+        o.step(15)
+        assert rel_err(gpu_f(s, o, b), o.f[3:3 + o.Nz]) < FP64_TOL, b
+
+
+def test_edge_minimum_sizes():
+    """Nz = 6 (three ghost-fed cells per wall) and the smallest velocity set (Q = 2, N = 0)."""
+    P = _lbs()
+    for p in (dict(W.C1, Nz=6), dict(W.C1, Qx=1, Qy=1, Qz=1, N_eq=0, Nz=8)):
+        o = oracle_of(p, None)
+        s = solver_of(p, o.dt, P.LBS_FP64)
+        o.step(20)
+        s.step(20)
+        assert rel_err(gpu_f(s, o), o.f[3:3 + o.Nz]) < FP64_TOL
+
+
+def test_warm_start_and_checkpoint():
+    """init_from_profiles seeds n Gx Gy Gz (1 + S); get/set_state round-trips."""
+    P = _lbs()
+    p = RAGGED
+    o = oracle_of(p, None)
+    s = solver_of(p, o.dt, P.LBS_FP64)
+    z = o.xc[3:3 + o.Nz]
+    prof = np.zeros((8, o.Nz))
+    prof[0] = 1.0 + 0.05 * np.cos(np.pi * z)
+    prof[1] = 0.8 * p["u_w"] * 2 * z
+    prof[2] = 1.0 + 0.1 * (0.25 - z ** 2)
+    prof[3] = 0.01 * z
+    prof[4] = -0.02 * z
+    s.init_from_profiles(0, prof)
+    u = np.zeros((3, o.Nz)); u[0] = prof[1]
+    q = np.zeros((3, o.Nz)); q[0] = prof[3]; q[2] = prof[4]
+    o.init_from_moments(prof[0], u, prof[2], q)
+    assert rel_err(gpu_f(s, o), o.f[3:3 + o.Nz]) < FP64_TOL
+    o.step(10)
+    s.step(10)
+    assert rel_err(gpu_f(s, o), o.f[3:3 + o.Nz]) < FP64_TOL
+    st = s.get_state(0)
+    s.step(5)
+    s.set_state(0, st)
+    assert np.array_equal(s.get_state(0), st)
+    s.step(5)
+    o.step(5)
+    assert rel_err(gpu_f(s, o), o.f[3:3 + o.Nz]) < FP64_TOL
+
+
+def test_nonfinite_inputs_rejected():
+    P = _lbs()
+    s = solver_of(W.C1, 0.004, P.LBS_FP64)
+    prof = np.ones((8, 32))
+    prof[2, 5] = np.nan
+    with pytest.raises(P.LbsError) as e:
+        s.init_from_profiles(0, prof)
+    assert e.value.status == 3
+    st = s.get_state(0)
+    st[3, 7] = np.inf
+    with pytest.raises(P.LbsError) as e:
+        s.set_state(0, st)
+    assert e.value.status == 3
+
+
+def test_run_to_steady_c1():
+    """Config C1 marches to R < 1e-8; the step count and profiles agree with the oracle."""
+    P = _lbs()
+    o = oracle_of(W.C1, None)
+    s = solver_of(W.C1, o.dt, P.LBS_FP64)
+    steps = s.run_to_steady(1e-8, max_steps=20000, check_every=50)[0]
+    r = o.step(int(steps), residuals=True)
+    first = int(np.nonzero(r < 1e-8)[0][0]) + 1
+    assert first == steps
+    assert rel_err(gpu_f(s, o), o.f[3:3 + o.Nz]) < 1e-10
+
+
+def test_c2_full_size_sampled_parity():
+    """Config C2 at full size in the benchmark's launch shape (a batch of replicas):
+    after a few steps every sampled replica matches the oracle's single solve."""
+    P = _lbs()
+    ref = oracle_of(W.C2, None)
+    ref.step(4)
+    for prec, tol in ((P.LBS_FP64, FP64_TOL), (P.LBS_FP32, FP32_TOL)):
+        s = solver_of([W.C2] * 16, ref.dt, prec)
+        s.step(4)
+        errs = [max(profile_errors(s.profiles(b), ref.profiles()).values()) for b in (0, 7, 15)]
+        assert max(errs) < tol, (prec, errs)
+        s.close()
+
+
+def test_c3_high_kn_fp32_free_molecular_bound():
+    """Config C3 (8192 velocities, Qz = 64) in FP32 storage: after a short march the shear
+    stress is bounded by the ballistic value of Eq. (Txy_bal) and mass is conserved."""
+    P = _lbs()
+    o = oracle_of(W.C3, None)
+    s = solver_of(W.C3, o.dt, P.LBS_FP32)
+    s.step(20)
+    o.step(20)
+    errs = profile_errors(s.profiles(), o.profiles())
+    assert max(errs[k] for k in ("n", "ux", "T", "Pxz", "Pxx", "Pzz")) < FP32_TOL, errs
+    p = s.profiles()
+    dz = np.diff(o.xf)
+    assert abs(np.sum(p["n"] * dz) - 1.0) < 1e-6
+    assert np.all(np.abs(p["Pxz"]) <= W.C3["u_w"] * math.sqrt(2 / math.pi) * 1.01)

@@ -1,0 +1,54 @@
+"""Seeded synthetic workloads (parameter sets only; no arithmetic of the method).
+
+Shared by the tests, the smoke check and the benchmark.  Each workload is a
+plain dict of instance parameters with the field names of
+`paper_1702_01335_gb300.Instance`; the oracle takes the same values.
+
+  C1  plain BGK-limit Couette (Shakhov with Pr = 1): 4 x 4 x (2 x 4) velocities,
+      N_eq = 3, Nz = 32 uniform, Kn = 0.1, u_w = 0.1
+  C2  Maxwell molecules (Pr = 2/3, mu ~ T): 8 x 8 x (2 x 16) = 2048 velocities,
+      N_eq = 4, Nz = 128 stretched toward the walls (A = 0.98), Kn = 1, u_w = 0.5
+  C3  high Kn: 16 x 4 x (2 x 64) = 8192 velocities, N_eq = 4, Nz = 256 uniform,
+      Kn = 100, u_w = 0.05, Pr = 2/3, mu ~ T^0.5
+  sweep(n, seed)  instances drawn like the batched Kn / wall-speed / gas-law sweep:
+      Kn log-uniform in [0.01, 100], u_w uniform in [0.05, 1], T_w = 1, Pr = 2/3,
+      first half mu ~ T^omega (omega uniform in [0.5, 1]), second half Sutherland
+      with S alternating 0.27 / 0.52; Nz, Qx, Qz drawn from the listed sets, Qy = 4,
+      N_eq = 4, uniform grid (numpy PCG64 streams)
+"""
+import numpy as np
+
+C1 = dict(Qx=4, Qy=4, Qz=4, N_eq=3, Nz=32, A=0.0, Kn=0.1, u_w=0.1, T_w=1.0, Pr=1.0,
+          visc_law=0, visc_param=1.0)
+C2 = dict(Qx=8, Qy=8, Qz=16, N_eq=4, Nz=128, A=0.98, Kn=1.0, u_w=0.5, T_w=1.0, Pr=2.0 / 3.0,
+          visc_law=0, visc_param=1.0)
+C3 = dict(Qx=16, Qy=4, Qz=64, N_eq=4, Nz=256, A=0.0, Kn=100.0, u_w=0.05, T_w=1.0, Pr=2.0 / 3.0,
+          visc_law=0, visc_param=0.5)
+
+SWEEP_SEED, TRAIN_SEED, HELDOUT_SEED = 1702, 1703, 1704
+NZ_SET = (32, 48, 64, 96, 128, 192, 256, 384, 512)
+QX_SET = (4, 6, 8, 12, 16)
+QZ_SET = (4, 8, 12, 16, 24, 32, 48)
+
+
+def sweep(n=64, seed=SWEEP_SEED, nz_set=NZ_SET, qx_set=QX_SET, qz_set=QZ_SET):
+    """n instances of the batched sweep, drawn from numpy PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for b in range(n):
+        Kn = float(10.0 ** rng.uniform(-2.0, 2.0))
+        u_w = float(rng.uniform(0.05, 1.0))
+        if b < n // 2:
+            law, param = 0, float(rng.uniform(0.5, 1.0))
+        else:
+            law, param = 1, (0.27 if (b - n // 2) % 2 == 0 else 0.52)
+        out.append(dict(Qx=int(rng.choice(qx_set)), Qy=4, Qz=int(rng.choice(qz_set)), N_eq=4,
+                        Nz=int(rng.choice(nz_set)), A=0.0, Kn=Kn, u_w=u_w, T_w=1.0, Pr=2.0 / 3.0,
+                        visc_law=law, visc_param=param))
+    return out
+
+
+def random_state(shape, seed, amplitude=0.05):
+    """Seeded multiplicative perturbation factors 1 + a N(0,1) (for parity inputs)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return 1.0 + amplitude * rng.standard_normal(shape)
