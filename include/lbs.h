@@ -155,6 +155,28 @@ lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host)
  * LBS_ERR_NONFINITE if a value is not finite or n <= 0 or T <= 0. */
 lbs_status lbs_init_from_profiles(lbs_handle h, int inst, const double* prof);
 
+/* Profiles of a distribution the caller holds in device memory, computed
+ * without allocating device memory.  The paper has no counterpart: this is a
+ * service for callers that cannot call cudaMalloc where they need moments, for
+ * example code running under another framework's device-memory budget, or a
+ * latency-critical loop where the device-wide synchronisation of cudaMalloc
+ * and cudaFree is not acceptable.
+ *   f_dev     device pointer, [Nz][Q] normalised populations of instance inst's
+ *             velocity set in the handle's precision (layout of lbs_get_state);
+ *             read only.
+ *   prof_dev  device pointer, [14][Nz] FP64 output in the layout of
+ *             lbs_profiles.
+ * The work is queued on the handle's stream; the call does not wait for it.
+ * Its only scratch is a fixed 2 MiB array in the library's device image (every
+ * GPU that loads the library holds it until the process exits), so the
+ * instance must satisfy ceil(Q / 512) * Nz <= 20164, else LBS_ERR_ARG.  The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array:
+ * calls whose GPU work overlaps (other streams, other threads on the same
+ * device) race and must be serialised by the caller.  The call allocates
+ * nothing and frees nothing. */
+lbs_status lbs_moments_static(lbs_handle h, int inst, const void* f_dev, double* prof_dev);
+
 /* Run nsteps steps launching every kernel directly with CUDA events around
  * each on the handle's stream, and return summed device times in ms:
  * out_ms[0] the stage kernels (WENO advection, collision, RK combine, moment

@@ -74,7 +74,22 @@ struct lbs_solver {
     double* d_macro = nullptr;  // [8][maxNz] staging for warm starts
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0;
+    int device = 0;
 };
+
+int lbs::handle_view(void* hv, int inst, HandleView* out)
+{
+    lbs_solver* h = static_cast<lbs_solver*>(hv);
+    if (!h || !out || inst < 0 || inst >= h->ninst) return fail(LBS_ERR_ARG, "invalid handle or instance index");
+    out->d_inst = h->d_inst;
+    out->inst = h->idev[inst];
+    out->fp32 = h->fp32;
+    out->device = h->device;
+    out->stream = static_cast<void*>(h->stream);
+    return LBS_OK;
+}
+
+int lbs::record_error(int status, const char* msg) { return fail(static_cast<lbs_status>(status), msg); }
 
 // ---------------------------------------------------------------- set-up ----
 static lbs_status validate(const lbs_instance_desc& d)
@@ -428,6 +443,7 @@ lbs_status lbs_batch_create(lbs_handle* out, const lbs_instance_desc* desc, int 
         if (s != LBS_OK) return fail(s, "instance " + std::to_string(b) + ": " + g_err);
     }
     lbs_solver* h = new lbs_solver();
+    if (cudaGetDevice(&h->device) != cudaSuccess) h->device = 0;
     h->fp32 = prec == LBS_FP32_STORE_FP64_ACC;
     h->esize = h->fp32 ? 4 : 8;
     h->ninst = n;

@@ -96,6 +96,18 @@ LBS_HD double relax_time(int law, double Kn, double param, double n, double T)
     return Kn * sqrt(T) * (1.0 + param) / (n * (T + param));
 }
 
+// ---- access to a handle for entry points defined outside api.cu ----
+struct HandleView {
+    const InstDev* d_inst;   // device array of descriptors
+    InstDev inst;            // host copy of the selected instance's descriptor
+    int fp32, device;
+    void* stream;            // cudaStream_t
+};
+// fills *out for instance inst of handle h (an lbs_handle); returns 0 or an lbs_status
+int handle_view(void* h, int inst, HandleView* out);
+// records msg as the calling thread's last error and returns status
+int record_error(int status, const char* msg);
+
 // ---- host helpers (quadrature.cpp) ----
 void recurrence(int kind, int n, std::vector<double>& alpha, std::vector<double>& beta);
 int gauss_rule(int kind, int Q, double* nodes, double* weights);

@@ -55,7 +55,7 @@ class _Desc(C.Structure):
 EXPORTS = ("lbs_create", "lbs_batch_create", "lbs_destroy", "lbs_step", "lbs_run_to_steady",
            "lbs_moments", "lbs_profiles", "lbs_residual", "lbs_steps_taken", "lbs_info",
            "lbs_get_state", "lbs_set_state", "lbs_init_from_profiles", "lbs_quadrature",
-           "lbs_get_stream", "lbs_profile_steps", "lbs_last_error")
+           "lbs_get_stream", "lbs_profile_steps", "lbs_moments_static", "lbs_last_error")
 
 
 def load(build_if_missing=True):
@@ -89,6 +89,7 @@ def load(build_if_missing=True):
         lib.lbs_quadrature.argtypes = [C.c_int, C.c_int, D, D]
         lib.lbs_get_stream.argtypes = [P, H]
         lib.lbs_profile_steps.argtypes = [P, C.c_long, D]
+        lib.lbs_moments_static.argtypes = [P, C.c_int, P, P]
         lib.lbs_last_error.restype = C.c_char_p
         for name in EXPORTS:
             if name != "lbs_last_error":
@@ -205,6 +206,11 @@ class Solver:
     def state_bytes(self):
         esize = 4 if self.precision == LBS_FP32 else 8
         return sum(i.Nz * i.Q for i in self.instances) * esize
+
+    def moments_static(self, inst, f_dev_ptr, prof_dev_ptr):
+        """Profiles [14][Nz] (FP64, device) of the device state at f_dev_ptr, computed
+        without any device allocation (lbs_moments_static); queued on the solver's stream."""
+        _check(self.lib.lbs_moments_static(self.h, inst, C.c_void_p(f_dev_ptr), C.c_void_p(prof_dev_ptr)))
 
     def get_state_all_ptr(self, ptr, to_host=True):
         """Copy every instance's state, concatenated, to the buffer at address ptr."""
