@@ -185,6 +185,17 @@ lbs_status lbs_moments_static(lbs_handle h, int inst, const void* f_dev, double*
  * the arithmetic is that of lbs_step. */
 lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms);
 
+/* Work decomposition of the stage kernel (no effect on the arithmetic): each
+ * CTA of 128 threads updates 128*V velocities (V in {1, 2, 4}) of about ZT
+ * consecutive cells (3 <= ZT <= 64).  Used by the tile autotuner.  Waits for
+ * the handle's stream and recomputes the moment partials of the current state.
+ * LBS_ERR_ARG outside the ranges. */
+lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT);
+
+/* Current tiling: V, ZT, number of stage CTAs, dynamic shared memory per CTA.
+ * Any output pointer may be NULL. */
+lbs_status lbs_get_tiling(lbs_handle h, int* V, int* ZT, int* ntiles, long* smem_bytes);
+
 /* The CUDA stream (cudaStream_t) the handle queues its work on: the one given at
  * creation, or the stream the library created when NULL was given. */
 lbs_status lbs_get_stream(lbs_handle h, void** out);

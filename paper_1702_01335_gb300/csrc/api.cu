@@ -20,6 +20,7 @@ cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int nins
                             cudaStream_t st);
 cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,
                         cudaStream_t st);
+size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage);
 }  // namespace lbs
 
 using namespace lbs;
@@ -43,10 +44,12 @@ namespace {
 
 struct InstHost {
     lbs_instance_desc d;
-    int Nz, Q, Qx, Qy, Qz, Nx, Ny, Nzq, nchunks, rec_stride, nzm_max;
+    int Nz, Q, Qx, Qy, Qz, Nx, Ny, Nzq, nchunks, nzm_max;
     double dt;
     std::vector<double> xc, xf;  // cell centres (s = -3..Nz+2, 0-based), interfaces
 };
+
+constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory of a stage CTA
 
 struct Pool {  // bump allocator over one device allocation
     size_t bytes = 0;
@@ -69,6 +72,7 @@ struct lbs_solver {
     InstDev* d_inst = nullptr;
     Tile* d_tiles = nullptr;
     int ntiles = 0;
+    size_t max_tiles = 0;
     size_t smem = 0;
     unsigned char* pool = nullptr;
     double* d_macro = nullptr;  // [8][maxNz] staging for warm starts
@@ -150,18 +154,21 @@ static void build_tiles(lbs_solver* h, std::vector<Tile>& tiles)
     for (int b = 0; b < h->ninst; ++b) {
         InstHost& I = h->ih[b];
         I.nchunks = (I.Q + KC - 1) / KC;
-        int nzt = std::min((I.Nz + h->ZT - 1) / h->ZT, I.Nz / 3);
-        nzt = std::max(nzt, 1);
-        const int base = I.Nz / nzt, rem = I.Nz % nzt;
         int nzm_max = 0;
         for (int c = 0; c < I.nchunks; ++c) {
             const int k0 = c * KC, k1 = std::min(I.Q, k0 + KC) - 1;
             nzm_max = std::max(nzm_max, k1 / (I.Qx * I.Qy) - k0 / (I.Qx * I.Qy) + 1);
         }
         I.nzm_max = nzm_max;
+        const int G = I.Qx + I.Qy + nzm_max;
+        // z-tiles of about ZT cells, at least 3 cells each, within the shared-memory budget
+        int zt = std::max(3, std::min(h->ZT, kMaxZT));
+        while (zt > 3 && stage_smem_bytes(h->fp32, h->V, zt, G, 3) > kSmemBudget) --zt;
+        int nzt = std::min((I.Nz + zt - 1) / zt, I.Nz / 3);
+        nzt = std::max(nzt, 1);
+        const int base = I.Nz / nzt, rem = I.Nz % nzt;
         const int zmax = base + (rem ? 1 : 0);
-        const size_t RS = kRecHead + I.Qx + I.Qy + nzm_max;
-        smem = std::max(smem, (size_t)zmax * (kThreads / 32) * kNMom * 8 + (size_t)zmax * RS * h->esize);
+        smem = std::max(smem, stage_smem_bytes(h->fp32, h->V, zmax, G, 3));
         for (int c = 0; c < I.nchunks; ++c) {
             int z0 = 0;
             for (int t = 0; t < nzt; ++t) {
@@ -204,7 +211,6 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         I.Nx = std::min(d.orders.N_eq, I.Qx - 1);
         I.Ny = std::min(d.orders.N_eq, I.Qy - 1);
         I.Nzq = std::min(d.orders.N_eq, I.Qz - 1);
-        I.rec_stride = kRecHead + I.Qx + I.Qy + 2 * I.Qz;
         h->maxNz = std::max(h->maxNz, I.Nz);
     }
     build_tiles(h, tiles);
@@ -268,7 +274,8 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         InstDev& D = h->idev[b];
         D.Nz = Nz; D.Qx = I.Qx; D.Qy = I.Qy; D.Qz = I.Qz; D.Q = I.Q; D.QxQy = I.Qx * I.Qy;
         D.Nx = I.Nx; D.Ny = I.Ny; D.Nzq = I.Nzq;
-        D.nchunks = I.nchunks; D.rec_stride = I.rec_stride;
+        D.nchunks = I.nchunks;
+        D.bulk = ((size_t)I.Q * sizeof(T)) % 16 == 0;  // every row segment starts on 16 bytes
         D.visc_law = d.visc.law; D.Kn = d.Kn; D.visc_param = d.visc.omega_or_S; D.Pr = d.Pr;
         D.dt = I.dt; D.tol = 0.0;
         const std::vector<double>& xc = I.xc;  // xc[s + 3]
@@ -292,7 +299,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         // memory layout
         Off& o = off[b];
         const size_t es = sizeof(T);
-        o.Hx = pool.take(t.Hx.size() * 8); o.Hy = pool.take(t.Hy.size() * 8); o.Pz = pool.take(t.Pz.size() * 8);
+        o.Hx = pool.take(t.Hx.size() * es); o.Hy = pool.take(t.Hy.size() * es); o.Pz = pool.take(t.Pz.size() * es);
         o.alpha = pool.take(t.alpha.size() * 8); o.beta = pool.take(t.beta.size() * 8);
         o.px = pool.take(I.Qx * es); o.py = pool.take(I.Qy * es); o.xi = pool.take(I.Qz * es);
         o.wx = pool.take(I.Qx * es); o.wy = pool.take(I.Qy * es); o.wz = pool.take(I.Qz * es);
@@ -300,15 +307,20 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         o.gwz = pool.take(2 * I.Qz * es); o.idz = pool.take(Nz * es);
         const size_t nf = (size_t)Nz * I.Q;
         o.F0 = pool.take(nf * es); o.F1 = pool.take(nf * es); o.F2 = pool.take(nf * es);
-        o.rec = pool.take((size_t)Nz * I.rec_stride * es);
-        o.partial = pool.take((size_t)I.nchunks * Nz * kNMom * 8);
-        o.flux = pool.take((size_t)I.nchunks * 2 * 8);
+        o.rec = pool.take((size_t)Nz * kRecStride * es);
+        const size_t maxch = (I.Q + kThreads - 1) / kThreads;  // chunks at V = 1, the finest tiling
+        o.partial = pool.take(maxch * Nz * kNMom * 8);
+        o.flux = pool.take(maxch * 2 * 8);
         o.nw = pool.take(2 * 8); o.prof = pool.take(14 * (size_t)Nz * 8);
         o.Wold = pool.take(3 * (size_t)Nz * 8); o.Wnew = pool.take(3 * (size_t)Nz * 8);
         o.res = pool.take(8); o.steps = pool.take(8); o.active = pool.take(4); o.status = pool.take(4);
     }
     const size_t inst_off = pool.take(sizeof(InstDev) * h->ninst);
-    const size_t tile_off = pool.take(sizeof(Tile) * tiles.size());
+    size_t max_tiles = 0;  // tiles of the finest tiling (V = 1, 3-cell z-tiles)
+    for (int b = 0; b < h->ninst; ++b)
+        max_tiles += (size_t)((h->ih[b].Q + kThreads - 1) / kThreads) * std::max(1, h->ih[b].Nz / 3);
+    h->max_tiles = max_tiles;
+    const size_t tile_off = pool.take(sizeof(Tile) * max_tiles);
     const size_t macro_off = pool.take(8 * (size_t)h->maxNz * 8);
     void* mem = nullptr;
     CK(cudaMalloc(&mem, pool.bytes));
@@ -320,7 +332,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         const Off& o = off[b];
         const Tables& t = tb[b];
         const InstHost& I = h->ih[b];
-        put<double>(img, o.Hx, t.Hx); put<double>(img, o.Hy, t.Hy); put<double>(img, o.Pz, t.Pz);
+        put<T>(img, o.Hx, t.Hx); put<T>(img, o.Hy, t.Hy); put<T>(img, o.Pz, t.Pz);
         put<double>(img, o.alpha, t.alpha); put<double>(img, o.beta, t.beta);
         put<T>(img, o.px, t.px); put<T>(img, o.py, t.py); put<T>(img, o.xi, t.xi);
         put<T>(img, o.wx, t.wx); put<T>(img, o.wy, t.wy); put<T>(img, o.wz, t.wz);
@@ -331,9 +343,9 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         for (size_t e = 0; e < nf; ++e) F0[e] = T(1);  // rest Maxwellian n = 1, T = 1: f_k = w_k
         *reinterpret_cast<int*>(img.data() + o.active) = 1;
         InstDev& D = h->idev[b];
-        D.Hx = reinterpret_cast<const double*>(P + o.Hx);
-        D.Hy = reinterpret_cast<const double*>(P + o.Hy);
-        D.Pz = reinterpret_cast<const double*>(P + o.Pz);
+        D.Hx = P + o.Hx;
+        D.Hy = P + o.Hy;
+        D.Pz = P + o.Pz;
         D.alpha = reinterpret_cast<const double*>(P + o.alpha);
         D.beta = reinterpret_cast<const double*>(P + o.beta);
         D.px = P + o.px; D.py = P + o.py; D.xi = P + o.xi; D.wx = P + o.wx; D.wy = P + o.wy; D.wz = P + o.wz;
@@ -592,6 +604,36 @@ lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms)
     out_ms[1] = tfin;
     out_ms[2] = tstep;
     return check_status(h);
+}
+
+lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT)
+{
+    if (!h || (V != 1 && V != 2 && V != 4) || ZT < 3 || ZT > kMaxZT)
+        return fail(LBS_ERR_ARG, "tiling needs V in {1, 2, 4} and 3 <= ZT <= 64");
+    CK(cudaStreamSynchronize(h->stream));
+    drop_graph(h);
+    h->V = V;
+    h->ZT = ZT;
+    std::vector<Tile> tiles;
+    build_tiles(h, tiles);
+    if (tiles.size() > h->max_tiles) return fail(LBS_ERR_ARG, "tile list exceeds its buffer");
+    for (int b = 0; b < h->ninst; ++b) h->idev[b].nchunks = h->ih[b].nchunks;
+    CK(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->ninst, cudaMemcpyHostToDevice, h->stream));
+    h->ntiles = (int)tiles.size();
+    lbs_status s = analyse(h);  // partial sums of the new chunking
+    if (s != LBS_OK) return s;
+    return check_status(h);
+}
+
+lbs_status lbs_get_tiling(lbs_handle h, int* V, int* ZT, int* ntiles, long* smem_bytes)
+{
+    if (!h) return fail(LBS_ERR_ARG, "invalid handle");
+    if (V) *V = h->V;
+    if (ZT) *ZT = h->ZT;
+    if (ntiles) *ntiles = h->ntiles;
+    if (smem_bytes) *smem_bytes = (long)h->smem;
+    return LBS_OK;
 }
 
 lbs_status lbs_get_stream(lbs_handle h, void** out)

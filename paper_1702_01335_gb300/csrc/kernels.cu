@@ -1,23 +1,27 @@
 // CUDA kernels of one RK-3 stage of the mixed-quadrature Shakhov scheme.
 //
 // Per stage (Eq. rk3 around Eq. L_def):
-//   stage_kernel     one CTA per tile = (instance, z-range, velocity chunk).
-//                    Each thread owns V velocities and marches up its z-range
-//                    with a register window of F_in; it forms the WENO-5
-//                    interface fluxes (Eqs. weno5_flux - weno_sigma, Table
-//                    weno), the divergence of Eq. (flux), the relaxation to
-//                    the cell's Shakhov target and the Shu-Osher combine, and
-//                    stores F_out.  Ghost values are synthesised in registers:
-//                    outgoing ones by the quadratic extrapolation of the
-//                    Appendix, incoming ones as n_w times the wall
-//                    equilibrium.  In the same pass it accumulates the raw
-//                    moments of F_out per cell and, in tiles that end at a
-//                    wall, the outgoing WENO flux of F_out through the wall
-//                    interface, so the next stage needs no extra read of F.
-//   finalize_cells   one CTA per cell: sums the per-chunk moment partials in
-//                    FP64, forms n, u, P, T, q (Eq. qdef) and tau, and writes
-//                    the cell record (the per-axis factors of the truncated
-//                    Hermite equilibrium, Sec. III) used by the next stage.
+//   stage_kernel     one CTA per tile = (instance, z-range of <= 64 cells,
+//                    velocity chunk of 128*V velocities).  The rows of F_in
+//                    the tile needs (its cells and a 3-cell halo each side) and
+//                    its rows of F_l are staged into shared memory by TMA bulk
+//                    copies (one cp.async.bulk per row, one mbarrier).  While
+//                    they land, the CTA evaluates the per-axis factors of the
+//                    truncated Hermite equilibrium (Sec. III) of its cells.
+//                    Ghost rows are then built in shared memory: outgoing
+//                    populations by the quadratic extrapolation of the
+//                    Appendix, incoming ones as n_w times the wall equilibrium.
+//                    Each thread marches up the z-range for its V velocities
+//                    with a register window: WENO-5 interface fluxes (Eqs.
+//                    weno5_flux - weno_sigma, Table weno), the divergence of
+//                    Eq. (flux), relaxation to n G_x G_y G_z (1 + S) and the
+//                    Shu-Osher combine; it stores F_out and accumulates the raw
+//                    moments of F_out (FP32 within a warp in FP32 mode, FP64
+//                    across warps and chunks).  Tiles that end at a wall also
+//                    reduce the outgoing WENO flux of F_out through the wall.
+//   finalize_cells   one thread per cell: sums the per-chunk moment partials
+//                    in FP64, forms n, u, P, T, q (Eq. qdef) and tau, and writes
+//                    the cell record (scalars and expansion coefficients).
 //   finalize_inst    one CTA per instance: wall densities n_w (zero net mass
 //                    flux, Appendix) and, after the third stage, the residual.
 //
@@ -25,12 +29,54 @@
 // k = ((sg*Qz + m)*Qx + i)*Qy + j fastest, holding f_k / w_k.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "lbs_internal.h"
 
 namespace lbs {
 
 template <typename T> struct Acc { typedef double type; };
 template <> struct Acc<float> { typedef float type; };
+
+constexpr uint32_t kSpinLimit = 1u << 26;  // bounded mbarrier waits (~seconds)
+constexpr int kIdz = 11;                   // smem copy of a record: slot 11 holds 1/dz
+
+// ---- PTX helpers: mbarrier and bulk global -> shared copies ------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 
 // WENO-5 reconstruction of five upwind-ordered values (no advection factor).
 // The weights are scale free, so they are formed from r_q = sigma_q / max
@@ -68,6 +114,38 @@ __device__ __forceinline__ T weno5(T v0, T v1, T v2, T v3, T v4)
     return (w1 * c1 + w2 * c2 + w3 * c3) / (w1 + w2 + w3);
 }
 
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// FP32 form: the same weights with sigma_q^2 floored at 1e-37 (branch free,
+// hardware reciprocals).  As sigma_q -> 0 the floor gives exactly the limits
+// of Table (weno); it changes nothing while sigma_q^2 > 1e-30, i.e. for
+// differences above the FP32 resolution of O(1) normalised populations.
+template <>
+__device__ __forceinline__ float weno5<float>(float v0, float v1, float v2, float v3, float v4)
+{
+    const float c1 = fmaf(1.f / 3.f, v0, fmaf(-7.f / 6.f, v1, (11.f / 6.f) * v2));
+    const float c2 = fmaf(-1.f / 6.f, v1, fmaf(5.f / 6.f, v2, (1.f / 3.f) * v3));
+    const float c3 = fmaf(1.f / 3.f, v2, fmaf(5.f / 6.f, v3, (-1.f / 6.f) * v4));
+    float a = fmaf(-2.f, v1, v0 + v2), b = fmaf(3.f, v2, fmaf(-4.f, v1, v0));
+    const float s1 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
+    a = fmaf(-2.f, v2, v1 + v3);
+    b = v1 - v3;
+    const float s2 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
+    a = fmaf(-2.f, v3, v2 + v4);
+    b = fmaf(3.f, v2, fmaf(-4.f, v3, v4));
+    const float s3 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
+    const float w1 = 0.1f * rcp_approx(fmaf(s1, s1, 1e-37f));
+    const float w2 = 0.6f * rcp_approx(fmaf(s2, s2, 1e-37f));
+    const float w3 = 0.3f * rcp_approx(fmaf(s3, s3, 1e-37f));
+    const float inv = rcp_approx(w1 + w2 + w3);
+    return fmaf(w1 * inv, c1, fmaf(w2 * inv, c2, (w3 * inv) * c3));
+}
+
 template <typename T>
 __device__ __forceinline__ T ld(const void* p, int i) { return static_cast<const T*>(p)[i]; }
 
@@ -85,59 +163,155 @@ __device__ double block_sum(double v, double* red)
     return s;
 }
 
+// Warp reduce-scatter of 16 values: afterwards lane l holds the warp total of
+// value m(l) = 8 b4 + 4 b3 + 2 b2 + b1 (b = bits of l); lanes l, l^1 agree.
+// 16 shuffles per lane instead of 16 x 5 for 16 separate butterflies.
+template <typename A>
+__device__ __forceinline__ A reduce_scatter16(A (&v)[16], int lane)
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool hi = lane & 16;
+        const A send = hi ? v[i] : v[i + 8], keep = hi ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = lane & 8;
+        const A send = hi ? v[i] : v[i + 4], keep = hi ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = lane & 4;
+        const A send = hi ? v[i] : v[i + 2], keep = hi ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool hi = lane & 2;
+        const A send = hi ? v[0] : v[1], keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// shared-memory layout of a stage CTA (element offsets are in bytes)
+struct StageSmem {
+    size_t fin, f0, g, sc, red, total;
+};
+__host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize, int asize, bool withF0)
+{
+    StageSmem L;
+    size_t o = 0;
+    L.fin = o; o += (size_t)(zn + 6) * KC * esize;
+    L.f0 = o; o += withF0 ? (size_t)zn * KC * esize : 0;
+    L.g = o; o += (size_t)zn * G * esize;
+    L.sc = o; o += (size_t)zn * kRecHead * esize;
+    o = (o + 15) & ~size_t(15);
+    L.red = o; o += (size_t)zn * (kThreads / 32) * 16 * asize;
+    L.total = o;
+    return L;
+}
+
 // ----------------------------------------------------------------------------
 // stage_kernel<T, V, STAGE>: STAGE 1..3 are the RK stages; STAGE 0 only
-// analyses F_in (moments and wall fluxes) without writing F.
+// analyses F0 (moments and wall fluxes) without writing F.
 // ----------------------------------------------------------------------------
 template <typename T, int V, int STAGE>
 __global__ void __launch_bounds__(kThreads)
 stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
 {
     typedef typename Acc<T>::type A;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double wall_red[kThreads / 32];
     const Tile tile = tiles[blockIdx.x];
     const InstDev& I = insts[tile.inst];
     if (*I.active == 0) return;
 
     const int Nz = I.Nz, Q = I.Q, Qx = I.Qx, Qy = I.Qy, Qz = I.Qz, QxQy = I.QxQy;
     const int z0 = tile.z0, zn = tile.zn;            // cells z0 .. z0+zn-1 (0-based)
-    const int KC = kThreads * V;
-    const int k0 = tile.chunk * KC;
-    const int kend = min(Q, k0 + KC);
+    constexpr int KC = kThreads * V;
+    const int k0 = tile.chunk * KC, kend = min(Q, k0 + KC), kn = kend - k0;
     const int zm_lo = k0 / QxQy, zm_hi = (kend - 1) / QxQy, nzm = zm_hi - zm_lo + 1;
-    const int RS = kRecHead + Qx + Qy + nzm;         // smem record stride
-    const int nwarp = kThreads / 32, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G = Qx + Qy + nzm;                     // per-cell factors held in smem
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr bool kF0 = STAGE >= 2;
 
-    // shared memory: per-warp moment partials [zn][nwarp][kNMom] (double), then
-    // the cell records [zn][RS] (T)
-    double* red = reinterpret_cast<double*>(smem_raw);
-    T* recs = reinterpret_cast<T*>(red + (size_t)zn * nwarp * kNMom);
-    __shared__ double wall_red[8];
+    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(A), kF0);
+    T* Fs = reinterpret_cast<T*>(smem_raw + L.fin);   // rows: cells z0-3 .. z0+zn+2
+    T* F0s = reinterpret_cast<T*>(smem_raw + L.f0);   // rows: cells z0 .. z0+zn-1
+    T* gsm = reinterpret_cast<T*>(smem_raw + L.g);
+    T* scs = reinterpret_cast<T*>(smem_raw + L.sc);
+    A* red = reinterpret_cast<A*>(smem_raw + L.red);
 
-    const T* Fin = static_cast<const T*>(STAGE == 0 ? I.F0 : STAGE == 1 ? I.F0 : STAGE == 2 ? I.F1 : I.F2);
+    const T* Fin = static_cast<const T*>(STAGE <= 1 ? I.F0 : STAGE == 2 ? I.F1 : I.F2);
     T* Fout = static_cast<T*>(STAGE == 1 ? I.F1 : STAGE == 2 ? I.F2 : I.F0);
-    const T* F0 = static_cast<const T*>(I.F0);
+    const T* F0g = static_cast<const T*>(I.F0);
+    const int s_lo = max(0, z0 - 3), s_hi = min(Nz - 1, z0 + zn + 2);
 
-    if (STAGE > 0) {
-        const T* R = static_cast<const T*>(I.rec);
-        for (int e = threadIdx.x; e < zn * RS; e += kThreads) {
-            const int c = e / RS, r = e - c * RS;
-            const int gr = r < kRecHead + Qx + Qy ? r : r + zm_lo;  // skip unused Gz rows
-            recs[e] = R[(size_t)(z0 + c) * I.rec_stride + gr];
+    // ---- 1. stage the input rows (TMA bulk copies, or plain loads if unaligned)
+    if (I.bulk) {
+        if (tid == 0) {
+            mbar_init(&bar, 1);
+            fence_barrier_init();
         }
         __syncthreads();
+        if (tid == 0) {
+            const uint32_t bytes = kn * sizeof(T);
+            mbar_expect_tx(&bar, bytes * ((s_hi - s_lo + 1) + (kF0 ? zn : 0)));
+            for (int s = s_lo; s <= s_hi; ++s)
+                bulk_g2s(Fs + (size_t)(s - z0 + 3) * KC, Fin + (size_t)s * Q + k0, bytes, &bar);
+            if (kF0)
+                for (int c = 0; c < zn; ++c)
+                    bulk_g2s(F0s + (size_t)c * KC, F0g + (size_t)(z0 + c) * Q + k0, bytes, &bar);
+        }
+    } else {
+        for (int s = s_lo; s <= s_hi; ++s)
+            for (int kl = tid; kl < kn; kl += kThreads) Fs[(size_t)(s - z0 + 3) * KC + kl] = Fin[(size_t)s * Q + k0 + kl];
+        if (kF0)
+            for (int c = 0; c < zn; ++c)
+                for (int kl = tid; kl < kn; kl += kThreads) F0s[(size_t)c * KC + kl] = F0g[(size_t)(z0 + c) * Q + k0 + kl];
     }
 
-    // per-velocity constants
-    int kk[V], ii[V], jj[V], zz[V];
-    T px[V], py[V], pz[V], wk[V];
+    // ---- 2. meanwhile: per-cell equilibrium factors from the cell records
+    if (STAGE > 0) {
+        const T* R = static_cast<const T*>(I.rec);
+        for (int e = tid; e < zn * G; e += kThreads) {
+            const int c = e / G, r = e - c * G;
+            const T* rc = R + (size_t)(z0 + c) * kRecStride;
+            T g = 0;
+            if (r < Qx) {
+                const T* h = static_cast<const T*>(I.Hx) + r * (I.Nx + 1);
+                for (int l = 0; l <= I.Nx; ++l) g += rc[R_AX + l] * h[l];
+                g *= rc[R_N];
+            } else if (r < Qx + Qy) {
+                const T* h = static_cast<const T*>(I.Hy) + (r - Qx) * (I.Ny + 1);
+                for (int l = 0; l <= I.Ny; ++l) g += rc[R_AY + l] * h[l];
+            } else {
+                const int zm = zm_lo + r - Qx - Qy, sg = zm >= Qz, m = zm - sg * Qz;
+                const T* h = static_cast<const T*>(I.Pz) + m * (I.Nzq + 1);
+                const T* b = rc + (sg ? R_BM : R_BP);
+                for (int l = 0; l <= I.Nzq; ++l) g += b[l] * h[l];
+            }
+            gsm[e] = g;
+        }
+        for (int e = tid; e < zn * kRecHead; e += kThreads) {
+            const int c = e / kRecHead, r = e - c * kRecHead;
+            scs[e] = r == kIdz ? ld<T>(I.inv_dz, z0 + c) : R[(size_t)(z0 + c) * kRecStride + r];
+        }
+    }
+
+    // per-velocity constants: p, and w * psi(p) for the 13 raw moments
+    int ii[V], jj[V], zz[V], kl[V];
+    T px[V], py[V], pz[V];
+    A wpsi[V][kNMom];
     bool up[V], ok[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const int k = k0 + threadIdx.x + v * kThreads;
-        ok[v] = k < kend;
-        const int kc = ok[v] ? k : kend - 1;
-        kk[v] = kc;
+        kl[v] = tid + v * kThreads;
+        ok[v] = kl[v] < kn;
+        const int kc = ok[v] ? k0 + kl[v] : kend - 1;
         jj[v] = kc % Qy;
         ii[v] = (kc / Qy) % Qx;
         zz[v] = kc / QxQy;
@@ -147,277 +321,258 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
         const T x = ld<T>(I.xi, m);
         pz[v] = sg ? -x : x;
         up[v] = !sg;
-        wk[v] = ld<T>(I.wx, ii[v]) * ld<T>(I.wy, jj[v]) * ld<T>(I.wz, m);
+        const A w = ok[v] ? A(ld<T>(I.wx, ii[v]) * ld<T>(I.wy, jj[v]) * ld<T>(I.wz, m)) : A(0);
+        const A X = px[v], Y = py[v], Z = pz[v], p2 = X * X + Y * Y + Z * Z;
+        wpsi[v][0] = w;
+        wpsi[v][1] = w * X; wpsi[v][2] = w * Y; wpsi[v][3] = w * Z;
+        wpsi[v][4] = w * X * X; wpsi[v][5] = w * Y * Y; wpsi[v][6] = w * Z * Z;
+        wpsi[v][7] = w * X * Y; wpsi[v][8] = w * X * Z; wpsi[v][9] = w * Y * Z;
+        wpsi[v][10] = w * p2 * X; wpsi[v][11] = w * p2 * Y; wpsi[v][12] = w * p2 * Z;
     }
 
-    // ghost values next to the walls (only needed if the window reaches them)
-    T gb[V][3], gt[V][3];
-    const bool near_bot = z0 < 3, near_top = z0 + zn + 3 > Nz;
+    // ---- 3. wait for the copies (bounded); a CTA whose copies never land flags
+    //         the instance and leaves once they are no longer in flight
+    int late = 0;
+    if (I.bulk) {
+        uint32_t spins = 0;
+        while (!mbar_try_wait(&bar, 0)) {
+            if (++spins > kSpinLimit) { late = 1; break; }
+        }
+    }
+    if (__syncthreads_or(late)) {
+        if (tid == 0) atomicOr(I.status, 2);
+        uint32_t spins = 0;
+        while (!mbar_try_wait(&bar, 0) && ++spins < kSpinLimit) {
+        }
+        return;
+    }
+
+    // ---- 4. ghost rows (each thread fills only its own columns)
+    const int rbase = 3 - z0;  // smem row of cell s is s + rbase
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const size_t k = kk[v];
-        if (near_bot) {
-            if (up[v]) {  // incoming at the bottom wall
+        T* col = Fs + kl[v];
+        if (z0 < 3) {
+            if (up[v]) {  // incoming at the bottom wall: n_w times the wall equilibrium
                 const T g = T(I.nw[0]) * ld<T>(I.gwx_bot, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
-                gb[v][0] = gb[v][1] = gb[v][2] = g;
-            } else {      // outgoing: quadratic extrapolation of the Appendix
-                const T f1 = Fin[k], f2 = Fin[(size_t)Q + k], f3 = Fin[2 * (size_t)Q + k];
+                for (int s = -3; s <= -1; ++s)
+                    if (s + rbase >= 0) col[(size_t)(s + rbase) * KC] = g;
+            } else {      // outgoing: quadratic extrapolation (Appendix)
+                const T f1 = col[(size_t)(0 + rbase) * KC], f2 = col[(size_t)(1 + rbase) * KC],
+                        f3 = col[(size_t)(2 + rbase) * KC];
                 const T g0 = T(I.ext_bot[0][0]) * f1 + T(I.ext_bot[0][1]) * f2 + T(I.ext_bot[0][2]) * f3;
                 const T g1 = T(I.ext_bot[1][0]) * g0 + T(I.ext_bot[1][1]) * f1 + T(I.ext_bot[1][2]) * f2;
-                gb[v][0] = g0; gb[v][1] = g1; gb[v][2] = g1;  // cell -2 is never read for p_z < 0
+                if (-1 + rbase >= 0) col[(size_t)(-1 + rbase) * KC] = g0;
+                if (-2 + rbase >= 0) col[(size_t)(-2 + rbase) * KC] = g1;
+                if (-3 + rbase >= 0) col[(size_t)(-3 + rbase) * KC] = g1;  // never read for p_z < 0
             }
         }
-        if (near_top) {
+        if (z0 + zn + 3 > Nz) {
+            const int smax = z0 + zn + 2;
             if (!up[v]) {
                 const T g = T(I.nw[1]) * ld<T>(I.gwx_top, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
-                gt[v][0] = gt[v][1] = gt[v][2] = g;
+                for (int s = Nz; s <= Nz + 2; ++s)
+                    if (s <= smax) col[(size_t)(s + rbase) * KC] = g;
             } else {
-                const T f1 = Fin[(size_t)(Nz - 1) * Q + k], f2 = Fin[(size_t)(Nz - 2) * Q + k],
-                        f3 = Fin[(size_t)(Nz - 3) * Q + k];
+                const T f1 = col[(size_t)(Nz - 1 + rbase) * KC], f2 = col[(size_t)(Nz - 2 + rbase) * KC],
+                        f3 = col[(size_t)(Nz - 3 + rbase) * KC];
                 const T g0 = T(I.ext_top[0][0]) * f1 + T(I.ext_top[0][1]) * f2 + T(I.ext_top[0][2]) * f3;
                 const T g1 = T(I.ext_top[1][0]) * g0 + T(I.ext_top[1][1]) * f1 + T(I.ext_top[1][2]) * f2;
-                gt[v][0] = g0; gt[v][1] = g1; gt[v][2] = g1;  // cell Nz+3 is never read for p_z > 0
+                if (Nz <= smax) col[(size_t)(Nz + rbase) * KC] = g0;
+                if (Nz + 1 <= smax) col[(size_t)(Nz + 1 + rbase) * KC] = g1;
+                if (Nz + 2 <= smax) col[(size_t)(Nz + 2 + rbase) * KC] = g1;  // never read for p_z > 0
             }
         }
     }
 
-    auto fetch = [&](int v, int s) -> T {  // F at cell s (0-based; ghosts outside 0..Nz-1)
-        if (s < 0) return gb[v][-1 - s];
-        if (s >= Nz) return gt[v][s - Nz];
-        return Fin[(size_t)s * Q + kk[v]];
-    };
-
-    // window F(s-3 .. s+2) and the flux through s - 1/2
+    // ---- 5. march up the z-range
     T w[V][6], flm[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
 #pragma unroll
-        for (int d = 0; d < 6; ++d) w[v][d] = fetch(v, z0 - 3 + d);
+        for (int d = 0; d < 6; ++d) w[v][d] = Fs[(size_t)d * KC + kl[v]];
         flm[v] = pz[v] * (up[v] ? weno5<T>(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4])
                                 : weno5<T>(w[v][5], w[v][4], w[v][3], w[v][2], w[v][1]));
     }
-
-    T first[V][3], last[V][3];  // outputs of the first / last three cells (wall fluxes)
     const T dt = T(I.dt);
     for (int c = 0; c < zn; ++c) {
         const int s = z0 + c;
-        T n_ = 0, ux = 0, uy = 0, uz = 0, i5T = 0, qx = 0, qy = 0, qz = 0, itau = 0, cS = 0, idz = 0;
-        const T* rc = recs + (size_t)c * RS;
+        const T* sc = scs + c * kRecHead;
+        const T* gc = gsm + c * G;
+        T ux = 0, uy = 0, uz = 0, i5T = 0, qx = 0, qy = 0, qz = 0, itau = 0, cS = 0, idz = 0;
         if (STAGE > 0) {
-            ux = rc[R_UX]; uy = rc[R_UY]; uz = rc[R_UZ];
-            qx = rc[R_QX]; qy = rc[R_QY]; qz = rc[R_QZ];
-            itau = rc[R_ITAU]; cS = rc[R_CS]; i5T = rc[R_I5T];
-            idz = ld<T>(I.inv_dz, s);
-            (void)n_;
+            ux = sc[R_UX]; uy = sc[R_UY]; uz = sc[R_UZ];
+            qx = sc[R_QX]; qy = sc[R_QY]; qz = sc[R_QZ];
+            itau = sc[R_ITAU]; cS = sc[R_CS]; i5T = sc[R_I5T]; idz = sc[kIdz];
         }
-        A acc[kNMom];
+        A acc[16];
 #pragma unroll
-        for (int a = 0; a < kNMom; ++a) acc[a] = A(0);
+        for (int a = 0; a < 16; ++a) acc[a] = A(0);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const T wn = fetch(v, s + 3);
+            const T wn = Fs[(size_t)(c + 6) * KC + kl[v]];
             T out = w[v][3];
             if (STAGE > 0) {
-                const T flp = pz[v] * (up[v] ? weno5<T>(w[v][1], w[v][2], w[v][3], w[v][4], w[v][5])
-                                             : weno5<T>(wn, w[v][5], w[v][4], w[v][3], w[v][2]));
+                // upwind-ordered stencil of the interface s + 1/2 (mirror image for p_z < 0)
+                const bool u = up[v];
+                const T a0 = u ? w[v][1] : wn, a1 = u ? w[v][2] : w[v][5], a2 = u ? w[v][3] : w[v][4];
+                const T a3 = u ? w[v][4] : w[v][3], a4 = u ? w[v][5] : w[v][2];
+                const T flp = pz[v] * weno5<T>(a0, a1, a2, a3, a4);
                 const T f = w[v][3];
                 // Shakhov target n Gx Gy Gz (1 + S), S = cS (xi^2/(5T) - 1) xi.q
                 const T ex = px[v] - ux, ey = py[v] - uy, ez = pz[v] - uz;
                 const T xi2 = ex * ex + ey * ey + ez * ez;
                 const T xq = ex * qx + ey * qy + ez * qz;
                 const T S = cS * (xi2 * i5T - T(1)) * xq;
-                const T geq = rc[kRecHead + ii[v]] * rc[kRecHead + Qx + jj[v]] *
-                              rc[kRecHead + Qx + Qy + zz[v] - zm_lo];
+                const T geq = gc[ii[v]] * gc[Qx + jj[v]] * gc[Qx + Qy + zz[v] - zm_lo];
                 const T Lv = -(flp - flm[v]) * idz - (f - geq * (T(1) + S)) * itau;
                 const T f1 = f + dt * Lv;
                 if (STAGE == 1) out = f1;
-                else if (STAGE == 2) out = T(0.75) * F0[(size_t)s * Q + kk[v]] + T(0.25) * f1;
-                else out = T(1.0 / 3.0) * F0[(size_t)s * Q + kk[v]] + T(2.0 / 3.0) * f1;
-                if (ok[v]) Fout[(size_t)s * Q + kk[v]] = out;
+                else if (STAGE == 2) out = T(0.75) * F0s[(size_t)c * KC + kl[v]] + T(0.25) * f1;
+                else out = T(1.0 / 3.0) * F0s[(size_t)c * KC + kl[v]] + T(2.0 / 3.0) * f1;
+                if (ok[v]) Fout[(size_t)s * Q + k0 + kl[v]] = out;
                 flm[v] = flp;
             }
-            if (c < 3) first[v][c] = out;
-            last[v][0] = last[v][1]; last[v][1] = last[v][2]; last[v][2] = out;
 #pragma unroll
             for (int d = 0; d < 5; ++d) w[v][d] = w[v][d + 1];
             w[v][5] = wn;
-            // raw moments of the output: sum w f psi(p)
-            if (ok[v]) {
-                const A g = A(wk[v]) * A(out);
-                const A X = A(px[v]), Y = A(py[v]), Z = A(pz[v]);
-                const A p2 = X * X + Y * Y + Z * Z;
-                acc[0] += g;
-                acc[1] += g * X; acc[2] += g * Y; acc[3] += g * Z;
-                acc[4] += g * X * X; acc[5] += g * Y * Y; acc[6] += g * Z * Z;
-                acc[7] += g * X * Y; acc[8] += g * X * Z; acc[9] += g * Y * Z;
-                acc[10] += g * p2 * X; acc[11] += g * p2 * Y; acc[12] += g * p2 * Z;
-            }
-        }
+            const A o = ok[v] ? A(out) : A(0);  // columns past the chunk hold no data
 #pragma unroll
-        for (int a = 0; a < kNMom; ++a) {
-            A x = acc[a];
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) red[((size_t)c * nwarp + warp) * kNMom + a] = double(x);
+            for (int a = 0; a < kNMom; ++a) acc[a] += o * wpsi[v][a];
         }
+        const A tot = reduce_scatter16<A>(acc, lane);
+        const int m = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+        if ((lane & 1) == 0) red[((size_t)c * (kThreads / 32) + warp) * 16 + m] = tot;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < zn * kNMom; e += kThreads) {
+    for (int e = tid; e < zn * kNMom; e += kThreads) {
         const int c = e / kNMom, a = e - c * kNMom;
-        double s = 0.0;
-        for (int q = 0; q < nwarp; ++q) s += red[((size_t)c * nwarp + q) * kNMom + a];
-        I.partial[((size_t)tile.chunk * Nz + z0 + c) * kNMom + a] = s;
+        A s = A(0);
+#pragma unroll
+        for (int q = 0; q < kThreads / 32; ++q) s += red[((size_t)c * (kThreads / 32) + q) * 16 + a];
+        I.partial[((size_t)tile.chunk * kNMom + a) * Nz + z0 + c] = double(s);
     }
 
-    // outgoing WENO flux of F_out through the wall interfaces (for n_w)
+    // ---- 6. outgoing WENO flux of F_out through the wall interfaces (for n_w).
+    // Each thread re-reads the outputs it wrote itself (STAGE 0: its input rows).
+    auto outval = [&](int v, int cell) -> T {
+        return STAGE == 0 ? Fs[(size_t)(cell + rbase) * KC + kl[v]] : Fout[(size_t)cell * Q + k0 + kl[v]];
+    };
     if (z0 == 0) {  // bottom: p_z < 0 leaves through s = -1/2
         double fl = 0.0;
 #pragma unroll
         for (int v = 0; v < V; ++v)
             if (ok[v] && !up[v]) {
-                const T f1 = first[v][0], f2 = first[v][1], f3 = first[v][2];
+                const T f1 = outval(v, 0), f2 = outval(v, 1), f3 = outval(v, 2);
                 const T g0 = T(I.ext_bot[0][0]) * f1 + T(I.ext_bot[0][1]) * f2 + T(I.ext_bot[0][2]) * f3;
                 const T g1 = T(I.ext_bot[1][0]) * g0 + T(I.ext_bot[1][1]) * f1 + T(I.ext_bot[1][2]) * f2;
-                fl += double(wk[v]) * double(pz[v] * weno5<T>(f3, f2, f1, g0, g1));
+                fl += double(wpsi[v][0]) * double(pz[v] * weno5<T>(f3, f2, f1, g0, g1));
             }
         fl = block_sum(fl, wall_red);
-        if (threadIdx.x == 0) I.flux_part[tile.chunk * 2 + 0] = fl;
+        if (tid == 0) I.flux_part[tile.chunk * 2 + 0] = fl;
     }
     if (z0 + zn == Nz) {  // top: p_z > 0 leaves through s = Nz - 1/2
         double fl = 0.0;
 #pragma unroll
         for (int v = 0; v < V; ++v)
             if (ok[v] && up[v]) {
-                const T f1 = last[v][2], f2 = last[v][1], f3 = last[v][0];
+                const T f1 = outval(v, Nz - 1), f2 = outval(v, Nz - 2), f3 = outval(v, Nz - 3);
                 const T g0 = T(I.ext_top[0][0]) * f1 + T(I.ext_top[0][1]) * f2 + T(I.ext_top[0][2]) * f3;
                 const T g1 = T(I.ext_top[1][0]) * g0 + T(I.ext_top[1][1]) * f1 + T(I.ext_top[1][2]) * f2;
-                fl += double(wk[v]) * double(pz[v] * weno5<T>(f3, f2, f1, g0, g1));
+                fl += double(wpsi[v][0]) * double(pz[v] * weno5<T>(f3, f2, f1, g0, g1));
             }
         fl = block_sum(fl, wall_red);
-        if (threadIdx.x == 0) I.flux_part[tile.chunk * 2 + 1] = fl;
+        if (tid == 0) I.flux_part[tile.chunk * 2 + 1] = fl;
     }
 }
 
 // ----------------------------------------------------------------------------
-// Cell record: scalars and the per-axis factors of the truncated Hermite
-// equilibrium (Sec. III, Eqs. fyz, Fmn_def) of a macroscopic state.  Called by
-// the whole CTA; thread 0 has set sc[] (n, u, T, q, 1/tau, ...) beforehand.
+// Cell record from a macroscopic state: scalars and the coefficients a_l, b_l
+// of the truncated Hermite equilibrium (Sec. III, Eqs. fyz, Fmn_def), FP64.
+// Returns false for a non-finite or non-positive state (a neutral state is
+// written instead).
 // ----------------------------------------------------------------------------
 template <typename T>
-__device__ void write_record(const InstDev& I, int cell, const double* sc, double (*coef)[kMaxN + 1])
-{
-    T* rec = static_cast<T*>(I.rec) + (size_t)cell * I.rec_stride;
-    const int t = threadIdx.x;
-    if (t < kRecHead) rec[t] = T(sc[t]);
-    const int Qx = I.Qx, Qy = I.Qy, Qz = I.Qz;
-    for (int e = t; e < Qx + Qy + 2 * Qz; e += blockDim.x) {
-        double g = 0.0;
-        if (e < Qx) {
-            for (int l = 0; l <= I.Nx; ++l) g += coef[0][l] * I.Hx[e * (I.Nx + 1) + l];
-            g *= sc[R_N];
-        } else if (e < Qx + Qy) {
-            const int j = e - Qx;
-            for (int l = 0; l <= I.Ny; ++l) g += coef[1][l] * I.Hy[j * (I.Ny + 1) + l];
-        } else {
-            const int zm = e - Qx - Qy, sg = zm >= Qz, m = zm - sg * Qz;
-            for (int l = 0; l <= I.Nzq; ++l) g += coef[2 + sg][l] * I.Pz[m * (I.Nzq + 1) + l];
-        }
-        rec[kRecHead + e] = T(g);
-    }
-}
-
-// thread 0: scalars and expansion coefficients of (n, u, T, q); returns false
-// for a non-finite or non-positive state (then a neutral state is used)
-__device__ bool macro_to_coeffs(const InstDev& I, double n, const double* u, double T_, const double* q,
-                                double* sc, double (*coef)[kMaxN + 1])
+__device__ bool write_record(const InstDev& I, int cell, double n, const double* u, double T_, const double* q)
 {
     bool bad = !(n > 0.0) || !(T_ > 0.0) || !isfinite(n) || !isfinite(T_);
     for (int a = 0; a < 3; ++a) bad |= !isfinite(u[a]) || !isfinite(q[a]);
     const double nn = bad ? 1.0 : n, Tc = bad ? 1.0 : T_;
     const double u0 = bad ? 0.0 : u[0], u1 = bad ? 0.0 : u[1], u2 = bad ? 0.0 : u[2];
-    full_coeffs(u0, Tc, I.Nx, coef[0]);
-    full_coeffs(u1, Tc, I.Ny, coef[1]);
-    half_coeffs(u2, Tc, I.Nzq, I.alpha, I.beta, coef[2]);
-    half_coeffs(-u2, Tc, I.Nzq, I.alpha, I.beta, coef[3]);
+    T* rec = static_cast<T*>(I.rec) + (size_t)cell * kRecStride;
+    double c[kMaxN + 1];
+    full_coeffs(u0, Tc, I.Nx, c);
+    for (int l = 0; l <= kMaxN; ++l) rec[R_AX + l] = l <= I.Nx ? T(c[l]) : T(0);
+    full_coeffs(u1, Tc, I.Ny, c);
+    for (int l = 0; l <= kMaxN; ++l) rec[R_AY + l] = l <= I.Ny ? T(c[l]) : T(0);
+    half_coeffs(u2, Tc, I.Nzq, I.alpha, I.beta, c);
+    for (int l = 0; l <= kMaxN; ++l) rec[R_BP + l] = l <= I.Nzq ? T(c[l]) : T(0);
+    half_coeffs(-u2, Tc, I.Nzq, I.alpha, I.beta, c);
+    for (int l = 0; l <= kMaxN; ++l) rec[R_BM + l] = l <= I.Nzq ? T(c[l]) : T(0);
     const double tau = relax_time(I.visc_law, I.Kn, I.visc_param, nn, Tc);
-    sc[R_N] = nn; sc[R_UX] = u0; sc[R_UY] = u1; sc[R_UZ] = u2; sc[R_T] = Tc;
-    sc[R_QX] = bad ? 0.0 : q[0]; sc[R_QY] = bad ? 0.0 : q[1]; sc[R_QZ] = bad ? 0.0 : q[2];
-    sc[R_ITAU] = 1.0 / tau;
-    sc[R_CS] = (1.0 - I.Pr) / (nn * Tc * Tc);
-    sc[R_I5T] = 1.0 / (5.0 * Tc);
-    sc[11] = 0.0;
+    rec[R_N] = T(nn); rec[R_UX] = T(u0); rec[R_UY] = T(u1); rec[R_UZ] = T(u2); rec[R_T] = T(Tc);
+    rec[R_QX] = T(bad ? 0.0 : q[0]); rec[R_QY] = T(bad ? 0.0 : q[1]); rec[R_QZ] = T(bad ? 0.0 : q[2]);
+    rec[R_ITAU] = T(1.0 / tau);
+    rec[R_CS] = T((1.0 - I.Pr) / (nn * Tc * Tc));
+    rec[R_I5T] = T(1.0 / (5.0 * Tc));
+    rec[11] = T(0);
     return !bad;
 }
 
 // ----------------------------------------------------------------------------
-// finalize_cells<T>: moments -> macroscopic state -> cell record
+// finalize_cells<T>: one thread per cell; moments -> macroscopic -> record
 // ----------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128) finalize_cells(const InstDev* __restrict__ insts)
+__global__ void __launch_bounds__(64) finalize_cells(const InstDev* __restrict__ insts)
 {
     const InstDev& I = insts[blockIdx.y];
-    const int cell = blockIdx.x, Nz = I.Nz;
+    const int Nz = I.Nz, cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= Nz || *I.active == 0) return;
-    __shared__ double mom[kNMom];
-    __shared__ double coef[4][kMaxN + 1];
-    __shared__ double sc[kRecHead];
-    const int t = threadIdx.x;
-    if (t < kNMom) {
-        double s = 0.0;
-        for (int c = 0; c < I.nchunks; ++c) s += I.partial[((size_t)c * Nz + cell) * kNMom + t];
-        mom[t] = s;
+    double mom[kNMom];
+    for (int a = 0; a < kNMom; ++a) mom[a] = 0.0;
+    for (int c = 0; c < I.nchunks; ++c)
+#pragma unroll
+        for (int a = 0; a < kNMom; ++a) mom[a] += I.partial[((size_t)c * kNMom + a) * Nz + cell];
+    const double n = mom[0];
+    const double u[3] = {mom[1] / n, mom[2] / n, mom[3] / n};
+    // central second moments P_ab = sum p_a p_b f - n u_a u_b
+    const double Pxx = mom[4] - n * u[0] * u[0], Pyy = mom[5] - n * u[1] * u[1];
+    const double Pzz = mom[6] - n * u[2] * u[2], Pxy = mom[7] - n * u[0] * u[1];
+    const double Pxz = mom[8] - n * u[0] * u[2], Pyz = mom[9] - n * u[1] * u[2];
+    const double T_ = (Pxx + Pyy + Pzz) / (3.0 * n);
+    // q_a = 1/2 sum |xi|^2 xi_a f with xi = p - u, expanded in raw moments
+    const double M2[3][3] = {{mom[4], mom[7], mom[8]}, {mom[7], mom[5], mom[9]}, {mom[8], mom[9], mom[6]}};
+    const double tr = mom[4] + mom[5] + mom[6];
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double um = u[0] * mom[1] + u[1] * mom[2] + u[2] * mom[3];
+    double q[3];
+    for (int a = 0; a < 3; ++a) {
+        const double uM2 = u[0] * M2[0][a] + u[1] * M2[1][a] + u[2] * M2[2][a];
+        q[a] = 0.5 * (mom[10 + a] - u[a] * tr - 2.0 * uM2 + 2.0 * u[a] * um + uu * mom[1 + a] - uu * u[a] * n);
     }
-    __syncthreads();
-    if (t == 0) {
-        const double n = mom[0];
-        const double u[3] = {mom[1] / n, mom[2] / n, mom[3] / n};
-        // central second moments P_ab = sum p_a p_b f - n u_a u_b
-        const double Pxx = mom[4] - n * u[0] * u[0], Pyy = mom[5] - n * u[1] * u[1];
-        const double Pzz = mom[6] - n * u[2] * u[2], Pxy = mom[7] - n * u[0] * u[1];
-        const double Pxz = mom[8] - n * u[0] * u[2], Pyz = mom[9] - n * u[1] * u[2];
-        const double T_ = (Pxx + Pyy + Pzz) / (3.0 * n);
-        // q_a = 1/2 sum |xi|^2 xi_a f with xi = p - u, expanded in raw moments
-        const double M2[3][3] = {{mom[4], mom[7], mom[8]}, {mom[7], mom[5], mom[9]}, {mom[8], mom[9], mom[6]}};
-        const double tr = mom[4] + mom[5] + mom[6];
-        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        const double um = u[0] * mom[1] + u[1] * mom[2] + u[2] * mom[3];
-        double q[3];
-        for (int a = 0; a < 3; ++a) {
-            const double uM2 = u[0] * M2[0][a] + u[1] * M2[1][a] + u[2] * M2[2][a];
-            q[a] = 0.5 * (mom[10 + a] - u[a] * tr - 2.0 * uM2 + 2.0 * u[a] * um + uu * mom[1 + a] -
-                          uu * u[a] * n);
-        }
-        const double vals[14] = {n, u[0], u[1], u[2], T_, q[0], q[1], q[2], Pxx, Pyy, Pzz, Pxy, Pxz, Pyz};
-        bool bad = false;
-        for (int a = 0; a < 14; ++a) {
-            I.prof[(size_t)a * Nz + cell] = vals[a];
-            bad |= !isfinite(vals[a]);
-        }
-        I.Wnew[cell] = n;
-        I.Wnew[Nz + cell] = u[0];
-        I.Wnew[2 * Nz + cell] = T_;
-        bad |= !macro_to_coeffs(I, n, u, T_, q, sc, coef);
-        if (bad) atomicOr(I.status, 1);
+    const double vals[14] = {n, u[0], u[1], u[2], T_, q[0], q[1], q[2], Pxx, Pyy, Pzz, Pxy, Pxz, Pyz};
+    bool bad = false;
+    for (int a = 0; a < 14; ++a) {
+        I.prof[(size_t)a * Nz + cell] = vals[a];
+        bad |= !isfinite(vals[a]);
     }
-    __syncthreads();
-    write_record<T>(I, cell, sc, coef);
+    I.Wnew[cell] = n;
+    I.Wnew[Nz + cell] = u[0];
+    I.Wnew[2 * Nz + cell] = T_;
+    bad |= !write_record<T>(I, cell, n, u, T_, q);
+    if (bad) atomicOr(I.status, 1);
 }
 
 // records from given macroscopic profiles macro[8][Nz] = n, ux, uy, uz, T, qx, qy, qz
 template <typename T>
-__global__ void __launch_bounds__(128) records_from_macro(const InstDev* __restrict__ insts, int inst,
-                                                         const double* __restrict__ macro)
+__global__ void records_from_macro(const InstDev* __restrict__ insts, int inst, const double* __restrict__ macro)
 {
     const InstDev& I = insts[inst];
-    const int cell = blockIdx.x, Nz = I.Nz;
-    __shared__ double coef[4][kMaxN + 1];
-    __shared__ double sc[kRecHead];
-    if (threadIdx.x == 0) {
-        const double u[3] = {macro[Nz + cell], macro[2 * Nz + cell], macro[3 * Nz + cell]};
-        const double q[3] = {macro[5 * Nz + cell], macro[6 * Nz + cell], macro[7 * Nz + cell]};
-        if (!macro_to_coeffs(I, macro[cell], u, macro[4 * Nz + cell], q, sc, coef)) atomicOr(I.status, 1);
-    }
-    __syncthreads();
-    write_record<T>(I, cell, sc, coef);
+    const int Nz = I.Nz, cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= Nz) return;
+    const double u[3] = {macro[Nz + cell], macro[2 * Nz + cell], macro[3 * Nz + cell]};
+    const double q[3] = {macro[5 * Nz + cell], macro[6 * Nz + cell], macro[7 * Nz + cell]};
+    if (!write_record<T>(I, cell, macro[cell], u, macro[4 * Nz + cell], q)) atomicOr(I.status, 1);
 }
 
 // ----------------------------------------------------------------------------
@@ -467,26 +622,36 @@ __global__ void __launch_bounds__(256) finalize_inst(const InstDev* __restrict__
     }
 }
 
-// ---- seed a cell from macroscopic values: n Gx Gy Gz (1 + S) --------------
+// ---- seed a cell from its record: f_k / w_k = n Gx Gy Gz (1 + S) ----------
 template <typename T>
-__global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ insts, int inst, int fbuf)
+__global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ insts, int inst)
 {
     const InstDev& I = insts[inst];
     const int cell = blockIdx.x;
-    const T* rc = static_cast<const T*>(I.rec) + (size_t)cell * I.rec_stride;
-    T* F = static_cast<T*>(fbuf == 0 ? I.F0 : fbuf == 1 ? I.F1 : I.F2) + (size_t)cell * I.Q;
+    const T* rc = static_cast<const T*>(I.rec) + (size_t)cell * kRecStride;
+    T* F = static_cast<T*>(I.F0) + (size_t)cell * I.Q;
     for (int k = threadIdx.x; k < I.Q; k += blockDim.x) {
         const int j = k % I.Qy, i = (k / I.Qy) % I.Qx, zm = k / I.QxQy;
         const int sg = zm >= I.Qz, m = zm - sg * I.Qz;
+        T gx = 0, gy = 0, gz = 0;
+        for (int l = 0; l <= I.Nx; ++l) gx += rc[R_AX + l] * ld<T>(I.Hx, i * (I.Nx + 1) + l);
+        for (int l = 0; l <= I.Ny; ++l) gy += rc[R_AY + l] * ld<T>(I.Hy, j * (I.Ny + 1) + l);
+        for (int l = 0; l <= I.Nzq; ++l) gz += rc[(sg ? R_BM : R_BP) + l] * ld<T>(I.Pz, m * (I.Nzq + 1) + l);
         const T x = ld<T>(I.xi, m);
         const T ex = ld<T>(I.px, i) - rc[R_UX], ey = ld<T>(I.py, j) - rc[R_UY], ez = (sg ? -x : x) - rc[R_UZ];
         const T S = rc[R_CS] * ((ex * ex + ey * ey + ez * ez) * rc[R_I5T] - T(1)) *
                     (ex * rc[R_QX] + ey * rc[R_QY] + ez * rc[R_QZ]);
-        F[k] = rc[kRecHead + i] * rc[kRecHead + I.Qx + j] * rc[kRecHead + I.Qx + I.Qy + zm] * (T(1) + S);
+        F[k] = rc[R_N] * gx * gy * gz * (T(1) + S);
     }
 }
 
 // ---- host launchers ---------------------------------------------------------
+size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage)
+{
+    const int KC = kThreads * V;
+    return stage_smem(zn, KC, G, fp32 ? 4 : 8, fp32 ? 4 : 8, stage >= 2).total;
+}
+
 template <typename T, int V, int STAGE>
 static cudaError_t launch_stage_t(const InstDev* d_inst, const Tile* d_tiles, int ntiles, size_t smem,
                                   cudaStream_t st)
@@ -526,9 +691,9 @@ cudaError_t launch_stage(int fp32, int V, int stage, const InstDev* d_inst, cons
 cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int ninst, int maxNz,
                             cudaStream_t st)
 {
-    dim3 g(maxNz, ninst);
-    if (fp32) finalize_cells<float><<<g, 128, 0, st>>>(d_inst);
-    else finalize_cells<double><<<g, 128, 0, st>>>(d_inst);
+    dim3 g((maxNz + 63) / 64, ninst);
+    if (fp32) finalize_cells<float><<<g, 64, 0, st>>>(d_inst);
+    else finalize_cells<double><<<g, 64, 0, st>>>(d_inst);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     finalize_inst<<<ninst, 256, 0, st>>>(d_inst, stage);
@@ -538,12 +703,13 @@ cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int nins
 cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,
                         cudaStream_t st)
 {
-    if (fp32) records_from_macro<float><<<Nz, 128, 0, st>>>(d_inst, inst, d_macro);
-    else records_from_macro<double><<<Nz, 128, 0, st>>>(d_inst, inst, d_macro);
+    const int g = (Nz + 63) / 64;
+    if (fp32) records_from_macro<float><<<g, 64, 0, st>>>(d_inst, inst, d_macro);
+    else records_from_macro<double><<<g, 64, 0, st>>>(d_inst, inst, d_macro);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (fp32) seed_cells<float><<<Nz, 128, 0, st>>>(d_inst, inst, 0);
-    else seed_cells<double><<<Nz, 128, 0, st>>>(d_inst, inst, 0);
+    if (fp32) seed_cells<float><<<Nz, 128, 0, st>>>(d_inst, inst);
+    else seed_cells<double><<<Nz, 128, 0, st>>>(d_inst, inst);
     return cudaGetLastError();
 }
 

@@ -21,22 +21,26 @@ constexpr int kMaxZT = 64;      // cells of a z-tile
 
 enum { QUAD_FULL = 0, QUAD_HALF = 1 };
 
-// Cell record head (storage type): n, ux, uy, uz, T, qx, qy, qz, 1/tau,
-// (1 - Pr)/(n T^2), 1/(5T), unused; then n*Gx[Qx], Gy[Qy], Gz[2 Qz].
+// Cell record (storage type T): n, ux, uy, uz, T, qx, qy, qz, 1/tau,
+// (1 - Pr)/(n T^2), 1/(5T), unused; then the expansion coefficients of the
+// truncated equilibrium: a_l (x), a_l (y), b_l (z, p_z > 0), b_l (z, p_z < 0),
+// kMaxN + 1 slots each.
 enum { R_N = 0, R_UX, R_UY, R_UZ, R_T, R_QX, R_QY, R_QZ, R_ITAU, R_CS, R_I5T };
+constexpr int R_AX = kRecHead, R_AY = R_AX + kMaxN + 1, R_BP = R_AY + kMaxN + 1, R_BM = R_BP + kMaxN + 1;
+constexpr int kRecStride = R_BM + kMaxN + 1;
 
 // Everything a kernel needs to know about one instance (lives in device memory).
 struct InstDev {
     int Nz, Qx, Qy, Qz, Q, QxQy;
     int Nx, Ny, Nzq;              // per-axis expansion orders
-    int nchunks, rec_stride;
+    int nchunks, bulk;            // bulk: rows are 16-byte aligned, stage them with TMA bulk copies
     int visc_law;
     double Kn, visc_param, Pr, dt, tol;
     double Dtop, Dbot;            // sum over incoming velocities of w p_z Gw (n_w = 1)
     double ext_top[2][3];         // ghost Nz+1 <- (Nz, Nz-1, Nz-2); Nz+2 <- (Nz+1, Nz, Nz-1)
     double ext_bot[2][3];         // ghost 0 <- (1, 2, 3); ghost -1 <- (0, 1, 2)
-    // FP64 tables
-    const double *Hx, *Hy, *Pz;   // [Q_a][N_a + 1] basis values
+    // tables
+    const void *Hx, *Hy, *Pz;     // storage type, [Q_a][N_a + 1] basis values He_l/l!, pi_l/h_l
     const double *alpha, *beta;   // half-range recurrence, [kMaxN + 2]
     // storage-typed tables (float or double)
     const void *px, *py, *xi, *wx, *wy, *wz;
@@ -44,8 +48,8 @@ struct InstDev {
     const void *inv_dz;                          // [Nz]
     // state and work
     void *F0, *F1, *F2;           // [Nz][Q] normalised populations f / w
-    void *rec;                    // [Nz][rec_stride]
-    double *partial;              // [nchunks][Nz][kNMom]
+    void *rec;                    // [Nz][kRecStride]
+    double *partial;              // [nchunks][kNMom][Nz]
     double *flux_part;            // [nchunks][2]: bottom, top outgoing flux
     double *nw;                   // [2]: bottom, top wall density
     double *prof;                 // [14][Nz]

@@ -55,7 +55,8 @@ class _Desc(C.Structure):
 EXPORTS = ("lbs_create", "lbs_batch_create", "lbs_destroy", "lbs_step", "lbs_run_to_steady",
            "lbs_moments", "lbs_profiles", "lbs_residual", "lbs_steps_taken", "lbs_info",
            "lbs_get_state", "lbs_set_state", "lbs_init_from_profiles", "lbs_quadrature",
-           "lbs_get_stream", "lbs_profile_steps", "lbs_moments_static", "lbs_last_error")
+           "lbs_get_stream", "lbs_profile_steps", "lbs_moments_static", "lbs_set_tiling",
+           "lbs_get_tiling", "lbs_last_error")
 
 
 def load(build_if_missing=True):
@@ -90,6 +91,9 @@ def load(build_if_missing=True):
         lib.lbs_get_stream.argtypes = [P, H]
         lib.lbs_profile_steps.argtypes = [P, C.c_long, D]
         lib.lbs_moments_static.argtypes = [P, C.c_int, P, P]
+        lib.lbs_set_tiling.argtypes = [P, C.c_int, C.c_int]
+        I = C.POINTER(C.c_int)
+        lib.lbs_get_tiling.argtypes = [P, I, I, I, L]
         lib.lbs_last_error.restype = C.c_char_p
         for name in EXPORTS:
             if name != "lbs_last_error":
@@ -196,6 +200,14 @@ class Solver:
 
     def step(self, nsteps=1):
         _check(self.lib.lbs_step(self.h, int(nsteps)))
+
+    def set_tiling(self, V, ZT):
+        _check(self.lib.lbs_set_tiling(self.h, int(V), int(ZT)))
+
+    def tiling(self):
+        v, z, n, sm = C.c_int(), C.c_int(), C.c_int(), C.c_long()
+        _check(self.lib.lbs_get_tiling(self.h, C.byref(v), C.byref(z), C.byref(n), C.byref(sm)))
+        return {"V": v.value, "ZT": z.value, "ctas": n.value, "smem": sm.value}
 
     def profile_steps(self, nsteps):
         """Event-timed steps: (stage-kernel ms, finalise-kernel ms, whole-step ms), summed."""

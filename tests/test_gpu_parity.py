@@ -54,10 +54,16 @@ def test_fp64_residual_sequence_matches_oracle():
     assert r[-1] > 0
 
 
-def test_fp32_profiles_match_oracle():
+# Q = 30: rows of 120 bytes are not 16-byte aligned, so the stage kernel takes its
+# plain-load path instead of TMA bulk copies
+UNALIGNED = dict(RAGGED, Qx=3, Qy=1, Qz=5, N_eq=2, Nz=19)
+
+
+@pytest.mark.parametrize("params", [RAGGED, UNALIGNED])
+def test_fp32_profiles_match_oracle(params):
     P = _lbs()
-    o = oracle_of(RAGGED, dt=None)
-    s = solver_of(RAGGED, o.dt, P.LBS_FP32)
+    o = oracle_of(params, dt=None)
+    s = solver_of(params, o.dt, P.LBS_FP32)
     o.step(30)
     s.step(30)
     errs = profile_errors(s.profiles(), o.profiles())
@@ -174,3 +180,29 @@ def test_c3_high_kn_fp32_free_molecular_bound():
     dz = np.diff(o.xf)
     assert abs(np.sum(p["n"] * dz) - 1.0) < 1e-6
     assert np.all(np.abs(p["Pxz"]) <= W.C3["u_w"] * math.sqrt(2 / math.pi) * 1.01)
+
+
+@pytest.mark.parametrize("V,ZT", [(1, 3), (2, 7), (4, 64)])
+def test_tiling_does_not_change_results(V, ZT):
+    """Every work decomposition of the stage kernel gives the oracle's state."""
+    P = _lbs()
+    o = oracle_of(RAGGED, dt=None)
+    s = solver_of(RAGGED, o.dt, P.LBS_FP64)
+    s.set_tiling(V, ZT)
+    t = s.tiling()
+    assert t["V"] == V and t["ZT"] == ZT
+    o.step(15)
+    s.step(15)
+    assert rel_err(gpu_f(s, o), o.f[3:3 + o.Nz]) < FP64_TOL
+
+
+def test_autotuner_picks_a_valid_tiling():
+    P = _lbs()
+    from paper_1702_01335_gb300.autotune import autotune
+    s = solver_of([W.C1] * 4, 0.004, P.LBS_FP32)
+    before = s.get_state(0)
+    r = autotune(s, candidates=((1, 8), (2, 16)), steps=2)
+    assert (r["V"], r["ZT"]) in ((1, 8), (2, 16))
+    assert s.tiling()["V"] == r["V"]
+    assert np.array_equal(s.get_state(0), before)  # tuning ran on a scratch solver
+    assert s.steps_taken() == 0

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from tests._pair import profile_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -36,11 +37,8 @@ def test_static_moments_match_profiles(params, precision, tol):
         with torch.cuda.stream(st):
             got = out.cpu().numpy()
         ref = s.profiles(0)
-        thermal = float(np.max(ref["n"] * ref["T"] ** 1.5))
-        for a, k in enumerate(PROFILE_NAMES):
-            scale = thermal if k.startswith("q") else max(np.abs(ref[k]).max(), 1e-3 * thermal)
-            err = np.abs(got[a] - ref[k]).max() / scale
-            assert err < tol, (call, k, err)
+        errs = profile_errors(dict(zip(PROFILE_NAMES, got)), ref)
+        assert max(errs.values()) < tol, (call, errs)
     s.close()
 
 
