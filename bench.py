@@ -35,7 +35,6 @@ import workloads as W  # noqa: E402
 
 BATCH = 256
 BYTES_PER_UPDATE = {"f32": 32, "f64": 64}   # algorithmic HBM bytes per update per RK-3 step
-KERNELS_PER_STEP = 9                        # 3 x (stage, finalize_cells, finalize_inst)
 
 
 def parse():
@@ -179,9 +178,12 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_1702_01335_gb300 import LBS_FP32, LBS_FP64, Instance, Solver
+    from paper_1702_01335_gb300.autotune import autotune
     prec = LBS_FP32 if a.precision == "f32" else LBS_FP64
     inst = [Instance(**W.C2)] * a.batch
     s = Solver(inst, precision=prec)
+    tuned = autotune(s, candidates=tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (8, 12, 16, 24)
+                                         for F in (0, 1)), steps=3)
     st = s.torch_stream()
     upd_step = sum(i.Nz * i.Q for i in inst)
 
@@ -250,11 +252,14 @@ def main():
                                    "Nz=128 A=0.98 Q=8x8x(2x16)=2048 N_eq=4",
                        "batch_per_gpu": a.batch, "state_bytes_per_buffer": s.state_bytes(),
                        "l2": "inputs larger than L2 (3 buffers of %d MiB)" % (s.state_bytes() >> 20),
-                       "parallelism": "replicas, independent batches per GPU"},
+                       "parallelism": "replicas, independent batches per GPU",
+                       "tiling": {"V": tuned["V"], "ZT": tuned["ZT"], "fused_finalise": tuned["fuse"],
+                                  "chosen_by": "autotune.py (CUDA-event timing of candidates)"}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                         "kernel": "stage_kernel (3 launches per step)",
+                         "kernel": "stage_kernel (3 launches per step%s)" % (
+                             ", finalisation folded in" if tuned["fuse"] else ""),
                          "algorithmic_bytes_per_update_step": bpu,
                          "stage_kernel_ms_per_step": k_stage / nprof,
                          "finalize_ms_per_step": k_fin / nprof,
@@ -263,7 +268,7 @@ def main():
                     "h2d_bytes_per_step": s.state_bytes(), "d2h_bytes_per_step": nprof_rows * 8,
                     "what": "lbs_set_state(all, pinned host) + lbs_step(1) + lbs_moments(all, host) "
                             "per step"},
-            "gpu_launches": KERNELS_PER_STEP * a.steps,
+            "gpu_launches": (3 if tuned["fuse"] else 9) * a.steps,
             "clocks": clk.summary(),
         }
         if not a.no_cpu_baseline and world == 1:

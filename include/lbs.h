@@ -179,22 +179,25 @@ lbs_status lbs_moments_static(lbs_handle h, int inst, const void* f_dev, double*
 
 /* Run nsteps steps launching every kernel directly with CUDA events around
  * each on the handle's stream, and return summed device times in ms:
- * out_ms[0] the stage kernels (WENO advection, collision, RK combine, moment
- * and wall-flux partials), out_ms[1] the per-cell and per-instance finalise
- * kernels, out_ms[2] the whole steps.  Synchronises.  For measurement only;
- * the arithmetic is that of lbs_step. */
+ * out_ms[0] the stage kernels (WENO advection, collision, RK combine, moments,
+ * walls, and the finalisation they fold in), out_ms[1] the separate finalisation
+ * launches (0 when fused), out_ms[2] the whole steps.
+ * Synchronises.  For measurement only; the arithmetic is that of lbs_step. */
 lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms);
 
 /* Work decomposition of the stage kernel (no effect on the arithmetic): each
  * CTA of 128 threads updates 128*V velocities (V in {1, 2, 4}) of about ZT
- * consecutive cells (3 <= ZT <= 64).  Used by the tile autotuner.  Waits for
- * the handle's stream and recomputes the moment partials of the current state.
- * LBS_ERR_ARG outside the ranges. */
-lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT);
+ * consecutive cells (3 <= ZT <= 64).  fuse = 1 folds the per-cell and
+ * per-instance finalisation into the stage kernel (the last CTA of a z-tile /
+ * of an instance does it: 3 launches per step); fuse = 0 runs it as two
+ * further launches per stage (cheaper for large batches).  Used by the tile
+ * autotuner.  Waits for the handle's stream and recomputes the moment
+ * partials of the current state.  LBS_ERR_ARG outside the ranges. */
+lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT, int fuse);
 
-/* Current tiling: V, ZT, number of stage CTAs, dynamic shared memory per CTA.
- * Any output pointer may be NULL. */
-lbs_status lbs_get_tiling(lbs_handle h, int* V, int* ZT, int* ntiles, long* smem_bytes);
+/* Current tiling: V, ZT, fuse, number of stage CTAs, dynamic shared memory per
+ * CTA.  Any output pointer may be NULL. */
+lbs_status lbs_get_tiling(lbs_handle h, int* V, int* ZT, int* fuse, int* ntiles, long* smem_bytes);
 
 /* The CUDA stream (cudaStream_t) the handle queues its work on: the one given at
  * creation, or the stream the library created when NULL was given. */

@@ -1,7 +1,7 @@
 """Tile autotuner for the stage kernel.
 
 The stage kernel's work decomposition (velocities per thread V, cells per
-z-tile ZT) changes how many CTAs fit on an SM, how much halo is re-read and how
+z-tile ZT, finalisation folded into the stage kernel or launched apart) changes how many CTAs fit on an SM, how much halo is re-read and how
 the per-cell moment reduction is amortised; it does not change the arithmetic.
 `autotune(solver)` times every candidate with CUDA events on a scratch solver
 built from the same instances (so the caller's state and step counters are not
@@ -14,7 +14,7 @@ import os
 
 from .lbs import LbsError, Solver
 
-CANDIDATES = tuple((V, ZT) for V in (1, 2, 4) for ZT in (4, 6, 8, 12, 16, 24, 32))
+CANDIDATES = tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (4, 6, 8, 12, 16, 24, 32) for F in (0, 1))
 _cache = {}
 
 
@@ -32,32 +32,33 @@ def _load(path):
 
 
 def autotune(solver, candidates=CANDIDATES, steps=3, cache_file=None, verbose=False):
-    """Pick the fastest (V, ZT) for solver's batch; returns {"V", "ZT", "ms_per_step", "table"}."""
+    """Pick the fastest (V, ZT, fuse) for solver's batch; returns {"V", "ZT", "fuse", "ms_per_step", "table"}."""
     key = signature(solver)
     disk = _load(cache_file)
     hit = _cache.get(key) or disk.get(key)
     if hit:
-        solver.set_tiling(hit["V"], hit["ZT"])
+        solver.set_tiling(hit["V"], hit["ZT"], hit["fuse"])
         return hit
     scratch = Solver(solver.instances, precision=solver.precision)
     table = []
     try:
-        for V, ZT in candidates:
+        for V, ZT, F in candidates:
             try:
-                scratch.set_tiling(V, ZT)
+                scratch.set_tiling(V, ZT, F)
             except LbsError:
                 continue
             scratch.profile_steps(1)
             stage_ms, fin_ms, step_ms = scratch.profile_steps(steps)
-            table.append({"V": V, "ZT": ZT, "ms_per_step": step_ms / steps,
+            table.append({"V": V, "ZT": ZT, "fuse": F, "ms_per_step": step_ms / steps,
                           "stage_ms_per_step": stage_ms / steps, "ctas": scratch.tiling()["ctas"]})
             if verbose:
                 print(table[-1], flush=True)
     finally:
         scratch.close()
     best = min(table, key=lambda r: r["ms_per_step"])
-    res = {"V": best["V"], "ZT": best["ZT"], "ms_per_step": best["ms_per_step"], "table": table}
-    solver.set_tiling(best["V"], best["ZT"])
+    res = {"V": best["V"], "ZT": best["ZT"], "fuse": best["fuse"], "ms_per_step": best["ms_per_step"],
+           "table": table}
+    solver.set_tiling(best["V"], best["ZT"], best["fuse"])
     _cache[key] = res
     if cache_file:
         disk[key] = res

@@ -15,12 +15,13 @@
 
 namespace lbs {
 cudaError_t launch_stage(int fp32, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
-                         int ntiles, size_t smem, cudaStream_t st);
-cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int ninst, int maxNz,
-                            cudaStream_t st);
+                         int ntiles, size_t smem, int fuse, int ninst, int maxNz, cudaStream_t st);
+cudaError_t launch_stage_only(int fp32, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
+                              int ntiles, size_t smem, int fuse, cudaStream_t st);
+cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int ninst, int maxNz, cudaStream_t st);
 cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,
                         cudaStream_t st);
-size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage);
+size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int nhx, int nhy, int npz);
 }  // namespace lbs
 
 using namespace lbs;
@@ -44,7 +45,7 @@ namespace {
 
 struct InstHost {
     lbs_instance_desc d;
-    int Nz, Q, Qx, Qy, Qz, Nx, Ny, Nzq, nchunks, nzm_max;
+    int Nz, Q, Qx, Qy, Qz, Nx, Ny, Nzq, nchunks, nzm_max, nzt;
     double dt;
     std::vector<double> xc, xf;  // cell centres (s = -3..Nz+2, 0-based), interfaces
 };
@@ -66,7 +67,7 @@ struct Pool {  // bump allocator over one device allocation
 struct lbs_solver {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int fp32 = 0, esize = 8, V = 1, ZT = 16, ninst = 0, maxNz = 0;
+    int fp32 = 0, esize = 8, V = 1, ZT = 16, fuse = 1, ninst = 0, maxNz = 0;
     std::vector<InstHost> ih;
     std::vector<InstDev> idev;
     InstDev* d_inst = nullptr;
@@ -161,19 +162,21 @@ static void build_tiles(lbs_solver* h, std::vector<Tile>& tiles)
         }
         I.nzm_max = nzm_max;
         const int G = I.Qx + I.Qy + nzm_max;
+        const int nhx = I.Qx * (I.Nx + 1), nhy = I.Qy * (I.Ny + 1), npz = I.Qz * (I.Nzq + 1);
         // z-tiles of about ZT cells, at least 3 cells each, within the shared-memory budget
         int zt = std::max(3, std::min(h->ZT, kMaxZT));
-        while (zt > 3 && stage_smem_bytes(h->fp32, h->V, zt, G, 3) > kSmemBudget) --zt;
+        while (zt > 3 && stage_smem_bytes(h->fp32, h->V, zt, G, 3, nhx, nhy, npz) > kSmemBudget) --zt;
         int nzt = std::min((I.Nz + zt - 1) / zt, I.Nz / 3);
         nzt = std::max(nzt, 1);
         const int base = I.Nz / nzt, rem = I.Nz % nzt;
         const int zmax = base + (rem ? 1 : 0);
-        smem = std::max(smem, stage_smem_bytes(h->fp32, h->V, zmax, G, 3));
+        I.nzt = nzt;
+        smem = std::max(smem, stage_smem_bytes(h->fp32, h->V, zmax, G, 3, nhx, nhy, npz));
         for (int c = 0; c < I.nchunks; ++c) {
             int z0 = 0;
             for (int t = 0; t < nzt; ++t) {
                 const int zn = base + (t < rem ? 1 : 0);
-                tiles.push_back(Tile{b, z0, zn, c});
+                tiles.push_back(Tile{b, z0, zn, c, t});
                 z0 += zn;
             }
         }
@@ -189,7 +192,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
     Pool pool;
     struct Off {
         size_t Hx, Hy, Pz, alpha, beta, px, py, xi, wx, wy, wz, gxt, gxb, gwy, gwz, idz;
-        size_t F0, F1, F2, rec, partial, flux, nw, prof, Wold, Wnew, res, steps, active, status;
+        size_t F0, F1, F2, rec, partial, flux, nw, prof, Wold, Wnew, res, steps, active, status, zcount, icount;
     };
     std::vector<Off> off(h->ninst);
     struct Tables {
@@ -314,6 +317,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         o.nw = pool.take(2 * 8); o.prof = pool.take(14 * (size_t)Nz * 8);
         o.Wold = pool.take(3 * (size_t)Nz * 8); o.Wnew = pool.take(3 * (size_t)Nz * 8);
         o.res = pool.take(8); o.steps = pool.take(8); o.active = pool.take(4); o.status = pool.take(4);
+        o.zcount = pool.take(4 * (size_t)std::max(1, Nz / 3)); o.icount = pool.take(4);
     }
     const size_t inst_off = pool.take(sizeof(InstDev) * h->ninst);
     size_t max_tiles = 0;  // tiles of the finest tiling (V = 1, 3-cell z-tiles)
@@ -362,6 +366,9 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         D.steps = reinterpret_cast<long long*>(P + o.steps);
         D.active = reinterpret_cast<int*>(P + o.active);
         D.status = reinterpret_cast<int*>(P + o.status);
+        D.zcount = reinterpret_cast<int*>(P + o.zcount);
+        D.icount = reinterpret_cast<int*>(P + o.icount);
+        D.nzt = I.nzt;
     }
     std::memcpy(img.data() + inst_off, h->idev.data(), sizeof(InstDev) * h->ninst);
     std::memcpy(img.data() + tile_off, tiles.data(), sizeof(Tile) * tiles.size());
@@ -377,16 +384,14 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
 // moments, records, wall densities and W_old of the current F0 (every active instance)
 static lbs_status analyse(lbs_solver* h)
 {
-    CK(launch_stage(h->fp32, h->V, 0, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->stream));
-    CK(launch_finalize(h->fp32, 0, h->d_inst, h->ninst, h->maxNz, h->stream));
+    CK(launch_stage(h->fp32, h->V, 0, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse, h->ninst, h->maxNz, h->stream));
     return LBS_OK;
 }
 
 static lbs_status enqueue_step(lbs_solver* h)
 {
     for (int s = 1; s <= 3; ++s) {
-        CK(launch_stage(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->stream));
-        CK(launch_finalize(h->fp32, s, h->d_inst, h->ninst, h->maxNz, h->stream));
+        CK(launch_stage(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse, h->ninst, h->maxNz, h->stream));
     }
     return LBS_OK;
 }
@@ -464,7 +469,8 @@ lbs_status lbs_batch_create(lbs_handle* out, const lbs_instance_desc* desc, int 
     for (int b = 0; b < n; ++b)
         work += (long)desc[b].grid.Nz * 2 * desc[b].orders.Qx * desc[b].orders.Qy * desc[b].orders.Qz_half;
     h->V = work >= (1L << 22) ? 2 : 1;
-    h->ZT = 16;
+    h->ZT = work >= (1L << 22) ? 16 : 4;
+    h->fuse = work >= (1L << 22) ? 0 : 1;
     if (cuda_stream) {
         h->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -574,29 +580,28 @@ lbs_status lbs_run_to_steady(lbs_handle h, double tol, long max_steps, int check
 lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms)
 {
     if (!h || nsteps < 1 || !out_ms) return fail(LBS_ERR_ARG, "need a handle, nsteps >= 1 and an output");
-    const int nev = 18;  // per step: 9 kernels, an event before and after each
-    std::vector<cudaEvent_t> ev(nev);
+    std::vector<cudaEvent_t> ev(7);  // per step: before/after each stage kernel, after its finalisation
     for (auto& e : ev) CK(cudaEventCreate(&e));
     double tstage = 0.0, tfin = 0.0, tstep = 0.0;
     lbs_status st = LBS_OK;
     for (long it = 0; it < nsteps && st == LBS_OK; ++it) {
+        CK(cudaEventRecord(ev[0], h->stream));
         for (int s = 1; s <= 3; ++s) {
-            CK(cudaEventRecord(ev[6 * (s - 1) + 0], h->stream));
-            CK(launch_stage(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->stream));
-            CK(cudaEventRecord(ev[6 * (s - 1) + 1], h->stream));
-            CK(launch_finalize(h->fp32, s, h->d_inst, h->ninst, h->maxNz, h->stream));
-            CK(cudaEventRecord(ev[6 * (s - 1) + 2], h->stream));
+            CK(launch_stage_only(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse, h->stream));
+            CK(cudaEventRecord(ev[2 * s - 1], h->stream));
+            if (!h->fuse) CK(launch_finalize(h->fp32, s, h->d_inst, h->ninst, h->maxNz, h->stream));
+            CK(cudaEventRecord(ev[2 * s], h->stream));
         }
-        CK(cudaEventSynchronize(ev[6 * 2 + 2]));
-        for (int s = 0; s < 3; ++s) {
+        CK(cudaEventSynchronize(ev[6]));
+        for (int s = 1; s <= 3; ++s) {
             float a = 0.f, b = 0.f;
-            CK(cudaEventElapsedTime(&a, ev[6 * s + 0], ev[6 * s + 1]));
-            CK(cudaEventElapsedTime(&b, ev[6 * s + 1], ev[6 * s + 2]));
+            CK(cudaEventElapsedTime(&a, ev[2 * s - 2], ev[2 * s - 1]));
+            CK(cudaEventElapsedTime(&b, ev[2 * s - 1], ev[2 * s]));
             tstage += a;
             tfin += b;
         }
         float w = 0.f;
-        CK(cudaEventElapsedTime(&w, ev[0], ev[6 * 2 + 2]));
+        CK(cudaEventElapsedTime(&w, ev[0], ev[6]));
         tstep += w;
     }
     for (auto& e : ev) cudaEventDestroy(e);
@@ -606,18 +611,22 @@ lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms)
     return check_status(h);
 }
 
-lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT)
+lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT, int fuse)
 {
-    if (!h || (V != 1 && V != 2 && V != 4) || ZT < 3 || ZT > kMaxZT)
-        return fail(LBS_ERR_ARG, "tiling needs V in {1, 2, 4} and 3 <= ZT <= 64");
+    if (!h || (V != 1 && V != 2 && V != 4) || ZT < 3 || ZT > kMaxZT || (fuse != 0 && fuse != 1))
+        return fail(LBS_ERR_ARG, "tiling needs V in {1, 2, 4}, 3 <= ZT <= 64 and fuse in {0, 1}");
     CK(cudaStreamSynchronize(h->stream));
     drop_graph(h);
     h->V = V;
     h->ZT = ZT;
+    h->fuse = fuse;
     std::vector<Tile> tiles;
     build_tiles(h, tiles);
     if (tiles.size() > h->max_tiles) return fail(LBS_ERR_ARG, "tile list exceeds its buffer");
-    for (int b = 0; b < h->ninst; ++b) h->idev[b].nchunks = h->ih[b].nchunks;
+    for (int b = 0; b < h->ninst; ++b) {
+        h->idev[b].nchunks = h->ih[b].nchunks;
+        h->idev[b].nzt = h->ih[b].nzt;
+    }
     CK(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->ninst, cudaMemcpyHostToDevice, h->stream));
     h->ntiles = (int)tiles.size();
@@ -626,11 +635,12 @@ lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT)
     return check_status(h);
 }
 
-lbs_status lbs_get_tiling(lbs_handle h, int* V, int* ZT, int* ntiles, long* smem_bytes)
+lbs_status lbs_get_tiling(lbs_handle h, int* V, int* ZT, int* fuse, int* ntiles, long* smem_bytes)
 {
     if (!h) return fail(LBS_ERR_ARG, "invalid handle");
     if (V) *V = h->V;
     if (ZT) *ZT = h->ZT;
+    if (fuse) *fuse = h->fuse;
     if (ntiles) *ntiles = h->ntiles;
     if (smem_bytes) *smem_bytes = (long)h->smem;
     return LBS_OK;

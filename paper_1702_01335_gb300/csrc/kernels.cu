@@ -19,11 +19,13 @@
 //                    moments of F_out (FP32 within a warp in FP32 mode, FP64
 //                    across warps and chunks).  Tiles that end at a wall also
 //                    reduce the outgoing WENO flux of F_out through the wall.
-//   finalize_cells   one thread per cell: sums the per-chunk moment partials
-//                    in FP64, forms n, u, P, T, q (Eq. qdef) and tau, and writes
-//                    the cell record (scalars and expansion coefficients).
-//   finalize_inst    one CTA per instance: wall densities n_w (zero net mass
-//                    flux, Appendix) and, after the third stage, the residual.
+//                    Finalisation needs no further launch: the CTA that ends
+//                    last among the chunks of a z-tile (threadfence tickets)
+//                    sums their partials in FP64 per cell, forms n, u, P, T, q
+//                    (Eq. qdef) and tau, and writes the cell records of the
+//                    next stage; the one that completes an instance's last
+//                    z-tile forms the wall densities n_w (zero net mass flux,
+//                    Appendix) and, after the third stage, the residual.
 //
 // Storage: F[s][k] for interior cells s = 0..Nz-1 (no ghost rows), velocity
 // k = ((sg*Qz + m)*Qx + i)*Qy + j fastest, holding f_k / w_k.
@@ -39,7 +41,6 @@ template <typename T> struct Acc { typedef double type; };
 template <> struct Acc<float> { typedef float type; };
 
 constexpr uint32_t kSpinLimit = 1u << 26;  // bounded mbarrier waits (~seconds)
-constexpr int kIdz = 11;                   // smem copy of a record: slot 11 holds 1/dz
 
 // ---- PTX helpers: mbarrier and bulk global -> shared copies ------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -195,31 +196,175 @@ __device__ __forceinline__ A reduce_scatter16(A (&v)[16], int lane)
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// shared-memory layout of a stage CTA (element offsets are in bytes)
+// shared-memory layout of a stage CTA (offsets in bytes): staged F_in rows,
+// F_l rows, the cell records and the Hermite basis tables (all by bulk copy),
+// the evaluated per-axis factors, 1/dz, and the per-warp moment sums.
 struct StageSmem {
-    size_t fin, f0, g, sc, red, total;
+    size_t fin, f0, rec, hx, hy, pz, g, idz, red, total;
 };
-__host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize, int asize, bool withF0)
+__host__ __device__ inline size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
+__host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize, int asize, bool withF0,
+                                                int nhx, int nhy, int npz)
 {
     StageSmem L;
     size_t o = 0;
     L.fin = o; o += (size_t)(zn + 6) * KC * esize;
     L.f0 = o; o += withF0 ? (size_t)zn * KC * esize : 0;
-    L.g = o; o += (size_t)zn * G * esize;
-    L.sc = o; o += (size_t)zn * kRecHead * esize;
-    o = (o + 15) & ~size_t(15);
+    L.rec = o; o += (size_t)zn * kRecStride * esize;
+    L.hx = o; o += pad16((size_t)nhx * esize);
+    L.hy = o; o += pad16((size_t)nhy * esize);
+    L.pz = o; o += pad16((size_t)npz * esize);
+    L.g = o; o += pad16((size_t)zn * G * esize);
+    L.idz = o; o += pad16((size_t)zn * esize);
     L.red = o; o += (size_t)zn * (kThreads / 32) * 16 * asize;
     L.total = o;
     return L;
 }
 
 // ----------------------------------------------------------------------------
+// Cell record from a macroscopic state: scalars and the coefficients a_l, b_l
+// of the truncated Hermite equilibrium (Sec. III, Eqs. fyz, Fmn_def), FP64.
+// Returns false for a non-finite or non-positive state (a neutral state is
+// written instead).
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ bool write_record(const InstDev& I, int cell, double n, const double* u, double T_, const double* q)
+{
+    bool bad = !(n > 0.0) || !(T_ > 0.0) || !isfinite(n) || !isfinite(T_);
+    for (int a = 0; a < 3; ++a) bad |= !isfinite(u[a]) || !isfinite(q[a]);
+    const double nn = bad ? 1.0 : n, Tc = bad ? 1.0 : T_;
+    const double u0 = bad ? 0.0 : u[0], u1 = bad ? 0.0 : u[1], u2 = bad ? 0.0 : u[2];
+    T* rec = static_cast<T*>(I.rec) + (size_t)cell * kRecStride;
+    double c[kMaxN + 1];
+    full_coeffs(u0, Tc, I.Nx, c);
+    for (int l = 0; l <= kMaxN; ++l) rec[R_AX + l] = l <= I.Nx ? T(c[l]) : T(0);
+    full_coeffs(u1, Tc, I.Ny, c);
+    for (int l = 0; l <= kMaxN; ++l) rec[R_AY + l] = l <= I.Ny ? T(c[l]) : T(0);
+    half_coeffs(u2, Tc, I.Nzq, I.alpha, I.beta, c);
+    for (int l = 0; l <= kMaxN; ++l) rec[R_BP + l] = l <= I.Nzq ? T(c[l]) : T(0);
+    half_coeffs(-u2, Tc, I.Nzq, I.alpha, I.beta, c);
+    for (int l = 0; l <= kMaxN; ++l) rec[R_BM + l] = l <= I.Nzq ? T(c[l]) : T(0);
+    const double tau = relax_time(I.visc_law, I.Kn, I.visc_param, nn, Tc);
+    rec[R_N] = T(nn); rec[R_UX] = T(u0); rec[R_UY] = T(u1); rec[R_UZ] = T(u2); rec[R_T] = T(Tc);
+    rec[R_QX] = T(bad ? 0.0 : q[0]); rec[R_QY] = T(bad ? 0.0 : q[1]); rec[R_QZ] = T(bad ? 0.0 : q[2]);
+    rec[R_ITAU] = T(1.0 / tau);
+    rec[R_CS] = T((1.0 - I.Pr) / (nn * Tc * Tc));
+    rec[R_I5T] = T(1.0 / (5.0 * Tc));
+    rec[11] = T(0);
+    return !bad;
+}
+
+// One cell (one thread): FP64 sum of the per-chunk moment partials (written by
+// other CTAs of this launch, hence read past L1), then n, u, P, T, q
+// (Eq. qdef) from the raw moments, the profiles, W for the residual, and the
+// cell record of the next stage.
+template <typename T>
+__device__ void finalize_cell(const InstDev& I, int cell)
+{
+    const int Nz = I.Nz;
+    double mom[kNMom];
+    for (int a = 0; a < kNMom; ++a) mom[a] = 0.0;
+    for (int c = 0; c < I.nchunks; ++c)
+#pragma unroll
+        for (int a = 0; a < kNMom; ++a) mom[a] += __ldcg(I.partial + ((size_t)c * kNMom + a) * Nz + cell);
+    const double n = mom[0];
+    const double u[3] = {mom[1] / n, mom[2] / n, mom[3] / n};
+    // central second moments P_ab = sum p_a p_b f - n u_a u_b
+    const double Pxx = mom[4] - n * u[0] * u[0], Pyy = mom[5] - n * u[1] * u[1];
+    const double Pzz = mom[6] - n * u[2] * u[2], Pxy = mom[7] - n * u[0] * u[1];
+    const double Pxz = mom[8] - n * u[0] * u[2], Pyz = mom[9] - n * u[1] * u[2];
+    const double T_ = (Pxx + Pyy + Pzz) / (3.0 * n);
+    // q_a = 1/2 sum |xi|^2 xi_a f with xi = p - u, expanded in raw moments
+    const double M2[3][3] = {{mom[4], mom[7], mom[8]}, {mom[7], mom[5], mom[9]}, {mom[8], mom[9], mom[6]}};
+    const double tr = mom[4] + mom[5] + mom[6];
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double um = u[0] * mom[1] + u[1] * mom[2] + u[2] * mom[3];
+    double q[3];
+    for (int a = 0; a < 3; ++a) {
+        const double uM2 = u[0] * M2[0][a] + u[1] * M2[1][a] + u[2] * M2[2][a];
+        q[a] = 0.5 * (mom[10 + a] - u[a] * tr - 2.0 * uM2 + 2.0 * u[a] * um + uu * mom[1 + a] - uu * u[a] * n);
+    }
+    const double vals[14] = {n, u[0], u[1], u[2], T_, q[0], q[1], q[2], Pxx, Pyy, Pzz, Pxy, Pxz, Pyz};
+    bool bad = false;
+    for (int a = 0; a < 14; ++a) {
+        I.prof[(size_t)a * Nz + cell] = vals[a];
+        bad |= !isfinite(vals[a]);
+    }
+    I.Wnew[cell] = n;
+    I.Wnew[Nz + cell] = u[0];
+    I.Wnew[2 * Nz + cell] = T_;
+    bad |= !write_record<T>(I, cell, n, u, T_, q);
+    if (bad) atomicOr(I.status, 1);
+}
+
+// One instance (whole CTA): wall densities n_w from the outgoing wall fluxes
+// (zero net mass flux, Appendix); after stage 3 the residual, the step count
+// and retirement; after the analysis pass W_old = W.
+__device__ void finalize_instance(const InstDev& I, int stage, double* red)
+{
+    const int t = threadIdx.x, Nz = I.Nz;
+    double fb = 0.0, ft = 0.0;
+    for (int c = t; c < I.nchunks; c += blockDim.x) {
+        fb += __ldcg(I.flux_part + 2 * c);
+        ft += __ldcg(I.flux_part + 2 * c + 1);
+    }
+    fb = block_sum(fb, red);
+    ft = block_sum(ft, red);
+    if (t == 0) {
+        I.nw[0] = -fb / I.Dbot;
+        I.nw[1] = -ft / I.Dtop;
+        if (!isfinite(I.nw[0]) || !isfinite(I.nw[1])) atomicOr(I.status, 1);
+    }
+    if (stage == 3) {
+        double R = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double d = 0.0, o = 0.0;
+            for (int s = t; s < Nz; s += blockDim.x) {
+                const double wn = __ldcg(I.Wnew + a * Nz + s), wo = I.Wold[a * Nz + s];
+                d += (wn - wo) * (wn - wo);
+                o += wo * wo;
+            }
+            d = block_sum(d, red);
+            o = block_sum(o, red);
+            R = fmax(R, sqrt(d) / fmax(sqrt(o), 1e-30));
+        }
+        __syncthreads();
+        for (int e = t; e < 3 * Nz; e += blockDim.x) I.Wold[e] = __ldcg(I.Wnew + e);
+        if (t == 0) {
+            *I.res = R;
+            *I.steps += 1;
+            if (!(R == R)) atomicOr(I.status, 1);
+            if (I.tol > 0.0 && R < I.tol) *I.active = 0;
+        }
+    } else if (stage == 0) {
+        for (int e = t; e < 3 * Nz; e += blockDim.x) I.Wold[e] = __ldcg(I.Wnew + e);
+    }
+}
+
+// records from given macroscopic profiles macro[8][Nz] = n, ux, uy, uz, T, qx, qy, qz
+template <typename T>
+__global__ void records_from_macro(const InstDev* __restrict__ insts, int inst, const double* __restrict__ macro)
+{
+    const InstDev& I = insts[inst];
+    const int Nz = I.Nz, cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= Nz) return;
+    const double u[3] = {macro[Nz + cell], macro[2 * Nz + cell], macro[3 * Nz + cell]};
+    const double q[3] = {macro[5 * Nz + cell], macro[6 * Nz + cell], macro[7 * Nz + cell]};
+    if (!write_record<T>(I, cell, macro[cell], u, macro[4 * Nz + cell], q)) atomicOr(I.status, 1);
+}
+
+// ----------------------------------------------------------------------------
 // stage_kernel<T, V, STAGE>: STAGE 1..3 are the RK stages; STAGE 0 only
 // analyses F0 (moments and wall fluxes) without writing F.
 // ----------------------------------------------------------------------------
+// Minimum resident CTAs per SM requested from the register allocator: the
+// per-velocity register window grows with V; the rarely taken finalisation
+// path may spill instead of lowering occupancy.
+template <int V> struct MinBlocks { static constexpr int value = V == 1 ? 8 : V == 2 ? 6 : 3; };
+
 template <typename T, int V, int STAGE>
-__global__ void __launch_bounds__(kThreads)
-stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
+__global__ void __launch_bounds__(kThreads, MinBlocks<V>::value)
+stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, int fuse)
 {
     typedef typename Acc<T>::type A;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -238,11 +383,16 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr bool kF0 = STAGE >= 2;
 
-    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(A), kF0);
+    const int nhx = Qx * (I.Nx + 1), nhy = Qy * (I.Ny + 1), npz = Qz * (I.Nzq + 1);
+    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(A), kF0, nhx, nhy, npz);
     T* Fs = reinterpret_cast<T*>(smem_raw + L.fin);   // rows: cells z0-3 .. z0+zn+2
     T* F0s = reinterpret_cast<T*>(smem_raw + L.f0);   // rows: cells z0 .. z0+zn-1
+    T* recs = reinterpret_cast<T*>(smem_raw + L.rec); // records of cells z0 .. z0+zn-1
+    T* hxs = reinterpret_cast<T*>(smem_raw + L.hx);
+    T* hys = reinterpret_cast<T*>(smem_raw + L.hy);
+    T* pzs = reinterpret_cast<T*>(smem_raw + L.pz);
     T* gsm = reinterpret_cast<T*>(smem_raw + L.g);
-    T* scs = reinterpret_cast<T*>(smem_raw + L.sc);
+    T* idzs = reinterpret_cast<T*>(smem_raw + L.idz);
     A* red = reinterpret_cast<A*>(smem_raw + L.red);
 
     const T* Fin = static_cast<const T*>(STAGE <= 1 ? I.F0 : STAGE == 2 ? I.F1 : I.F2);
@@ -250,7 +400,10 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
     const T* F0g = static_cast<const T*>(I.F0);
     const int s_lo = max(0, z0 - 3), s_hi = min(Nz - 1, z0 + zn + 2);
 
-    // ---- 1. stage the input rows (TMA bulk copies, or plain loads if unaligned)
+    // ---- 1. stage the input rows, the cell records and the basis tables
+    //         (TMA bulk copies; plain loads if the rows are not 16-byte aligned)
+    const T* Rg = static_cast<const T*>(I.rec) + (size_t)z0 * kRecStride;
+    const size_t rec_bytes = (size_t)zn * kRecStride * sizeof(T);
     if (I.bulk) {
         if (tid == 0) {
             mbar_init(&bar, 1);
@@ -259,12 +412,21 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
         __syncthreads();
         if (tid == 0) {
             const uint32_t bytes = kn * sizeof(T);
-            mbar_expect_tx(&bar, bytes * ((s_hi - s_lo + 1) + (kF0 ? zn : 0)));
+            uint32_t total = bytes * ((s_hi - s_lo + 1) + (kF0 ? zn : 0));
+            if (STAGE > 0)
+                total += rec_bytes + pad16(nhx * sizeof(T)) + pad16(nhy * sizeof(T)) + pad16(npz * sizeof(T));
+            mbar_expect_tx(&bar, total);
             for (int s = s_lo; s <= s_hi; ++s)
                 bulk_g2s(Fs + (size_t)(s - z0 + 3) * KC, Fin + (size_t)s * Q + k0, bytes, &bar);
             if (kF0)
                 for (int c = 0; c < zn; ++c)
                     bulk_g2s(F0s + (size_t)c * KC, F0g + (size_t)(z0 + c) * Q + k0, bytes, &bar);
+            if (STAGE > 0) {
+                bulk_g2s(recs, Rg, rec_bytes, &bar);
+                bulk_g2s(hxs, I.Hx, pad16(nhx * sizeof(T)), &bar);  // tables are padded to 16 bytes
+                bulk_g2s(hys, I.Hy, pad16(nhy * sizeof(T)), &bar);
+                bulk_g2s(pzs, I.Pz, pad16(npz * sizeof(T)), &bar);
+            }
         }
     } else {
         for (int s = s_lo; s <= s_hi; ++s)
@@ -272,35 +434,15 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
         if (kF0)
             for (int c = 0; c < zn; ++c)
                 for (int kl = tid; kl < kn; kl += kThreads) F0s[(size_t)c * KC + kl] = F0g[(size_t)(z0 + c) * Q + k0 + kl];
-    }
-
-    // ---- 2. meanwhile: per-cell equilibrium factors from the cell records
-    if (STAGE > 0) {
-        const T* R = static_cast<const T*>(I.rec);
-        for (int e = tid; e < zn * G; e += kThreads) {
-            const int c = e / G, r = e - c * G;
-            const T* rc = R + (size_t)(z0 + c) * kRecStride;
-            T g = 0;
-            if (r < Qx) {
-                const T* h = static_cast<const T*>(I.Hx) + r * (I.Nx + 1);
-                for (int l = 0; l <= I.Nx; ++l) g += rc[R_AX + l] * h[l];
-                g *= rc[R_N];
-            } else if (r < Qx + Qy) {
-                const T* h = static_cast<const T*>(I.Hy) + (r - Qx) * (I.Ny + 1);
-                for (int l = 0; l <= I.Ny; ++l) g += rc[R_AY + l] * h[l];
-            } else {
-                const int zm = zm_lo + r - Qx - Qy, sg = zm >= Qz, m = zm - sg * Qz;
-                const T* h = static_cast<const T*>(I.Pz) + m * (I.Nzq + 1);
-                const T* b = rc + (sg ? R_BM : R_BP);
-                for (int l = 0; l <= I.Nzq; ++l) g += b[l] * h[l];
-            }
-            gsm[e] = g;
-        }
-        for (int e = tid; e < zn * kRecHead; e += kThreads) {
-            const int c = e / kRecHead, r = e - c * kRecHead;
-            scs[e] = r == kIdz ? ld<T>(I.inv_dz, z0 + c) : R[(size_t)(z0 + c) * kRecStride + r];
+        if (STAGE > 0) {
+            for (int e = tid; e < zn * kRecStride; e += kThreads) recs[e] = Rg[e];
+            for (int e = tid; e < nhx; e += kThreads) hxs[e] = ld<T>(I.Hx, e);
+            for (int e = tid; e < nhy; e += kThreads) hys[e] = ld<T>(I.Hy, e);
+            for (int e = tid; e < npz; e += kThreads) pzs[e] = ld<T>(I.Pz, e);
         }
     }
+    if (STAGE > 0)
+        for (int c = tid; c < zn; c += kThreads) idzs[c] = ld<T>(I.inv_dz, z0 + c);
 
     // per-velocity constants: p, and w * psi(p) for the 13 raw moments
     int ii[V], jj[V], zz[V], kl[V];
@@ -347,7 +489,31 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
         return;
     }
 
-    // ---- 4. ghost rows (each thread fills only its own columns)
+    // ---- 4a. per-cell factors of the truncated Hermite equilibrium (Sec. III)
+    //          from the staged records: n*Gx[i], Gy[j], Gz[zm] for this chunk's zm
+    if (STAGE > 0) {
+        for (int e = tid; e < zn * G; e += kThreads) {
+            const int c = e / G, r = e - c * G;
+            const T* rc = recs + (size_t)c * kRecStride;
+            T g = 0;
+            if (r < Qx) {
+                const T* h = hxs + r * (I.Nx + 1);
+                for (int l = 0; l <= I.Nx; ++l) g += rc[R_AX + l] * h[l];
+                g *= rc[R_N];
+            } else if (r < Qx + Qy) {
+                const T* h = hys + (r - Qx) * (I.Ny + 1);
+                for (int l = 0; l <= I.Ny; ++l) g += rc[R_AY + l] * h[l];
+            } else {
+                const int zm = zm_lo + r - Qx - Qy, sg = zm >= Qz, m = zm - sg * Qz;
+                const T* h = pzs + m * (I.Nzq + 1);
+                const T* b = rc + (sg ? R_BM : R_BP);
+                for (int l = 0; l <= I.Nzq; ++l) g += b[l] * h[l];
+            }
+            gsm[e] = g;
+        }
+    }
+
+    // ---- 4b. ghost rows (each thread fills only its own columns)
     const int rbase = 3 - z0;  // smem row of cell s is s + rbase
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -385,6 +551,8 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
         }
     }
 
+    __syncthreads();  // per-cell factors complete
+
     // ---- 5. march up the z-range
     T w[V][6], flm[V];
 #pragma unroll
@@ -395,15 +563,16 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
                                 : weno5<T>(w[v][5], w[v][4], w[v][3], w[v][2], w[v][1]));
     }
     const T dt = T(I.dt);
+    T* outp = Fout + (size_t)z0 * Q + k0;
+#pragma unroll 2
     for (int c = 0; c < zn; ++c) {
-        const int s = z0 + c;
-        const T* sc = scs + c * kRecHead;
+        const T* sc = recs + (size_t)c * kRecStride;
         const T* gc = gsm + c * G;
         T ux = 0, uy = 0, uz = 0, i5T = 0, qx = 0, qy = 0, qz = 0, itau = 0, cS = 0, idz = 0;
         if (STAGE > 0) {
             ux = sc[R_UX]; uy = sc[R_UY]; uz = sc[R_UZ];
             qx = sc[R_QX]; qy = sc[R_QY]; qz = sc[R_QZ];
-            itau = sc[R_ITAU]; cS = sc[R_CS]; i5T = sc[R_I5T]; idz = sc[kIdz];
+            itau = sc[R_ITAU]; cS = sc[R_CS]; i5T = sc[R_I5T]; idz = idzs[c];
         }
         A acc[16];
 #pragma unroll
@@ -430,7 +599,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
                 if (STAGE == 1) out = f1;
                 else if (STAGE == 2) out = T(0.75) * F0s[(size_t)c * KC + kl[v]] + T(0.25) * f1;
                 else out = T(1.0 / 3.0) * F0s[(size_t)c * KC + kl[v]] + T(2.0 / 3.0) * f1;
-                if (ok[v]) Fout[(size_t)s * Q + k0 + kl[v]] = out;
+                if (ok[v]) outp[kl[v]] = out;
                 flm[v] = flp;
             }
 #pragma unroll
@@ -443,6 +612,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
         const A tot = reduce_scatter16<A>(acc, lane);
         const int m = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
         if ((lane & 1) == 0) red[((size_t)c * (kThreads / 32) + warp) * 16 + m] = tot;
+        outp += Q;
     }
     __syncthreads();
     for (int e = tid; e < zn * kNMom; e += kThreads) {
@@ -484,142 +654,47 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles)
         fl = block_sum(fl, wall_red);
         if (tid == 0) I.flux_part[tile.chunk * 2 + 1] = fl;
     }
+
+    // ---- 7. (fuse != 0) finalisation without extra launches (threadfence tickets): the CTA
+    // that finishes last among the chunks of this z-tile finalises the tile's
+    // cells; the one that finalises the instance's last z-tile does the walls
+    // and the residual.  Counters are reset by their last user.
+    if (!fuse) return;  // finalize_cells / finalize_inst follow as separate launches
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(I.zcount + tile.zt, 1) == I.nchunks - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (tid < zn) finalize_cell<T>(I, z0 + tid);
+    if (tid == 0) I.zcount[tile.zt] = 0;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(I.icount, 1) == I.nzt - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (tid == 0) *I.icount = 0;
+    finalize_instance(I, STAGE, wall_red);
 }
 
-// ----------------------------------------------------------------------------
-// Cell record from a macroscopic state: scalars and the coefficients a_l, b_l
-// of the truncated Hermite equilibrium (Sec. III, Eqs. fyz, Fmn_def), FP64.
-// Returns false for a non-finite or non-positive state (a neutral state is
-// written instead).
-// ----------------------------------------------------------------------------
-template <typename T>
-__device__ bool write_record(const InstDev& I, int cell, double n, const double* u, double T_, const double* q)
-{
-    bool bad = !(n > 0.0) || !(T_ > 0.0) || !isfinite(n) || !isfinite(T_);
-    for (int a = 0; a < 3; ++a) bad |= !isfinite(u[a]) || !isfinite(q[a]);
-    const double nn = bad ? 1.0 : n, Tc = bad ? 1.0 : T_;
-    const double u0 = bad ? 0.0 : u[0], u1 = bad ? 0.0 : u[1], u2 = bad ? 0.0 : u[2];
-    T* rec = static_cast<T*>(I.rec) + (size_t)cell * kRecStride;
-    double c[kMaxN + 1];
-    full_coeffs(u0, Tc, I.Nx, c);
-    for (int l = 0; l <= kMaxN; ++l) rec[R_AX + l] = l <= I.Nx ? T(c[l]) : T(0);
-    full_coeffs(u1, Tc, I.Ny, c);
-    for (int l = 0; l <= kMaxN; ++l) rec[R_AY + l] = l <= I.Ny ? T(c[l]) : T(0);
-    half_coeffs(u2, Tc, I.Nzq, I.alpha, I.beta, c);
-    for (int l = 0; l <= kMaxN; ++l) rec[R_BP + l] = l <= I.Nzq ? T(c[l]) : T(0);
-    half_coeffs(-u2, Tc, I.Nzq, I.alpha, I.beta, c);
-    for (int l = 0; l <= kMaxN; ++l) rec[R_BM + l] = l <= I.Nzq ? T(c[l]) : T(0);
-    const double tau = relax_time(I.visc_law, I.Kn, I.visc_param, nn, Tc);
-    rec[R_N] = T(nn); rec[R_UX] = T(u0); rec[R_UY] = T(u1); rec[R_UZ] = T(u2); rec[R_T] = T(Tc);
-    rec[R_QX] = T(bad ? 0.0 : q[0]); rec[R_QY] = T(bad ? 0.0 : q[1]); rec[R_QZ] = T(bad ? 0.0 : q[2]);
-    rec[R_ITAU] = T(1.0 / tau);
-    rec[R_CS] = T((1.0 - I.Pr) / (nn * Tc * Tc));
-    rec[R_I5T] = T(1.0 / (5.0 * Tc));
-    rec[11] = T(0);
-    return !bad;
-}
-
-// ----------------------------------------------------------------------------
-// finalize_cells<T>: one thread per cell; moments -> macroscopic -> record
-// ----------------------------------------------------------------------------
+// ---- separate finalisation launches (used when the stage kernel does not fuse them)
 template <typename T>
 __global__ void __launch_bounds__(64) finalize_cells(const InstDev* __restrict__ insts)
 {
     const InstDev& I = insts[blockIdx.y];
-    const int Nz = I.Nz, cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= Nz || *I.active == 0) return;
-    double mom[kNMom];
-    for (int a = 0; a < kNMom; ++a) mom[a] = 0.0;
-    for (int c = 0; c < I.nchunks; ++c)
-#pragma unroll
-        for (int a = 0; a < kNMom; ++a) mom[a] += I.partial[((size_t)c * kNMom + a) * Nz + cell];
-    const double n = mom[0];
-    const double u[3] = {mom[1] / n, mom[2] / n, mom[3] / n};
-    // central second moments P_ab = sum p_a p_b f - n u_a u_b
-    const double Pxx = mom[4] - n * u[0] * u[0], Pyy = mom[5] - n * u[1] * u[1];
-    const double Pzz = mom[6] - n * u[2] * u[2], Pxy = mom[7] - n * u[0] * u[1];
-    const double Pxz = mom[8] - n * u[0] * u[2], Pyz = mom[9] - n * u[1] * u[2];
-    const double T_ = (Pxx + Pyy + Pzz) / (3.0 * n);
-    // q_a = 1/2 sum |xi|^2 xi_a f with xi = p - u, expanded in raw moments
-    const double M2[3][3] = {{mom[4], mom[7], mom[8]}, {mom[7], mom[5], mom[9]}, {mom[8], mom[9], mom[6]}};
-    const double tr = mom[4] + mom[5] + mom[6];
-    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const double um = u[0] * mom[1] + u[1] * mom[2] + u[2] * mom[3];
-    double q[3];
-    for (int a = 0; a < 3; ++a) {
-        const double uM2 = u[0] * M2[0][a] + u[1] * M2[1][a] + u[2] * M2[2][a];
-        q[a] = 0.5 * (mom[10 + a] - u[a] * tr - 2.0 * uM2 + 2.0 * u[a] * um + uu * mom[1 + a] - uu * u[a] * n);
-    }
-    const double vals[14] = {n, u[0], u[1], u[2], T_, q[0], q[1], q[2], Pxx, Pyy, Pzz, Pxy, Pxz, Pyz};
-    bool bad = false;
-    for (int a = 0; a < 14; ++a) {
-        I.prof[(size_t)a * Nz + cell] = vals[a];
-        bad |= !isfinite(vals[a]);
-    }
-    I.Wnew[cell] = n;
-    I.Wnew[Nz + cell] = u[0];
-    I.Wnew[2 * Nz + cell] = T_;
-    bad |= !write_record<T>(I, cell, n, u, T_, q);
-    if (bad) atomicOr(I.status, 1);
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= I.Nz || *I.active == 0) return;
+    finalize_cell<T>(I, cell);
 }
 
-// records from given macroscopic profiles macro[8][Nz] = n, ux, uy, uz, T, qx, qy, qz
-template <typename T>
-__global__ void records_from_macro(const InstDev* __restrict__ insts, int inst, const double* __restrict__ macro)
+__global__ void __launch_bounds__(128) finalize_inst(const InstDev* __restrict__ insts, int stage)
 {
-    const InstDev& I = insts[inst];
-    const int Nz = I.Nz, cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= Nz) return;
-    const double u[3] = {macro[Nz + cell], macro[2 * Nz + cell], macro[3 * Nz + cell]};
-    const double q[3] = {macro[5 * Nz + cell], macro[6 * Nz + cell], macro[7 * Nz + cell]};
-    if (!write_record<T>(I, cell, macro[cell], u, macro[4 * Nz + cell], q)) atomicOr(I.status, 1);
-}
-
-// ----------------------------------------------------------------------------
-// finalize_inst: wall densities; after stage 3 the residual and retirement
-// ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) finalize_inst(const InstDev* __restrict__ insts, int stage)
-{
+    __shared__ double red[4];
     const InstDev& I = insts[blockIdx.x];
     if (*I.active == 0) return;
-    __shared__ double red[8];
-    const int t = threadIdx.x, Nz = I.Nz;
-    double fb = 0.0, ft = 0.0;
-    for (int c = t; c < I.nchunks; c += blockDim.x) {
-        fb += I.flux_part[2 * c];
-        ft += I.flux_part[2 * c + 1];
-    }
-    fb = block_sum(fb, red);
-    ft = block_sum(ft, red);
-    if (t == 0) {
-        I.nw[0] = -fb / I.Dbot;
-        I.nw[1] = -ft / I.Dtop;
-        if (!isfinite(I.nw[0]) || !isfinite(I.nw[1])) atomicOr(I.status, 1);
-    }
-    if (stage == 3) {
-        double R = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            double d = 0.0, o = 0.0;
-            for (int s = t; s < Nz; s += blockDim.x) {
-                const double e = I.Wnew[a * Nz + s] - I.Wold[a * Nz + s];
-                d += e * e;
-                o += I.Wold[a * Nz + s] * I.Wold[a * Nz + s];
-            }
-            d = block_sum(d, red);
-            o = block_sum(o, red);
-            R = fmax(R, sqrt(d) / fmax(sqrt(o), 1e-30));
-        }
-        __syncthreads();
-        for (int e = t; e < 3 * Nz; e += blockDim.x) I.Wold[e] = I.Wnew[e];
-        if (t == 0) {
-            *I.res = R;
-            *I.steps += 1;
-            if (!(R == R)) atomicOr(I.status, 1);
-            if (I.tol > 0.0 && R < I.tol) *I.active = 0;
-        }
-    } else if (stage == 0) {
-        for (int e = t; e < 3 * Nz; e += blockDim.x) I.Wold[e] = I.Wnew[e];
-    }
+    finalize_instance(I, stage, red);
 }
 
 // ---- seed a cell from its record: f_k / w_k = n Gx Gy Gz (1 + S) ----------
@@ -646,58 +721,77 @@ __global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ in
 }
 
 // ---- host launchers ---------------------------------------------------------
-size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage)
+size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int nhx, int nhy, int npz)
 {
     const int KC = kThreads * V;
-    return stage_smem(zn, KC, G, fp32 ? 4 : 8, fp32 ? 4 : 8, stage >= 2).total;
+    return stage_smem(zn, KC, G, fp32 ? 4 : 8, fp32 ? 4 : 8, stage >= 2, nhx, nhy, npz).total;
 }
 
 template <typename T, int V, int STAGE>
 static cudaError_t launch_stage_t(const InstDev* d_inst, const Tile* d_tiles, int ntiles, size_t smem,
-                                  cudaStream_t st)
+                                  int fuse, cudaStream_t st)
 {
     auto kfn = stage_kernel<T, V, STAGE>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kfn<<<ntiles, kThreads, smem, st>>>(d_inst, d_tiles);
+    kfn<<<ntiles, kThreads, smem, st>>>(d_inst, d_tiles, fuse);
     return cudaGetLastError();
 }
 
 template <typename T, int V>
-static cudaError_t launch_stage_v(int stage, const InstDev* d, const Tile* t, int n, size_t smem,
+static cudaError_t launch_stage_v(int stage, const InstDev* d, const Tile* t, int n, size_t smem, int fuse,
                                   cudaStream_t st)
 {
     switch (stage) {
-        case 0: return launch_stage_t<T, V, 0>(d, t, n, smem, st);
-        case 1: return launch_stage_t<T, V, 1>(d, t, n, smem, st);
-        case 2: return launch_stage_t<T, V, 2>(d, t, n, smem, st);
-        default: return launch_stage_t<T, V, 3>(d, t, n, smem, st);
+        case 0: return launch_stage_t<T, V, 0>(d, t, n, smem, fuse, st);
+        case 1: return launch_stage_t<T, V, 1>(d, t, n, smem, fuse, st);
+        case 2: return launch_stage_t<T, V, 2>(d, t, n, smem, fuse, st);
+        default: return launch_stage_t<T, V, 3>(d, t, n, smem, fuse, st);
     }
 }
 
-cudaError_t launch_stage(int fp32, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
-                         int ntiles, size_t smem, cudaStream_t st)
+template <typename T>
+static cudaError_t launch_finalize_t(int stage, const InstDev* d_inst, int ninst, int maxNz, cudaStream_t st)
 {
-    if (fp32) {
-        if (V == 1) return launch_stage_v<float, 1>(stage, d_inst, d_tiles, ntiles, smem, st);
-        if (V == 2) return launch_stage_v<float, 2>(stage, d_inst, d_tiles, ntiles, smem, st);
-        return launch_stage_v<float, 4>(stage, d_inst, d_tiles, ntiles, smem, st);
-    }
-    if (V == 1) return launch_stage_v<double, 1>(stage, d_inst, d_tiles, ntiles, smem, st);
-    if (V == 2) return launch_stage_v<double, 2>(stage, d_inst, d_tiles, ntiles, smem, st);
-    return launch_stage_v<double, 4>(stage, d_inst, d_tiles, ntiles, smem, st);
-}
-
-cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int ninst, int maxNz,
-                            cudaStream_t st)
-{
-    dim3 g((maxNz + 63) / 64, ninst);
-    if (fp32) finalize_cells<float><<<g, 64, 0, st>>>(d_inst);
-    else finalize_cells<double><<<g, 64, 0, st>>>(d_inst);
+    finalize_cells<T><<<dim3((maxNz + 63) / 64, ninst), 64, 0, st>>>(d_inst);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    finalize_inst<<<ninst, 256, 0, st>>>(d_inst, stage);
+    finalize_inst<<<ninst, 128, 0, st>>>(d_inst, stage);
     return cudaGetLastError();
+}
+
+// the stage kernel alone
+cudaError_t launch_stage_only(int fp32, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
+                              int ntiles, size_t smem, int fuse, cudaStream_t st)
+{
+    cudaError_t e;
+    if (fp32) {
+        if (V == 1) e = launch_stage_v<float, 1>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+        else if (V == 2) e = launch_stage_v<float, 2>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+        else e = launch_stage_v<float, 4>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+    } else {
+        if (V == 1) e = launch_stage_v<double, 1>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+        else if (V == 2) e = launch_stage_v<double, 2>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+        else e = launch_stage_v<double, 4>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+    }
+    return e;
+}
+
+// the separate finalisation launches of an unfused stage
+cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int ninst, int maxNz, cudaStream_t st)
+{
+    return fp32 ? launch_finalize_t<float>(stage, d_inst, ninst, maxNz, st)
+                : launch_finalize_t<double>(stage, d_inst, ninst, maxNz, st);
+}
+
+// one RK stage (stage 1..3) or the analysis pass (stage 0); without fusion the
+// finalisation follows as two more launches
+cudaError_t launch_stage(int fp32, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
+                         int ntiles, size_t smem, int fuse, int ninst, int maxNz, cudaStream_t st)
+{
+    cudaError_t e = launch_stage_only(fp32, V, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+    if (e != cudaSuccess || fuse) return e;
+    return launch_finalize(fp32, stage, d_inst, ninst, maxNz, st);
 }
 
 cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,

@@ -57,10 +57,13 @@ struct InstDev {
     double *res;                  // [1]
     long long *steps;             // [1]
     int *active;                  // [1]
+    int *zcount;                  // [nzt] chunks of a z-tile finished this stage (ticket counters)
+    int *icount;                  // [1] z-tiles of the instance finalised this stage
+    int nzt;                      // z-tiles of the current tiling
     int *status;                  // [1]: bit 0 non-finite / non-positive n, T
 };
 
-struct Tile { int inst, z0, zn, chunk; };
+struct Tile { int inst, z0, zn, chunk, zt; };
 
 // ---- equilibrium coefficients (shared by host set-up and device finalise) ----
 

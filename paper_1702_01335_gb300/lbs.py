@@ -91,9 +91,9 @@ def load(build_if_missing=True):
         lib.lbs_get_stream.argtypes = [P, H]
         lib.lbs_profile_steps.argtypes = [P, C.c_long, D]
         lib.lbs_moments_static.argtypes = [P, C.c_int, P, P]
-        lib.lbs_set_tiling.argtypes = [P, C.c_int, C.c_int]
+        lib.lbs_set_tiling.argtypes = [P, C.c_int, C.c_int, C.c_int]
         I = C.POINTER(C.c_int)
-        lib.lbs_get_tiling.argtypes = [P, I, I, I, L]
+        lib.lbs_get_tiling.argtypes = [P, I, I, I, I, L]
         lib.lbs_last_error.restype = C.c_char_p
         for name in EXPORTS:
             if name != "lbs_last_error":
@@ -201,13 +201,15 @@ class Solver:
     def step(self, nsteps=1):
         _check(self.lib.lbs_step(self.h, int(nsteps)))
 
-    def set_tiling(self, V, ZT):
-        _check(self.lib.lbs_set_tiling(self.h, int(V), int(ZT)))
+    def set_tiling(self, V, ZT, fuse=None):
+        if fuse is None:
+            fuse = self.tiling()["fuse"]
+        _check(self.lib.lbs_set_tiling(self.h, int(V), int(ZT), int(fuse)))
 
     def tiling(self):
-        v, z, n, sm = C.c_int(), C.c_int(), C.c_int(), C.c_long()
-        _check(self.lib.lbs_get_tiling(self.h, C.byref(v), C.byref(z), C.byref(n), C.byref(sm)))
-        return {"V": v.value, "ZT": z.value, "ctas": n.value, "smem": sm.value}
+        v, z, f, n, sm = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_long()
+        _check(self.lib.lbs_get_tiling(self.h, C.byref(v), C.byref(z), C.byref(f), C.byref(n), C.byref(sm)))
+        return {"V": v.value, "ZT": z.value, "fuse": f.value, "ctas": n.value, "smem": sm.value}
 
     def profile_steps(self, nsteps):
         """Event-timed steps: (stage-kernel ms, finalise-kernel ms, whole-step ms), summed."""

@@ -182,15 +182,16 @@ def test_c3_high_kn_fp32_free_molecular_bound():
     assert np.all(np.abs(p["Pxz"]) <= W.C3["u_w"] * math.sqrt(2 / math.pi) * 1.01)
 
 
-@pytest.mark.parametrize("V,ZT", [(1, 3), (2, 7), (4, 64)])
-def test_tiling_does_not_change_results(V, ZT):
-    """Every work decomposition of the stage kernel gives the oracle's state."""
+@pytest.mark.parametrize("V,ZT,fuse", [(1, 3, 1), (2, 7, 0), (4, 64, 1), (4, 5, 0)])
+def test_tiling_does_not_change_results(V, ZT, fuse):
+    """Every work decomposition of the stage kernel, with the finalisation folded in
+    or launched apart, gives the oracle's state."""
     P = _lbs()
     o = oracle_of(RAGGED, dt=None)
     s = solver_of(RAGGED, o.dt, P.LBS_FP64)
-    s.set_tiling(V, ZT)
+    s.set_tiling(V, ZT, fuse)
     t = s.tiling()
-    assert t["V"] == V and t["ZT"] == ZT
+    assert t["V"] == V and t["ZT"] == ZT and t["fuse"] == fuse
     o.step(15)
     s.step(15)
     assert rel_err(gpu_f(s, o), o.f[3:3 + o.Nz]) < FP64_TOL
@@ -201,8 +202,8 @@ def test_autotuner_picks_a_valid_tiling():
     from paper_1702_01335_gb300.autotune import autotune
     s = solver_of([W.C1] * 4, 0.004, P.LBS_FP32)
     before = s.get_state(0)
-    r = autotune(s, candidates=((1, 8), (2, 16)), steps=2)
-    assert (r["V"], r["ZT"]) in ((1, 8), (2, 16))
+    r = autotune(s, candidates=((1, 8, 1), (2, 16, 0)), steps=2)
+    assert (r["V"], r["ZT"], r["fuse"]) in ((1, 8, 1), (2, 16, 0))
     assert s.tiling()["V"] == r["V"]
     assert np.array_equal(s.get_state(0), before)  # tuning ran on a scratch solver
     assert s.steps_taken() == 0
