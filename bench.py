@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning-cache", default=None,
+                    help="JSON cache of tile choices (default: the package's tuning_cache.json)")
     return ap.parse_args()
 
 
@@ -178,12 +180,13 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_1702_01335_gb300 import LBS_FP32, LBS_FP64, Instance, Solver
-    from paper_1702_01335_gb300.autotune import autotune
+    from paper_1702_01335_gb300.autotune import DEFAULT_CACHE, autotune
     prec = LBS_FP32 if a.precision == "f32" else LBS_FP64
     inst = [Instance(**W.C2)] * a.batch
     s = Solver(inst, precision=prec)
     tuned = autotune(s, candidates=tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (8, 12, 16, 24)
-                                         for F in (0, 1)), steps=3)
+                                         for F in (0, 1)), steps=3,
+                     cache_file=a.tuning_cache or DEFAULT_CACHE)
     st = s.torch_stream()
     upd_step = sum(i.Nz * i.Q for i in inst)
 
@@ -239,6 +242,7 @@ def main():
     tpath = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
     if os.path.exists(tpath):
         d = json.load(open(tpath))
+        from paper_1702_01335_gb300.autotune import kernel_hash
         if d.get("kernel_hash") == kernel_hash() and d.get("precision") == a.precision:
             traffic = d["bytes_per_step_per_update"] * upd_step / 3.0
 
@@ -277,14 +281,6 @@ def main():
     s.close()
     if dist is not None:
         dist.destroy_process_group()
-
-
-def kernel_hash():
-    import hashlib
-    h = hashlib.sha256()
-    for f in ("kernels.cu", "lbs_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1702_01335_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()[:16]
 
 
 if __name__ == "__main__":

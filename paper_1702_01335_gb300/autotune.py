@@ -9,17 +9,30 @@ touched), applies the fastest tiling to `solver`, and caches the choice per
 batch signature (precision and the (Nz, Q) of every instance) in memory and,
 optionally, in a JSON file.
 """
+import hashlib
 import json
 import os
 
 from .lbs import LbsError, Solver
 
+_CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
+
 CANDIDATES = tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (4, 6, 8, 12, 16, 24, 32) for F in (0, 1))
 _cache = {}
 
 
+def kernel_hash():
+    """Hash of the stage kernel's sources: a cached choice is ignored once they change."""
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "lbs_internal.h"):
+        h.update(open(os.path.join(_CSRC, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def signature(solver):
-    return "p%d:" % solver.precision + ",".join("%dx%d" % (i.Nz, i.Q) for i in solver.instances)
+    return "%s:p%d:" % (kernel_hash(), solver.precision) + ",".join(
+        "%dx%d" % (i.Nz, i.Q) for i in solver.instances)
 
 
 def _load(path):
