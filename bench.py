@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tiling", default=None,
+                    help="V,ZT,fuse: use this stage-kernel tiling instead of the autotuner")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON cache of tile choices (default: the package's tuning_cache.json)")
     return ap.parse_args()
@@ -184,9 +186,14 @@ def main():
     prec = LBS_FP32 if a.precision == "f32" else LBS_FP64
     inst = [Instance(**W.C2)] * a.batch
     s = Solver(inst, precision=prec)
-    tuned = autotune(s, candidates=tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (8, 12, 16, 24)
-                                         for F in (0, 1)), steps=3,
-                     cache_file=a.tuning_cache or DEFAULT_CACHE)
+    if a.tiling:
+        V, ZT, F = (int(x) for x in a.tiling.split(","))
+        s.set_tiling(V, ZT, F)
+        tuned = {"V": V, "ZT": ZT, "fuse": F, "source": "--tiling"}
+    else:
+        tuned = autotune(s, candidates=tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (8, 12, 16, 24)
+                                             for F in (0, 1)), steps=3,
+                         cache_file=a.tuning_cache or DEFAULT_CACHE)
     st = s.torch_stream()
     upd_step = sum(i.Nz * i.Q for i in inst)
 
@@ -258,7 +265,8 @@ def main():
                        "l2": "inputs larger than L2 (3 buffers of %d MiB)" % (s.state_bytes() >> 20),
                        "parallelism": "replicas, independent batches per GPU",
                        "tiling": {"V": tuned["V"], "ZT": tuned["ZT"], "fused_finalise": tuned["fuse"],
-                                  "chosen_by": "autotune.py (CUDA-event timing of candidates)"}},
+                                  "chosen_by": tuned.get("source", "autotune.py (CUDA-event timing of "
+                                                                   "candidates, cached per kernel hash)")}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",

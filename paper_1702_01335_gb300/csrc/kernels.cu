@@ -511,16 +511,48 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             }
             gsm[e] = g;
         }
+        __syncthreads();
+        // Normalise the factors so that the discrete equilibrium carries exactly
+        // the cell's n: in exact arithmetic sum_i wx Gx = n, sum_j wy Gy = 1 and
+        // sum over both half ranges of wz Gz = 1 (orthogonality of the bases);
+        // with bases and coefficients rounded to the storage type the sums are
+        // off by a few ulps of the same sign every step, which would make FP32
+        // runs drift in mass.  One warp per cell, FP64 sums.
+        for (int c = warp; c < zn; c += kThreads / 32) {
+            const T* rc = recs + (size_t)c * kRecStride;
+            const T* gc = gsm + (size_t)c * G;
+            double sx = 0.0, sy = 0.0, sz = 0.0;
+            for (int i = lane; i < Qx; i += 32) sx += double(ld<T>(I.wx, i)) * double(gc[i]);
+            for (int j = lane; j < Qy; j += 32) sy += double(ld<T>(I.wy, j)) * double(gc[Qx + j]);
+            for (int zm = lane; zm < 2 * Qz; zm += 32) {
+                const int sg = zm >= Qz, m = zm - sg * Qz;
+                const T* h = pzs + m * (I.Nzq + 1);
+                const T* b = rc + (sg ? R_BM : R_BP);
+                T g = 0;
+                for (int l = 0; l <= I.Nzq; ++l) g += b[l] * h[l];
+                sz += double(ld<T>(I.wz, m)) * double(g);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                sz += __shfl_xor_sync(0xffffffffu, sz, o);
+            }
+            const T scale = T(double(rc[R_N]) / (sx * sy * sz));
+            for (int i = lane; i < Qx; i += 32) gsm[(size_t)c * G + i] *= scale;
+        }
     }
 
     // ---- 4b. ghost rows (each thread fills only its own columns)
     const int rbase = 3 - z0;  // smem row of cell s is s + rbase
+    T gin[V];                  // incoming ghost value n_w Gw next to this tile's wall
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         T* col = Fs + kl[v];
+        gin[v] = T(0);
         if (z0 < 3) {
             if (up[v]) {  // incoming at the bottom wall: n_w times the wall equilibrium
                 const T g = T(I.nw[0]) * ld<T>(I.gwx_bot, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
+                gin[v] = g;
                 for (int s = -3; s <= -1; ++s)
                     if (s + rbase >= 0) col[(size_t)(s + rbase) * KC] = g;
             } else {      // outgoing: quadratic extrapolation (Appendix)
@@ -537,6 +569,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             const int smax = z0 + zn + 2;
             if (!up[v]) {
                 const T g = T(I.nw[1]) * ld<T>(I.gwx_top, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
+                gin[v] = g;
                 for (int s = Nz; s <= Nz + 2; ++s)
                     if (s <= smax) col[(size_t)(s + rbase) * KC] = g;
             } else {
@@ -561,8 +594,12 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         for (int d = 0; d < 6; ++d) w[v][d] = Fs[(size_t)d * KC + kl[v]];
         flm[v] = pz[v] * (up[v] ? weno5<T>(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4])
                                 : weno5<T>(w[v][5], w[v][4], w[v][3], w[v][2], w[v][1]));
+        // through a wall the incoming flux is the wall Maxwellian's, p_z n_w Gw (the
+        // first stencil is constant: Table weno gives exactly this value)
+        if (z0 == 0 && up[v]) flm[v] = pz[v] * gin[v];
     }
     const T dt = T(I.dt);
+    const int last_c = z0 + zn == Nz ? zn - 1 : -1;  // iteration whose upper face is the top wall
     T* outp = Fout + (size_t)z0 * Q + k0;
 #pragma unroll 2
     for (int c = 0; c < zn; ++c) {
@@ -586,7 +623,8 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 const bool u = up[v];
                 const T a0 = u ? w[v][1] : wn, a1 = u ? w[v][2] : w[v][5], a2 = u ? w[v][3] : w[v][4];
                 const T a3 = u ? w[v][4] : w[v][3], a4 = u ? w[v][5] : w[v][2];
-                const T flp = pz[v] * weno5<T>(a0, a1, a2, a3, a4);
+                T flp = pz[v] * weno5<T>(a0, a1, a2, a3, a4);
+                if (!u && c == last_c) flp = pz[v] * gin[v];  // incoming through the top wall
                 const T f = w[v][3];
                 // Shakhov target n Gx Gy Gz (1 + S), S = cS (xi^2/(5T) - 1) xi.q
                 const T ex = px[v] - ux, ey = py[v] - uy, ez = pz[v] - uz;
@@ -596,9 +634,16 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 const T geq = gc[ii[v]] * gc[Qx + jj[v]] * gc[Qx + Qy + zz[v] - zm_lo];
                 const T Lv = -(flp - flm[v]) * idz - (f - geq * (T(1) + S)) * itau;
                 const T f1 = f + dt * Lv;
-                if (STAGE == 1) out = f1;
-                else if (STAGE == 2) out = T(0.75) * F0s[(size_t)c * KC + kl[v]] + T(0.25) * f1;
-                else out = T(1.0 / 3.0) * F0s[(size_t)c * KC + kl[v]] + T(2.0 / 3.0) * f1;
+                // Shu-Osher combine written as F_l + b (f1 - F_l): identical to
+                // (1 - b) F_l + b f1, but a rounded b only scales the increment
+                // (with b = 2/3 the two rounded weights would not add up to 1 and
+                // would scale the whole state every step)
+                if (STAGE == 1) {
+                    out = f1;
+                } else {
+                    const T fl = F0s[(size_t)c * KC + kl[v]];
+                    out = fl + (STAGE == 2 ? T(0.25) : T(2.0 / 3.0)) * (f1 - fl);
+                }
                 if (ok[v]) outp[kl[v]] = out;
                 flm[v] = flp;
             }

@@ -30,11 +30,12 @@ def rel_err(a, b, scale=None):
 PROFILES = ("n", "ux", "uy", "uz", "T", "qx", "qy", "qz", "Pxx", "Pyy", "Pzz", "Pxy", "Pxz", "Pyz")
 
 
-def profile_errors(gp, op):
+def profile_errors(gp, op, uw=None):
     """max |gpu - oracle| / scale per profile.  The scale is max |oracle| of the profile,
     except: u_y, u_z, P_xy, P_yz vanish by symmetry and take the scale of u_x or P_xz;
     the heat fluxes are differences of raw third moments of size n T^(3/2), so they are
-    compared on that scale (a q of 1e-3 n T^(3/2) keeps ~3 fewer digits than the sums)."""
+    compared on that scale (a q of 1e-3 n T^(3/2) keeps ~3 fewer digits than the sums).
+    With uw given, velocities are compared on the Couette scale max(max |u_x|, u_w)."""
     out = {}
     ref_scale = {"uy": "ux", "uz": "ux", "Pxy": "Pxz", "Pyz": "Pxz"}
     thermal = float(np.max(op["n"] * op["T"] ** 1.5))
@@ -43,5 +44,7 @@ def profile_errors(gp, op):
             scale = thermal
         else:
             scale = np.abs(op[ref_scale.get(k, k)]).max()
+            if uw is not None and k in ("ux", "uy", "uz"):
+                scale = max(scale, uw)
         out[k] = rel_err(gp[k], op[k], max(scale, 1e-300))
     return out
