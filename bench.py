@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-steady", action="store_true",
+                    help="skip the time-to-steady-state comparison (plain vs batched vs warm-started)")
     ap.add_argument("--tiling", default=None,
                     help="V,ZT,fuse: use this stage-kernel tiling instead of the autotuner")
     ap.add_argument("--tuning-cache", default=None,
@@ -137,6 +139,22 @@ def cpu_baseline(seconds=12.0):
     return {"value": upd / dt, "unit": "updates/s", "cores": cores, "kind": "oracle",
             "sample": "one C2 instance (128 cells x 2048 velocities), %d full RK-3 steps, FP64, "
                       "%.1f s" % (n, dt)}
+
+
+def time_to_steady():
+    """Wall time to R < 1e-8 of 256 held-out sweep draws: the plain single-instance
+    solver from rest (a sample of 16, extrapolated), one batched launch from rest, and
+    one batched launch from the warm-start network trained on 2000 steady solves."""
+    try:
+        from paper_1702_01335_gb300.warmstart import evaluate
+        r = evaluate(W.warm_start_draws(2000, W.TRAIN_SEED), W.warm_start_draws(256, W.HELDOUT_SEED),
+                     n_plain=16)
+        r["workload"] = ("sweep draws: Kn log-uniform clipped to [0.05, 20], u_w in [0.05, 1], "
+                         "Pr = 2/3, half mu ~ T^omega, half Sutherland; Nz 32-64, Qx 4-8, Qy 4, Qz 4-8; "
+                         "FP32 storage; train seed 1703, held-out seed 1704")
+        return r
+    except Exception as e:  # reported, never fatal to the throughput line
+        return {"error": "%s: %s" % (type(e).__name__, e)}
 
 
 def run_reference(a):
@@ -285,6 +303,8 @@ def main():
         }
         if not a.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
+        if not a.no_steady and world == 1:
+            line["time_to_steady"] = time_to_steady()
         print(json.dumps(line), flush=True)
     s.close()
     if dist is not None:

@@ -208,6 +208,43 @@ lbs_status lbs_get_stream(lbs_handle h, void** out);
  * Needs no GPU.  LBS_ERR_ARG for Q outside 1..64. */
 lbs_status lbs_quadrature(int kind, int Q, double* nodes, double* weights);
 
+/* ---- Warm-start network (not in the paper: the learned initial state of the
+ * batched sweep).  A perceptron n_in -> n_hidden -> n_hidden -> n_out with GELU
+ * activations, gelu(z) = z (1 + erf(z / sqrt 2)) / 2, maps the parameters of a
+ * Couette problem to its steady profiles; its output seeds a solve through
+ * lbs_init_from_profiles.  Products run on tensor cores in BF16 with FP32
+ * accumulation; every product operand is rounded to BF16 (nearest even);
+ * biases, GELU, the loss and Adam are FP32 with FP32 master weights.
+ * Parameters are packed FP32 in the order W1 [n_hidden][n_in], b1, W2
+ * [n_hidden][n_hidden], b2, W3 [n_out][n_hidden], b3.  Batches are row-major
+ * [B][n_in] / [B][n_out] FP32 arrays in device memory owned by the caller. */
+typedef struct lbs_mlp* lbs_mlp_handle;
+
+/* Allocate the network's parameters, Adam state and activations for batches
+ * up to max_batch (all zero: call lbs_mlp_set_params).  stream as in
+ * lbs_create.  LBS_ERR_ARG for sizes outside 1..4096 or max_batch outside
+ * 1..2^20; LBS_ERR_CUDA if the allocation fails. */
+lbs_status lbs_mlp_create(lbs_mlp_handle* out, int n_in, int n_hidden, int n_out, int max_batch, void* stream);
+lbs_status lbs_mlp_destroy(lbs_mlp_handle h);
+/* Number of packed parameters. */
+lbs_status lbs_mlp_num_params(lbs_mlp_handle h, long* out);
+/* Set the FP32 master parameters from host memory (and their BF16 copies);
+ * resets the Adam state.  LBS_ERR_NONFINITE for a non-finite value. */
+lbs_status lbs_mlp_set_params(lbs_mlp_handle h, const float* host_params);
+/* Copy the FP32 master parameters to host memory (synchronises). */
+lbs_status lbs_mlp_get_params(lbs_mlp_handle h, float* host_params);
+/* y = network(x) for B rows (asynchronous on the network's stream). */
+lbs_status lbs_mlp_forward(lbs_mlp_handle h, const float* x_dev, int B, float* y_dev);
+/* Forward and backward pass of the loss L = mean (y - t)^2 over the batch and the
+ * outputs; the gradients stay on the device for lbs_mlp_adam.  loss_out and
+ * grad_host (packed like the parameters) may be NULL; either one synchronises. */
+lbs_status lbs_mlp_loss_grad(lbs_mlp_handle h, const float* x_dev, const float* t_dev, int B, double* loss_out,
+                             float* grad_host);
+/* One Adam step (bias-corrected) with the last gradients. */
+lbs_status lbs_mlp_adam(lbs_mlp_handle h, float lr, float beta1, float beta2, float eps);
+/* The network's CUDA stream. */
+lbs_status lbs_mlp_get_stream(lbs_mlp_handle h, void** out);
+
 /* Message of the last error of the calling thread ("" if none). */
 const char* lbs_last_error(void);
 

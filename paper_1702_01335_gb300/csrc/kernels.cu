@@ -125,26 +125,32 @@ __device__ __forceinline__ float rcp_approx(float x)
 // FP32 form: the same weights with sigma_q^2 floored at 1e-37 (branch free,
 // hardware reciprocals).  As sigma_q -> 0 the floor gives exactly the limits
 // of Table (weno); it changes nothing while sigma_q^2 > 1e-30, i.e. for
-// differences above the FP32 resolution of O(1) normalised populations.
+// differences above the FP32 resolution of O(1) normalised populations.  The
+// candidate reconstructions are written as v2 plus corrections made of
+// differences (c_q = v2 + e_q / 6), so a constant stencil gives exactly its
+// value (the incoming ghosts at a wall: the flux is then exactly the wall
+// Maxwellian's, as Table weno implies) and the rounded weights only multiply the
+// small corrections.
 template <>
 __device__ __forceinline__ float weno5<float>(float v0, float v1, float v2, float v3, float v4)
 {
-    const float c1 = fmaf(1.f / 3.f, v0, fmaf(-7.f / 6.f, v1, (11.f / 6.f) * v2));
-    const float c2 = fmaf(-1.f / 6.f, v1, fmaf(5.f / 6.f, v2, (1.f / 3.f) * v3));
-    const float c3 = fmaf(1.f / 3.f, v2, fmaf(5.f / 6.f, v3, (-1.f / 6.f) * v4));
-    float a = fmaf(-2.f, v1, v0 + v2), b = fmaf(3.f, v2, fmaf(-4.f, v1, v0));
+    const float d0 = v0 - v2, d1 = v1 - v2, d3 = v3 - v2, d4 = v4 - v2;
+    const float e1 = fmaf(2.f, d0, -7.f * d1);   // 6 (c1 - v2)
+    const float e2 = fmaf(2.f, d3, -d1);         // 6 (c2 - v2)
+    const float e3 = fmaf(5.f, d3, -d4);         // 6 (c3 - v2)
+    float a = d0 - 2.f * d1, b = fmaf(-4.f, d1, d0);          // v0-2v1+v2, v0-4v1+3v2
     const float s1 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
-    a = fmaf(-2.f, v2, v1 + v3);
-    b = v1 - v3;
+    a = d1 + d3;                                             // v1-2v2+v3
+    b = d1 - d3;                                             // v1-v3
     const float s2 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
-    a = fmaf(-2.f, v3, v2 + v4);
-    b = fmaf(3.f, v2, fmaf(-4.f, v3, v4));
+    a = fmaf(-2.f, d3, d4);                                  // v2-2v3+v4
+    b = fmaf(-4.f, d3, d4);                                  // 3v2-4v3+v4
     const float s3 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
     const float w1 = 0.1f * rcp_approx(fmaf(s1, s1, 1e-37f));
     const float w2 = 0.6f * rcp_approx(fmaf(s2, s2, 1e-37f));
     const float w3 = 0.3f * rcp_approx(fmaf(s3, s3, 1e-37f));
-    const float inv = rcp_approx(w1 + w2 + w3);
-    return fmaf(w1 * inv, c1, fmaf(w2 * inv, c2, (w3 * inv) * c3));
+    const float inv = (1.f / 6.f) * rcp_approx(w1 + w2 + w3);
+    return fmaf(fmaf(w1, e1, fmaf(w2, e2, w3 * e3)), inv, v2);
 }
 
 template <typename T>
@@ -250,7 +256,32 @@ __device__ bool write_record(const InstDev& I, int cell, double n, const double*
     rec[R_ITAU] = T(1.0 / tau);
     rec[R_CS] = T((1.0 - I.Pr) / (nn * Tc * Tc));
     rec[R_I5T] = T(1.0 / (5.0 * Tc));
-    rec[11] = T(0);
+    // R_SCALE multiplies the x factors so that the discrete equilibrium carries
+    // exactly n: in exact arithmetic sum_i wx Gx = 1, sum_j wy Gy = 1 and the sum
+    // over both half ranges of wz Gz = 1 (orthogonality of the bases); with
+    // coefficients and bases rounded to the storage type the sums miss by a few
+    // ulps of the same sign every step, which would let FP32 runs drift in mass.
+    // The factors are evaluated here exactly as the stage kernel evaluates them.
+    typedef typename Acc<T>::type A;
+    A sx = 0, sy = 0, sz = 0;
+    for (int i = 0; i < I.Qx; ++i) {
+        T g = 0;
+        for (int l = 0; l <= I.Nx; ++l) g += rec[R_AX + l] * ld<T>(I.Hx, i * (I.Nx + 1) + l);
+        sx += A(ld<T>(I.wx, i)) * A(g);
+    }
+    for (int j = 0; j < I.Qy; ++j) {
+        T g = 0;
+        for (int l = 0; l <= I.Ny; ++l) g += rec[R_AY + l] * ld<T>(I.Hy, j * (I.Ny + 1) + l);
+        sy += A(ld<T>(I.wy, j)) * A(g);
+    }
+    for (int zm = 0; zm < 2 * I.Qz; ++zm) {
+        const int sg = zm >= I.Qz, m = zm - sg * I.Qz;
+        const T* b = rec + (sg ? R_BM : R_BP);
+        T g = 0;
+        for (int l = 0; l <= I.Nzq; ++l) g += b[l] * ld<T>(I.Pz, m * (I.Nzq + 1) + l);
+        sz += A(ld<T>(I.wz, m)) * A(g);
+    }
+    rec[R_SCALE] = T(A(nn) / (sx * sy * sz));
     return !bad;
 }
 
@@ -499,7 +530,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             if (r < Qx) {
                 const T* h = hxs + r * (I.Nx + 1);
                 for (int l = 0; l <= I.Nx; ++l) g += rc[R_AX + l] * h[l];
-                g *= rc[R_N];
+                g *= rc[R_SCALE];
             } else if (r < Qx + Qy) {
                 const T* h = hys + (r - Qx) * (I.Ny + 1);
                 for (int l = 0; l <= I.Ny; ++l) g += rc[R_AY + l] * h[l];
@@ -511,48 +542,16 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             }
             gsm[e] = g;
         }
-        __syncthreads();
-        // Normalise the factors so that the discrete equilibrium carries exactly
-        // the cell's n: in exact arithmetic sum_i wx Gx = n, sum_j wy Gy = 1 and
-        // sum over both half ranges of wz Gz = 1 (orthogonality of the bases);
-        // with bases and coefficients rounded to the storage type the sums are
-        // off by a few ulps of the same sign every step, which would make FP32
-        // runs drift in mass.  One warp per cell, FP64 sums.
-        for (int c = warp; c < zn; c += kThreads / 32) {
-            const T* rc = recs + (size_t)c * kRecStride;
-            const T* gc = gsm + (size_t)c * G;
-            double sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int i = lane; i < Qx; i += 32) sx += double(ld<T>(I.wx, i)) * double(gc[i]);
-            for (int j = lane; j < Qy; j += 32) sy += double(ld<T>(I.wy, j)) * double(gc[Qx + j]);
-            for (int zm = lane; zm < 2 * Qz; zm += 32) {
-                const int sg = zm >= Qz, m = zm - sg * Qz;
-                const T* h = pzs + m * (I.Nzq + 1);
-                const T* b = rc + (sg ? R_BM : R_BP);
-                T g = 0;
-                for (int l = 0; l <= I.Nzq; ++l) g += b[l] * h[l];
-                sz += double(ld<T>(I.wz, m)) * double(g);
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                sy += __shfl_xor_sync(0xffffffffu, sy, o);
-                sz += __shfl_xor_sync(0xffffffffu, sz, o);
-            }
-            const T scale = T(double(rc[R_N]) / (sx * sy * sz));
-            for (int i = lane; i < Qx; i += 32) gsm[(size_t)c * G + i] *= scale;
-        }
     }
 
     // ---- 4b. ghost rows (each thread fills only its own columns)
     const int rbase = 3 - z0;  // smem row of cell s is s + rbase
-    T gin[V];                  // incoming ghost value n_w Gw next to this tile's wall
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         T* col = Fs + kl[v];
-        gin[v] = T(0);
         if (z0 < 3) {
             if (up[v]) {  // incoming at the bottom wall: n_w times the wall equilibrium
                 const T g = T(I.nw[0]) * ld<T>(I.gwx_bot, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
-                gin[v] = g;
                 for (int s = -3; s <= -1; ++s)
                     if (s + rbase >= 0) col[(size_t)(s + rbase) * KC] = g;
             } else {      // outgoing: quadratic extrapolation (Appendix)
@@ -569,7 +568,6 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             const int smax = z0 + zn + 2;
             if (!up[v]) {
                 const T g = T(I.nw[1]) * ld<T>(I.gwx_top, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
-                gin[v] = g;
                 for (int s = Nz; s <= Nz + 2; ++s)
                     if (s <= smax) col[(size_t)(s + rbase) * KC] = g;
             } else {
@@ -594,12 +592,8 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         for (int d = 0; d < 6; ++d) w[v][d] = Fs[(size_t)d * KC + kl[v]];
         flm[v] = pz[v] * (up[v] ? weno5<T>(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4])
                                 : weno5<T>(w[v][5], w[v][4], w[v][3], w[v][2], w[v][1]));
-        // through a wall the incoming flux is the wall Maxwellian's, p_z n_w Gw (the
-        // first stencil is constant: Table weno gives exactly this value)
-        if (z0 == 0 && up[v]) flm[v] = pz[v] * gin[v];
     }
     const T dt = T(I.dt);
-    const int last_c = z0 + zn == Nz ? zn - 1 : -1;  // iteration whose upper face is the top wall
     T* outp = Fout + (size_t)z0 * Q + k0;
 #pragma unroll 2
     for (int c = 0; c < zn; ++c) {
@@ -623,8 +617,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 const bool u = up[v];
                 const T a0 = u ? w[v][1] : wn, a1 = u ? w[v][2] : w[v][5], a2 = u ? w[v][3] : w[v][4];
                 const T a3 = u ? w[v][4] : w[v][3], a4 = u ? w[v][5] : w[v][2];
-                T flp = pz[v] * weno5<T>(a0, a1, a2, a3, a4);
-                if (!u && c == last_c) flp = pz[v] * gin[v];  // incoming through the top wall
+                const T flp = pz[v] * weno5<T>(a0, a1, a2, a3, a4);
                 const T f = w[v][3];
                 // Shakhov target n Gx Gy Gz (1 + S), S = cS (xi^2/(5T) - 1) xi.q
                 const T ex = px[v] - ux, ey = py[v] - uy, ez = pz[v] - uz;
@@ -761,7 +754,7 @@ __global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ in
         const T ex = ld<T>(I.px, i) - rc[R_UX], ey = ld<T>(I.py, j) - rc[R_UY], ez = (sg ? -x : x) - rc[R_UZ];
         const T S = rc[R_CS] * ((ex * ex + ey * ey + ez * ez) * rc[R_I5T] - T(1)) *
                     (ex * rc[R_QX] + ey * rc[R_QY] + ez * rc[R_QZ]);
-        F[k] = rc[R_N] * gx * gy * gz * (T(1) + S);
+        F[k] = rc[R_SCALE] * gx * gy * gz * (T(1) + S);
     }
 }
 

@@ -22,10 +22,11 @@ constexpr int kMaxZT = 64;      // cells of a z-tile
 enum { QUAD_FULL = 0, QUAD_HALF = 1 };
 
 // Cell record (storage type T): n, ux, uy, uz, T, qx, qy, qz, 1/tau,
-// (1 - Pr)/(n T^2), 1/(5T), unused; then the expansion coefficients of the
+// (1 - Pr)/(n T^2), 1/(5T), n / (discrete weighted sums of the per-axis factors);
+// then the expansion coefficients of the
 // truncated equilibrium: a_l (x), a_l (y), b_l (z, p_z > 0), b_l (z, p_z < 0),
 // kMaxN + 1 slots each.
-enum { R_N = 0, R_UX, R_UY, R_UZ, R_T, R_QX, R_QY, R_QZ, R_ITAU, R_CS, R_I5T };
+enum { R_N = 0, R_UX, R_UY, R_UZ, R_T, R_QX, R_QY, R_QZ, R_ITAU, R_CS, R_I5T, R_SCALE };
 constexpr int R_AX = kRecHead, R_AY = R_AX + kMaxN + 1, R_BP = R_AY + kMaxN + 1, R_BM = R_BP + kMaxN + 1;
 constexpr int kRecStride = R_BM + kMaxN + 1;
 

@@ -1,0 +1,362 @@
+"""Learned warm start for batches of Couette problems.
+
+A perceptron (6 -> 256 -> 256 -> 512, GELU; the lbs_mlp_* kernels, BF16 products
+with FP32 accumulation) maps the parameters of a problem
+    (log10 Kn, u_w, T_w, Pr, viscosity law, omega or S)
+to its steady profiles n, u_x, T, q_x, q_z, P_xx, P_xz, P_zz sampled at 64
+uniform points across the channel.  It is trained on steady solves produced by the
+batched solver itself.  Its prediction seeds a solve: the profiles are
+interpolated onto the instance's own cells, the density is rescaled to unit mass
+(the channel holds mass 1 from the rest start), and every cell is set to the
+discrete Shakhov target of (n, u, T, q) (lbs_init_from_profiles).  The solver
+then marches to the same residual target as from the rest state; the network only
+changes where it starts.
+
+Data movement uses PyTorch tensors on the device; every arithmetic step of the
+network runs in the library's kernels.
+"""
+import ctypes as C
+import dataclasses
+import math
+import time
+
+import numpy as np
+
+from . import lbs as L
+
+NPTS = 64            # points per profile
+NPROF = 8            # profiles n, u_x, T, q_x, q_z, P_xx, P_xz, P_zz
+SIZES = (6, 256, 256, NPROF * NPTS)
+
+
+def _mlp_lib():
+    lib = L.load()
+    if not getattr(lib, "_mlp_ready", False):
+        P, D, H = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_void_p)
+        F = C.POINTER(C.c_float)
+        lib.lbs_mlp_create.argtypes = [H, C.c_int, C.c_int, C.c_int, C.c_int, P]
+        lib.lbs_mlp_destroy.argtypes = [P]
+        lib.lbs_mlp_num_params.argtypes = [P, C.POINTER(C.c_long)]
+        lib.lbs_mlp_set_params.argtypes = [P, F]
+        lib.lbs_mlp_get_params.argtypes = [P, F]
+        lib.lbs_mlp_forward.argtypes = [P, P, C.c_int, P]
+        lib.lbs_mlp_loss_grad.argtypes = [P, P, P, C.c_int, D, F]
+        lib.lbs_mlp_adam.argtypes = [P, C.c_float, C.c_float, C.c_float, C.c_float]
+        lib.lbs_mlp_get_stream.argtypes = [P, H]
+        for n in ("lbs_mlp_create", "lbs_mlp_destroy", "lbs_mlp_num_params", "lbs_mlp_set_params",
+                  "lbs_mlp_get_params", "lbs_mlp_forward", "lbs_mlp_loss_grad", "lbs_mlp_adam",
+                  "lbs_mlp_get_stream"):
+            getattr(lib, n).restype = C.c_int
+        lib._mlp_ready = True
+    return lib
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class Mlp:
+    """Device-resident network with FP32 masters, BF16 working copies and Adam state."""
+
+    def __init__(self, sizes=SIZES, max_batch=4096, seed=0):
+        self.lib = _mlp_lib()
+        self.sizes = sizes
+        self.h = C.c_void_p()
+        L._check(self.lib.lbs_mlp_create(C.byref(self.h), sizes[0], sizes[1], sizes[3], max_batch, None))
+        n = C.c_long()
+        L._check(self.lib.lbs_mlp_num_params(self.h, C.byref(n)))
+        self.nparams = n.value
+        self.set_params(self.init_params(seed))
+
+    def init_params(self, seed):
+        """He initialisation of the weights, zero biases, packed FP32."""
+        rng = np.random.Generator(np.random.PCG64(seed))
+        parts = []
+        for a, b in zip(self.sizes[:-1], self.sizes[1:]):
+            parts.append((rng.standard_normal((b, a)) * math.sqrt(2.0 / a)).ravel())
+            parts.append(np.zeros(b))
+        return np.concatenate(parts).astype(np.float32)
+
+    def unpack(self, flat):
+        out, o = {}, 0
+        for i, (a, b) in enumerate(zip(self.sizes[:-1], self.sizes[1:]), start=1):
+            out["W%d" % i] = flat[o:o + a * b].reshape(b, a)
+            o += a * b
+            out["b%d" % i] = flat[o:o + b]
+            o += b
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.nparams
+        L._check(self.lib.lbs_mlp_set_params(self.h, _fptr(flat)))
+
+    def get_params(self):
+        out = np.zeros(self.nparams, dtype=np.float32)
+        L._check(self.lib.lbs_mlp_get_params(self.h, _fptr(out)))
+        return out
+
+    def stream(self):
+        import torch
+        s = C.c_void_p()
+        L._check(self.lib.lbs_mlp_get_stream(self.h, C.byref(s)))
+        return torch.cuda.ExternalStream(s.value)
+
+    def forward(self, x):
+        """x: float32 CUDA tensor [B, n_in] -> y [B, n_out] (on the network's stream)."""
+        import torch
+        x = x.contiguous()
+        y = torch.empty((x.shape[0], self.sizes[-1]), dtype=torch.float32, device=x.device)
+        torch.cuda.current_stream().synchronize()
+        L._check(self.lib.lbs_mlp_forward(self.h, C.c_void_p(x.data_ptr()), x.shape[0],
+                                          C.c_void_p(y.data_ptr())))
+        self.stream().synchronize()
+        return y
+
+    def loss_grad(self, x, t, want_grad=False):
+        g = np.zeros(self.nparams, dtype=np.float32) if want_grad else None
+        loss = C.c_double()
+        torch_sync()
+        L._check(self.lib.lbs_mlp_loss_grad(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()),
+                                            x.shape[0], C.byref(loss), _fptr(g) if want_grad else None))
+        return loss.value, g
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        L._check(self.lib.lbs_mlp_adam(self.h, lr, beta1, beta2, eps))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbs_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def torch_sync():
+    import torch
+    torch.cuda.current_stream().synchronize()
+
+
+# ---------------------------------------------------------------- features ------
+def features(params):
+    """Raw network inputs of a list of instance parameter dicts."""
+    return np.array([[math.log10(p["Kn"]), p["u_w"], p["T_w"], p["Pr"], float(p["visc_law"]),
+                      p["visc_param"]] for p in params], dtype=np.float64)
+
+
+def cell_centres(p):
+    from .lbs import Instance  # noqa: F401  (documentation of the grid convention)
+    Nz, A = p["Nz"], p["A"]
+    s = np.arange(Nz) + 0.5
+    if A == 0.0:
+        return -0.5 + s / Nz
+    E = math.atanh(A)
+    return np.tanh(-E + s * 2 * E / Nz) / (2 * A)
+
+
+ZPTS = -0.5 + (np.arange(NPTS) + 0.5) / NPTS
+
+
+def to_points(prof8, z):
+    """[8, Nz] profiles on cell centres z -> [8 * 64] at the uniform points."""
+    return np.concatenate([np.interp(ZPTS, z, prof8[a]) for a in range(NPROF)])
+
+
+def from_points(v, z):
+    """[8 * 64] -> [8, Nz] on the cell centres z (linear, constant beyond the end points)."""
+    v = v.reshape(NPROF, NPTS)
+    return np.stack([np.interp(z, ZPTS, v[a]) for a in range(NPROF)])
+
+
+# Targets are scaled by the wall speed before standardisation: under u_w -> -u_w the
+# profiles u_x, q_x, P_xz change sign and n, T, q_z, P_xx, P_zz do not, so at leading
+# order they scale as u_w or u_w^2 about the rest state (n = 1, T = T_w, P = T_w).
+_ODD = np.array([False, True, False, True, False, False, True, False])   # n ux T qx qz Pxx Pxz Pzz
+_REST = np.array([1.0, 0.0, 1.0, 0.0, 0.0, 1.0, 0.0, 1.0])
+
+
+def scale_profiles(prof8, p):
+    u = p["u_w"]
+    rest = _REST * np.where(np.arange(NPROF) == 0, 1.0, p["T_w"])
+    fac = np.where(_ODD, u, u * u)
+    return (prof8 - rest[:, None]) / fac[:, None]
+
+
+def unscale_profiles(scaled8, p):
+    u = p["u_w"]
+    rest = _REST * np.where(np.arange(NPROF) == 0, 1.0, p["T_w"])
+    fac = np.where(_ODD, u, u * u)
+    return scaled8 * fac[:, None] + rest[:, None]
+
+
+@dataclasses.dataclass
+class Scaler:
+    mean: np.ndarray
+    std: np.ndarray
+
+    @classmethod
+    def fit(cls, a):
+        s = a.std(0)
+        return cls(a.mean(0), np.where(s > 1e-12, s, 1.0))
+
+    def fwd(self, a):
+        return (a - self.mean) / self.std
+
+    def inv(self, a):
+        return a * self.std + self.mean
+
+
+# ---------------------------------------------------------------- data ----------
+def steady_solves(params, precision=L.LBS_FP32, tol=1e-8, max_steps=200_000, check_every=200, warm=None,
+                  tiling=None):
+    """Solve a batch to R < tol in one handle; returns (profiles [list of 8 x Nz],
+    steps per instance, wall seconds, converged mask)."""
+    import torch
+    s = L.Solver([L.Instance(**p) for p in params], precision=precision)
+    if tiling:
+        s.set_tiling(*tiling)
+    if warm is not None:
+        for b, prof in enumerate(warm):
+            s.init_from_profiles(b, prof)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = s.run_to_steady(tol, max_steps=max_steps, check_every=check_every, raise_on_fail=False)
+    wall = time.perf_counter() - t0
+    res = np.array([s.residual(b) for b in range(len(params))])
+    profs = [s.moments(b) for b in range(len(params))]
+    s.close()
+    profs = [np.stack([m[k] for k in L.MOMENT_NAMES]) for m in profs]
+    return profs, steps, wall, res < tol
+
+
+class WarmStart:
+    """Feature/target scaling plus the network."""
+
+    def __init__(self, seed=0, max_batch=4096):
+        self.net = Mlp(SIZES, max_batch=max_batch, seed=seed)
+        self.xs = self.ys = None
+        self.history = []
+
+    def fit(self, params, profiles, epochs=400, batch=256, lr=2e-3, seed=0, verbose=False):
+        """Train on (params, steady profiles); returns the final training loss."""
+        import torch
+        X = features(params)
+        Y = np.stack([to_points(scale_profiles(pr, p), cell_centres(p)) for p, pr in zip(params, profiles)])
+        self.xs, self.ys = Scaler.fit(X), Scaler.fit(Y)
+        Xd = torch.tensor(self.xs.fwd(X), dtype=torch.float32, device="cuda")
+        Yd = torch.tensor(self.ys.fwd(Y), dtype=torch.float32, device="cuda")
+        rng = np.random.Generator(np.random.PCG64(seed))
+        n = len(params)
+        last = None
+        for ep in range(epochs):
+            perm = torch.tensor(rng.permutation(n), device="cuda")
+            lr_ep = lr * 0.5 * (1 + math.cos(math.pi * ep / epochs))  # cosine decay
+            tot = 0.0
+            for i in range(0, n, batch):
+                idx = perm[i:i + batch]
+                xb, yb = Xd[idx].contiguous(), Yd[idx].contiguous()
+                loss, _ = self.net.loss_grad(xb, yb)
+                self.net.adam(max(lr_ep, 1e-5))
+                tot += loss * len(idx)
+            last = tot / n
+            self.history.append(last)
+            if verbose and ep % 50 == 0:
+                print("epoch %d loss %.3e" % (ep, last), flush=True)
+        return last
+
+    def predict(self, params):
+        """Profiles [8, Nz] on each instance's cells, density rescaled to unit mass."""
+        import torch
+        X = torch.tensor(self.xs.fwd(features(params)), dtype=torch.float32, device="cuda")
+        Y = self.ys.inv(self.net.forward(X).cpu().numpy().astype(np.float64))
+        out = []
+        for p, y in zip(params, Y):
+            z = cell_centres(p)
+            pr = unscale_profiles(from_points(y, z), p)
+            # unit mass and sane floors (the target state must have n > 0 and T > 0)
+            s = np.arange(p["Nz"] + 1)
+            if p["A"] == 0.0:
+                dz = np.full(p["Nz"], 1.0 / p["Nz"])
+            else:
+                E = math.atanh(p["A"])
+                xf = np.tanh(-E + s * 2 * E / p["Nz"]) / (2 * p["A"])
+                dz = np.diff(xf)
+            pr[0] = np.maximum(pr[0], 0.05)
+            pr[0] /= np.sum(pr[0] * dz)
+            pr[2] = np.maximum(pr[2], 0.05 * p["T_w"])
+            out.append(pr)
+        return out
+
+
+# ---------------------------------------------------------------- evaluation ----
+def profile_difference(a, b, p):
+    """max over the 8 profiles of |a - b| on its physical scale: n, T, P on their own
+    maximum, velocities on u_w, heat fluxes on n T^(3/2)."""
+    scale = np.abs(b).max(axis=1)
+    scale[1] = max(scale[1], p["u_w"])
+    scale[3] = scale[4] = float(np.max(b[0] * b[2] ** 1.5))
+    return float(np.max(np.abs(a - b).max(axis=1) / np.maximum(scale, 1e-300)))
+
+
+def evaluate(train_params, eval_params, n_plain=16, tol=1e-8, max_steps=20000, epochs=600, seed=0,
+             precision=L.LBS_FP32, verbose=False):
+    """Train on steady solves of train_params, then time the held-out eval_params to
+    R < tol three ways: one instance at a time from the rest state (a sample of n_plain
+    instances, the plain single-instance solver), all at once from the rest state
+    (batched), and all at once from the network's prediction (batched + warm start).
+    Returns a dict of steps, wall times and the warm/cold profile agreement."""
+    import torch
+    t0 = time.perf_counter()
+    profs, steps, wall_gen, conv = steady_solves(train_params, precision=precision, tol=tol,
+                                                 max_steps=max_steps, check_every=200)
+    keep = [i for i in range(len(train_params)) if conv[i]]
+    ws = WarmStart(seed=seed, max_batch=max(256, len(keep)))
+    t1 = time.perf_counter()
+    loss = ws.fit([train_params[i] for i in keep], [profs[i] for i in keep], epochs=epochs, seed=seed,
+                  verbose=verbose)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    # held out: batched from rest
+    prof_cold, steps_cold, wall_cold, conv_cold = steady_solves(eval_params, precision=precision, tol=tol,
+                                                                max_steps=max_steps, check_every=50)
+    # held out: batched from the network's prediction (inference and seeding timed too)
+    t2 = time.perf_counter()
+    warm = ws.predict(eval_params)
+    t_pred = time.perf_counter() - t2
+    prof_warm, steps_warm, wall_warm, conv_warm = steady_solves(eval_params, precision=precision, tol=tol,
+                                                                max_steps=max_steps, check_every=50,
+                                                                warm=warm)
+    # plain: one instance at a time from rest (sample)
+    plain_walls, plain_steps = [], []
+    for p in eval_params[:n_plain]:
+        _, st, w, c = steady_solves([p], precision=precision, tol=tol, max_steps=max_steps, check_every=50)
+        plain_walls.append(w)
+        plain_steps.append(int(st[0]))
+    both = conv_cold & conv_warm
+    agree = []
+    for b in np.nonzero(both)[0]:
+        agree.append(profile_difference(prof_warm[b], prof_cold[b], eval_params[b]))
+    n = len(eval_params)
+    per_plain = float(np.mean(plain_walls))
+    return {
+        "train": {"instances": len(train_params), "converged": int(conv.sum()),
+                  "steady_solve_wall_s": wall_gen, "fit_wall_s": t_train, "final_loss": loss,
+                  "epochs": epochs},
+        "eval_instances": n,
+        "steps_median": {"cold": float(np.median(steps_cold)), "warm": float(np.median(steps_warm))},
+        "steps_mean": {"cold": float(np.mean(steps_cold)), "warm": float(np.mean(steps_warm))},
+        "converged": {"cold": int(conv_cold.sum()), "warm": int(conv_warm.sum())},
+        "wall_s": {"plain_single_instance_per_instance": per_plain,
+                   "plain_single_instance_extrapolated_all": per_plain * n,
+                   "plain_sample": n_plain,
+                   "batched_cold": wall_cold, "batched_warm": wall_warm + t_pred,
+                   "warm_inference_and_seeding": t_pred},
+        "speedup_vs_plain": {"batched_cold": per_plain * n / wall_cold,
+                             "batched_warm": per_plain * n / (wall_warm + t_pred)},
+        "warm_vs_cold_final_profile_max_rel_diff": max(agree) if agree else None,
+        "total_wall_s": time.perf_counter() - t0,
+    }

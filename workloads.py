@@ -48,6 +48,16 @@ def sweep(n=64, seed=SWEEP_SEED, nz_set=NZ_SET, qx_set=QX_SET, qz_set=QZ_SET):
     return out
 
 
+def warm_start_draws(n, seed):
+    """Draws for training and evaluating the warm-start network: the sweep's
+    distribution restricted to sizes whose steady solves a batch reaches in seconds
+    (Nz in {32, 48, 64}, Qx in {4, 6, 8}, Qz in {4, 8}) and Kn clipped to [0.05, 20]."""
+    ps = sweep(n, seed=seed, nz_set=(32, 48, 64), qx_set=(4, 6, 8), qz_set=(4, 8))
+    for p in ps:
+        p["Kn"] = float(min(max(p["Kn"], 0.05), 20.0))
+    return ps
+
+
 def random_state(shape, seed, amplitude=0.05):
     """Seeded multiplicative perturbation factors 1 + a N(0,1) (for parity inputs)."""
     rng = np.random.Generator(np.random.PCG64(seed))
