@@ -299,6 +299,18 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         }
         D.Dtop = sxt * sy * szm;
         D.Dbot = sxb * sy * szp;
+        // weighted sums of the stored basis tables (exactly delta_l0 before rounding)
+        {
+            const std::vector<double> Hx = rounded<T>(t.Hx), Hy = rounded<T>(t.Hy), Pz = rounded<T>(t.Pz);
+            for (int l = 0; l <= kMaxN; ++l) D.wsum[0][l] = D.wsum[1][l] = D.wsum[2][l] = D.wsum[3][l] = 0.0;
+            for (int l = 0; l <= I.Nx; ++l)
+                for (int i = 0; i < I.Qx; ++i) D.wsum[0][l] += wx[i] * Hx[i * (I.Nx + 1) + l];
+            for (int l = 0; l <= I.Ny; ++l)
+                for (int j = 0; j < I.Qy; ++j) D.wsum[1][l] += wy[j] * Hy[j * (I.Ny + 1) + l];
+            for (int l = 0; l <= I.Nzq; ++l)
+                for (int m = 0; m < I.Qz; ++m) D.wsum[2][l] += wz[m] * Pz[m * (I.Nzq + 1) + l];
+            for (int l = 0; l <= I.Nzq; ++l) D.wsum[3][l] = D.wsum[2][l];
+        }
         // memory layout
         Off& o = off[b];
         const size_t es = sizeof(T);

@@ -233,6 +233,10 @@ __host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize
 // Returns false for a non-finite or non-positive state (a neutral state is
 // written instead).
 // ----------------------------------------------------------------------------
+// Cell record of a macroscopic state: the scalars and the coefficients a_l, b_l
+// of the truncated Hermite equilibrium (Sec. III, Eqs. fyz, Fmn_def), computed in
+// FP64 (the half-range ones cancel strongly for N >= 4).  Returns false for a
+// non-finite or non-positive state (a neutral state is written instead).
 template <typename T>
 __device__ bool write_record(const InstDev& I, int cell, double n, const double* u, double T_, const double* q)
 {
@@ -241,54 +245,51 @@ __device__ bool write_record(const InstDev& I, int cell, double n, const double*
     const double nn = bad ? 1.0 : n, Tc = bad ? 1.0 : T_;
     const double u0 = bad ? 0.0 : u[0], u1 = bad ? 0.0 : u[1], u2 = bad ? 0.0 : u[2];
     T* rec = static_cast<T*>(I.rec) + (size_t)cell * kRecStride;
-    double c[kMaxN + 1];
-    full_coeffs(u0, Tc, I.Nx, c);
-    for (int l = 0; l <= kMaxN; ++l) rec[R_AX + l] = l <= I.Nx ? T(c[l]) : T(0);
-    full_coeffs(u1, Tc, I.Ny, c);
-    for (int l = 0; l <= kMaxN; ++l) rec[R_AY + l] = l <= I.Ny ? T(c[l]) : T(0);
-    half_coeffs(u2, Tc, I.Nzq, I.alpha, I.beta, c);
-    for (int l = 0; l <= kMaxN; ++l) rec[R_BP + l] = l <= I.Nzq ? T(c[l]) : T(0);
-    half_coeffs(-u2, Tc, I.Nzq, I.alpha, I.beta, c);
-    for (int l = 0; l <= kMaxN; ++l) rec[R_BM + l] = l <= I.Nzq ? T(c[l]) : T(0);
     const double tau = relax_time(I.visc_law, I.Kn, I.visc_param, nn, Tc);
+    const double iT = 1.0 / Tc;
     rec[R_N] = T(nn); rec[R_UX] = T(u0); rec[R_UY] = T(u1); rec[R_UZ] = T(u2); rec[R_T] = T(Tc);
     rec[R_QX] = T(bad ? 0.0 : q[0]); rec[R_QY] = T(bad ? 0.0 : q[1]); rec[R_QZ] = T(bad ? 0.0 : q[2]);
     rec[R_ITAU] = T(1.0 / tau);
-    rec[R_CS] = T((1.0 - I.Pr) / (nn * Tc * Tc));
-    rec[R_I5T] = T(1.0 / (5.0 * Tc));
+    rec[R_CS] = T((1.0 - I.Pr) / nn * iT * iT);
+    rec[R_I5T] = T(0.2 * iT);
     // R_SCALE multiplies the x factors so that the discrete equilibrium carries
     // exactly n: in exact arithmetic sum_i wx Gx = 1, sum_j wy Gy = 1 and the sum
     // over both half ranges of wz Gz = 1 (orthogonality of the bases); with
     // coefficients and bases rounded to the storage type the sums miss by a few
     // ulps of the same sign every step, which would let FP32 runs drift in mass.
-    // The factors are evaluated here exactly as the stage kernel evaluates them.
-    typedef typename Acc<T>::type A;
-    A sx = 0, sy = 0, sz = 0;
-    for (int i = 0; i < I.Qx; ++i) {
-        T g = 0;
-        for (int l = 0; l <= I.Nx; ++l) g += rec[R_AX + l] * ld<T>(I.Hx, i * (I.Nx + 1) + l);
-        sx += A(ld<T>(I.wx, i)) * A(g);
+    // The sums are sum_l c_l W_l with the stored coefficients c_l and the
+    // weighted sums W_l of the stored basis tables (computed at set-up).
+    double c[kMaxN + 1], cm[kMaxN + 1], s[3];
+    full_coeffs(u0, Tc, I.Nx, c);
+    s[0] = 0.0;
+    for (int l = 0; l <= kMaxN; ++l) {
+        const T v = l <= I.Nx ? T(c[l]) : T(0);
+        rec[R_AX + l] = v;
+        if (l <= I.Nx) s[0] += double(v) * I.wsum[0][l];
     }
-    for (int j = 0; j < I.Qy; ++j) {
-        T g = 0;
-        for (int l = 0; l <= I.Ny; ++l) g += rec[R_AY + l] * ld<T>(I.Hy, j * (I.Ny + 1) + l);
-        sy += A(ld<T>(I.wy, j)) * A(g);
+    full_coeffs(u1, Tc, I.Ny, c);
+    s[1] = 0.0;
+    for (int l = 0; l <= kMaxN; ++l) {
+        const T v = l <= I.Ny ? T(c[l]) : T(0);
+        rec[R_AY + l] = v;
+        if (l <= I.Ny) s[1] += double(v) * I.wsum[1][l];
     }
-    for (int zm = 0; zm < 2 * I.Qz; ++zm) {
-        const int sg = zm >= I.Qz, m = zm - sg * I.Qz;
-        const T* b = rec + (sg ? R_BM : R_BP);
-        T g = 0;
-        for (int l = 0; l <= I.Nzq; ++l) g += b[l] * ld<T>(I.Pz, m * (I.Nzq + 1) + l);
-        sz += A(ld<T>(I.wz, m)) * A(g);
+    half_coeffs_pm(u2, Tc, I.Nzq, I.alpha, I.beta, c, cm);
+    s[2] = 0.0;
+    for (int l = 0; l <= kMaxN; ++l) {
+        const T vp = l <= I.Nzq ? T(c[l]) : T(0), vm = l <= I.Nzq ? T(cm[l]) : T(0);
+        rec[R_BP + l] = vp;
+        rec[R_BM + l] = vm;
+        if (l <= I.Nzq) s[2] += double(vp) * I.wsum[2][l] + double(vm) * I.wsum[3][l];
     }
-    rec[R_SCALE] = T(A(nn) / (sx * sy * sz));
+    rec[R_SCALE] = T(nn / (s[0] * s[1] * s[2]));
     return !bad;
 }
 
 // One cell (one thread): FP64 sum of the per-chunk moment partials (written by
-// other CTAs of this launch, hence read past L1), then n, u, P, T, q
-// (Eq. qdef) from the raw moments, the profiles, W for the residual, and the
-// cell record of the next stage.
+// other CTAs of this launch, hence read past L1), n, u, P, T, q (Eq. qdef) from
+// the raw moments, the profiles, W for the residual, and the cell record of the
+// next stage.
 template <typename T>
 __device__ void finalize_cell(const InstDev& I, int cell)
 {
@@ -298,13 +299,13 @@ __device__ void finalize_cell(const InstDev& I, int cell)
     for (int c = 0; c < I.nchunks; ++c)
 #pragma unroll
         for (int a = 0; a < kNMom; ++a) mom[a] += __ldcg(I.partial + ((size_t)c * kNMom + a) * Nz + cell);
-    const double n = mom[0];
-    const double u[3] = {mom[1] / n, mom[2] / n, mom[3] / n};
+    const double n = mom[0], in = 1.0 / n;
+    const double u[3] = {mom[1] * in, mom[2] * in, mom[3] * in};
     // central second moments P_ab = sum p_a p_b f - n u_a u_b
     const double Pxx = mom[4] - n * u[0] * u[0], Pyy = mom[5] - n * u[1] * u[1];
     const double Pzz = mom[6] - n * u[2] * u[2], Pxy = mom[7] - n * u[0] * u[1];
     const double Pxz = mom[8] - n * u[0] * u[2], Pyz = mom[9] - n * u[1] * u[2];
-    const double T_ = (Pxx + Pyy + Pzz) / (3.0 * n);
+    const double T_ = (Pxx + Pyy + Pzz) * (1.0 / 3.0) * in;
     // q_a = 1/2 sum |xi|^2 xi_a f with xi = p - u, expanded in raw moments
     const double M2[3][3] = {{mom[4], mom[7], mom[8]}, {mom[7], mom[5], mom[9]}, {mom[8], mom[9], mom[6]}};
     const double tr = mom[4] + mom[5] + mom[6];
@@ -595,7 +596,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     }
     const T dt = T(I.dt);
     T* outp = Fout + (size_t)z0 * Q + k0;
-#pragma unroll 2
+#pragma unroll 1  // unrolling the z-march only adds instruction-cache misses
     for (int c = 0; c < zn; ++c) {
         const T* sc = recs + (size_t)c * kRecStride;
         const T* gc = gsm + c * G;
@@ -625,6 +626,8 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 const T xq = ex * qx + ey * qy + ez * qz;
                 const T S = cS * (xi2 * i5T - T(1)) * xq;
                 const T geq = gc[ii[v]] * gc[Qx + jj[v]] * gc[Qx + Qy + zz[v] - zm_lo];
+                // the advection and relaxation increments nearly cancel near a steady
+                // state: combine them first, then add to f once
                 const T Lv = -(flp - flm[v]) * idz - (f - geq * (T(1) + S)) * itau;
                 const T f1 = f + dt * Lv;
                 // Shu-Osher combine written as F_l + b (f1 - F_l): identical to
@@ -719,7 +722,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
 
 // ---- separate finalisation launches (used when the stage kernel does not fuse them)
 template <typename T>
-__global__ void __launch_bounds__(64) finalize_cells(const InstDev* __restrict__ insts)
+__global__ void __launch_bounds__(32) finalize_cells(const InstDev* __restrict__ insts)
 {
     const InstDev& I = insts[blockIdx.y];
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -791,7 +794,7 @@ static cudaError_t launch_stage_v(int stage, const InstDev* d, const Tile* t, in
 template <typename T>
 static cudaError_t launch_finalize_t(int stage, const InstDev* d_inst, int ninst, int maxNz, cudaStream_t st)
 {
-    finalize_cells<T><<<dim3((maxNz + 63) / 64, ninst), 64, 0, st>>>(d_inst);
+    finalize_cells<T><<<dim3((maxNz + 31) / 32, ninst), 32, 0, st>>>(d_inst);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     finalize_inst<<<ninst, 128, 0, st>>>(d_inst, stage);

@@ -38,6 +38,8 @@ struct InstDev {
     int visc_law;
     double Kn, visc_param, Pr, dt, tol;
     double Dtop, Dbot;            // sum over incoming velocities of w p_z Gw (n_w = 1)
+    double wsum[4][kMaxN + 1];    // sum_i w_i basis_l(p_i) of the stored (rounded) tables:
+                                  // x, y, z (p_z > 0), z (p_z < 0); 1, 0, 0, ... exactly
     double ext_top[2][3];         // ghost Nz+1 <- (Nz, Nz-1, Nz-2); Nz+2 <- (Nz+1, Nz, Nz-1)
     double ext_bot[2][3];         // ghost 0 <- (1, 2, 3); ghost -1 <- (0, 1, 2)
     // tables
@@ -97,10 +99,48 @@ LBS_HD void half_coeffs(double u, double T, int N, const double* alpha, const do
     for (int l = 0; l <= N; ++l) b[l] = J[l][0];
 }
 
+// Both half-range coefficient sets at once: bp for u, bm for -u (the p_z < 0 half
+// range, written in xi = -p_z >= 0).  The two share g(0) and, through
+// erfc(x) + erfc(-x) = 2, one erfc: the one of |x| is evaluated (no cancellation)
+// and the other is 2 minus it (a value in [1, 2], exact to an ulp).
+LBS_HD void half_coeffs_pm(double u, double T, int N, const double* alpha, const double* beta,
+                           double* bp, double* bm)
+{
+    double Jp[kMaxN + 1][kMaxN + 1], Jm[kMaxN + 1][kMaxN + 1];
+    const int K = N;
+    const double iT = 1.0 / T, r2T = sqrt(0.5 * iT);
+    const double g0 = exp(-0.5 * u * u * iT) * (r2T * (1.0 / sqrt(M_PI)));
+    const double e = erfc(fabs(u) * r2T);  // erfc of the non-negative argument
+    Jp[0][0] = u >= 0.0 ? 1.0 - 0.5 * e : 0.5 * e;  // erfc(-u / sqrt(2T)) / 2
+    Jm[0][0] = u >= 0.0 ? 0.5 * e : 1.0 - 0.5 * e;  // erfc(u / sqrt(2T)) / 2
+    if (K >= 1) {
+        Jp[0][1] = u * Jp[0][0] + T * g0;
+        Jm[0][1] = -u * Jm[0][0] + T * g0;
+    }
+    for (int k = 1; k < K; ++k) {
+        Jp[0][k + 1] = u * Jp[0][k] + k * T * Jp[0][k - 1];
+        Jm[0][k + 1] = -u * Jm[0][k] + k * T * Jm[0][k - 1];
+    }
+    for (int l = 0; l < N; ++l)
+        for (int k = 0; k + l + 1 <= K; ++k) {
+            Jp[l + 1][k] = Jp[l][k + 1] - alpha[l] * Jp[l][k] - (l > 0 ? beta[l] * Jp[l - 1][k] : 0.0);
+            Jm[l + 1][k] = Jm[l][k + 1] - alpha[l] * Jm[l][k] - (l > 0 ? beta[l] * Jm[l - 1][k] : 0.0);
+        }
+    for (int l = 0; l <= N; ++l) {
+        bp[l] = Jp[l][0];
+        bm[l] = Jm[l][0];
+    }
+}
+
 // relaxation time: power law tau = Kn T^(omega-1)/n, Sutherland tau = Kn sqrt(T)(1+S)/(n(T+S))
 LBS_HD double relax_time(int law, double Kn, double param, double n, double T)
 {
-    if (law == 0) return Kn * pow(T, param - 1.0) / n;
+    if (law == 0) {
+        // the hard-sphere and Maxwell-molecule exponents without a general pow
+        if (param == 1.0) return Kn / n;
+        if (param == 0.5) return Kn / (n * sqrt(T));
+        return Kn * pow(T, param - 1.0) / n;
+    }
     return Kn * sqrt(T) * (1.0 + param) / (n * (T + param));
 }
 
