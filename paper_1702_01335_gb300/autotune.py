@@ -1,8 +1,9 @@
 """Tile autotuner for the stage kernel.
 
 The stage kernel's work decomposition (velocities per thread V, cells per
-z-tile ZT, finalisation folded into the stage kernel or launched apart) changes how many CTAs fit on an SM, how much halo is re-read and how
-the per-cell moment reduction is amortised; it does not change the arithmetic.
+z-tile ZT, finalisation folded into the stage kernel or launched apart) changes
+how many CTAs fit on an SM, how much halo is re-read and how the per-cell
+moment reduction is amortised; it does not change the arithmetic.
 `autotune(solver)` times every candidate with CUDA events on a scratch solver
 built from the same instances (so the caller's state and step counters are not
 touched), applies the fastest tiling to `solver`, and caches the choice per
@@ -68,6 +69,8 @@ def autotune(solver, candidates=CANDIDATES, steps=3, cache_file=None, verbose=Fa
                 print(table[-1], flush=True)
     finally:
         scratch.close()
+    if not table:
+        raise ValueError("no valid tiling among the candidates")
     best = min(table, key=lambda r: r["ms_per_step"])
     res = {"V": best["V"], "ZT": best["ZT"], "fuse": best["fuse"], "ms_per_step": best["ms_per_step"],
            "table": table}

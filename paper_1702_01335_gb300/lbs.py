@@ -56,7 +56,11 @@ EXPORTS = ("lbs_create", "lbs_batch_create", "lbs_destroy", "lbs_step", "lbs_run
            "lbs_moments", "lbs_profiles", "lbs_residual", "lbs_steps_taken", "lbs_info",
            "lbs_get_state", "lbs_set_state", "lbs_init_from_profiles", "lbs_quadrature",
            "lbs_get_stream", "lbs_profile_steps", "lbs_moments_static", "lbs_set_tiling",
-           "lbs_get_tiling", "lbs_last_error")
+           "lbs_get_tiling", "lbs_last_error",
+           # the warm-start network (bound in warmstart.py)
+           "lbs_mlp_create", "lbs_mlp_destroy", "lbs_mlp_num_params", "lbs_mlp_set_params",
+           "lbs_mlp_get_params", "lbs_mlp_forward", "lbs_mlp_loss_grad", "lbs_mlp_adam",
+           "lbs_mlp_get_stream")
 
 
 def load(build_if_missing=True):

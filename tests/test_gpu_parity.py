@@ -202,8 +202,9 @@ def test_autotuner_picks_a_valid_tiling():
     from paper_1702_01335_gb300.autotune import autotune
     s = solver_of([W.C1] * 4, 0.004, P.LBS_FP32)
     before = s.get_state(0)
-    r = autotune(s, candidates=((1, 8, 1), (2, 16, 0)), steps=2)
+    r = autotune(s, candidates=((1, 8, 1), (2, 16, 0), (4, 99, 0)), steps=2)  # the last one is invalid
     assert (r["V"], r["ZT"], r["fuse"]) in ((1, 8, 1), (2, 16, 0))
+    assert len(r["table"]) == 2
     assert s.tiling()["V"] == r["V"]
     assert np.array_equal(s.get_state(0), before)  # tuning ran on a scratch solver
     assert s.steps_taken() == 0
