@@ -157,6 +157,19 @@ def time_to_steady():
         return {"error": "%s: %s" % (type(e).__name__, e)}
 
 
+def whole_job(local_time, units_per_rank, dist=None, device="cpu"):
+    """Whole-job rate of a run in which every rank processed units_per_rank units in
+    local_time: (the slowest rank's time, all ranks' units / that time)."""
+    import torch
+    t = torch.tensor([float(local_time)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    slowest = float(t.item())
+    return slowest, units_per_rank * world / slowest
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -231,11 +244,8 @@ def main():
         e1.record(st)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = upd_step * world * a.steps / (ms_max * 1e-3)
+    s_max, value = whole_job(ms * 1e-3, upd_step * a.steps, dist, device="cuda")
+    ms_max = s_max * 1e3
 
     # ---- roofline of the stage kernels (live CUDA events, same stream)
     nprof = max(3, min(200, a.steps // 10))
@@ -258,10 +268,7 @@ def main():
         s.moments_all_ptr(out_host.data_ptr())
     barrier()
     e2e_s = time.perf_counter() - t0
-    tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_value = upd_step * world * e2e_steps / float(tt.item())
+    _, e2e_value = whole_job(e2e_s, upd_step * e2e_steps, dist, device="cuda")
 
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")

@@ -11,6 +11,7 @@ batch signature (precision and the (Nz, Q) of every instance) in memory and,
 optionally, in a JSON file.
 """
 import hashlib
+import itertools
 import json
 import os
 
@@ -32,8 +33,11 @@ def kernel_hash():
 
 
 def signature(solver):
+    """Kernel hash, precision and the (Nz, Q) of the batch's instances, run-length
+    encoded ("256*128x2048")."""
+    runs = [(k, len(list(g))) for k, g in itertools.groupby("%dx%d" % (i.Nz, i.Q) for i in solver.instances)]
     return "%s:p%d:" % (kernel_hash(), solver.precision) + ",".join(
-        "%dx%d" % (i.Nz, i.Q) for i in solver.instances)
+        ("%d*%s" % (n, k)) if n > 1 else k for k, n in runs)
 
 
 def _load(path):
