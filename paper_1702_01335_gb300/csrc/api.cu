@@ -77,6 +77,11 @@ struct lbs_solver {
     size_t smem = 0;
     unsigned char* pool = nullptr;
     double* d_macro = nullptr;  // [8][maxNz] staging for warm starts
+    // every instance's profiles ([14][Nz] each) and status word, back to back in
+    // instance order: whole-batch reads are one copy each
+    double* prof_all = nullptr;
+    size_t prof_all_n = 0;
+    int* status_all = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0;
     int device = 0;
@@ -321,15 +326,39 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         o.gxt = pool.take(I.Qx * es); o.gxb = pool.take(I.Qx * es); o.gwy = pool.take(I.Qy * es);
         o.gwz = pool.take(2 * I.Qz * es); o.idz = pool.take(Nz * es);
         const size_t nf = (size_t)Nz * I.Q;
-        o.F0 = pool.take(nf * es); o.F1 = pool.take(nf * es); o.F2 = pool.take(nf * es);
+        o.F1 = pool.take(nf * es); o.F2 = pool.take(nf * es);  // F0: below
         o.rec = pool.take((size_t)Nz * kRecStride * es);
         const size_t maxch = (I.Q + kThreads - 1) / kThreads;  // chunks at V = 1, the finest tiling
         o.partial = pool.take(maxch * Nz * kNMom * 8);
         o.flux = pool.take(maxch * 2 * 8);
-        o.nw = pool.take(2 * 8); o.prof = pool.take(14 * (size_t)Nz * 8);
+        o.nw = pool.take(2 * 8);  // prof: below
         o.Wold = pool.take(3 * (size_t)Nz * 8); o.Wnew = pool.take(3 * (size_t)Nz * 8);
-        o.res = pool.take(8); o.steps = pool.take(8); o.active = pool.take(4); o.status = pool.take(4);
+        o.res = pool.take(8); o.steps = pool.take(8); o.active = pool.take(4);  // status: below
         o.zcount = pool.take(4 * (size_t)std::max(1, Nz / 3)); o.icount = pool.take(4);
+    }
+    // F0 of every instance back to back, each rounded up to 256 bytes so that every
+    // state starts aligned.  Where the rounding adds nothing (states of a multiple of
+    // 256 bytes, such as C2's 1 MiB), a whole-batch lbs_get_state / lbs_set_state is one
+    // copy.  Profiles and status words are packed.
+    size_t prof_base = 0, status_base = 0;
+    {
+        size_t f0_total = 0, prof_total = 0;
+        for (int b = 0; b < h->ninst; ++b) {
+            f0_total += ((size_t)h->ih[b].Nz * h->ih[b].Q * sizeof(T) + 255) & ~size_t(255);
+            prof_total += 14 * (size_t)h->ih[b].Nz;
+        }
+        const size_t f0_base = pool.take(f0_total);
+        prof_base = pool.take(prof_total * 8);
+        status_base = pool.take(4 * (size_t)h->ninst);
+        h->prof_all_n = prof_total;
+        size_t fo = 0, po = 0;
+        for (int b = 0; b < h->ninst; ++b) {
+            off[b].F0 = f0_base + fo;
+            fo += ((size_t)h->ih[b].Nz * h->ih[b].Q * sizeof(T) + 255) & ~size_t(255);
+            off[b].prof = prof_base + 8 * po;
+            po += 14 * (size_t)h->ih[b].Nz;
+            off[b].status = status_base + 4 * (size_t)b;
+        }
     }
     const size_t inst_off = pool.take(sizeof(InstDev) * h->ninst);
     size_t max_tiles = 0;  // tiles of the finest tiling (V = 1, 3-cell z-tiles)
@@ -387,6 +416,8 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
     h->d_inst = reinterpret_cast<InstDev*>(P + inst_off);
     h->d_tiles = reinterpret_cast<Tile*>(P + tile_off);
     h->d_macro = reinterpret_cast<double*>(P + macro_off);
+    h->prof_all = reinterpret_cast<double*>(P + prof_base);
+    h->status_all = reinterpret_cast<int*>(P + status_base);
     h->ntiles = (int)tiles.size();
     CK(cudaMemcpyAsync(P, img.data(), pool.bytes, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -439,8 +470,7 @@ static lbs_status get_graph(lbs_solver* h, int nsteps)
 static lbs_status check_status(lbs_solver* h)
 {
     std::vector<int> st(h->ninst);
-    for (int b = 0; b < h->ninst; ++b)
-        CK(cudaMemcpyAsync(&st[b], h->idev[b].status, 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(st.data(), h->status_all, 4 * (size_t)h->ninst, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     for (int b = 0; b < h->ninst; ++b)
         if (st[b]) return fail(LBS_ERR_NONFINITE, "instance " + std::to_string(b) + " reached a non-finite or non-positive state");
@@ -691,12 +721,17 @@ lbs_status lbs_profiles(lbs_handle h, int inst, double* host_out)
 
 lbs_status lbs_moments(lbs_handle h, int inst, double* host_out)
 {
-    if (h && inst == -1 && host_out) {
-        size_t off = 0;
+    if (h && inst == -1 && host_out) {  // every instance: one copy of the packed profiles
+        std::vector<double> all(h->prof_all_n);
+        CK(cudaMemcpyAsync(all.data(), h->prof_all, 8 * h->prof_all_n, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        const int rows[8] = {0, 1, 4, 5, 7, 8, 12, 10};  // n, u_x, T, q_x, q_z, P_xx, P_xz, P_zz
+        size_t in = 0, out = 0;
         for (int b = 0; b < h->ninst; ++b) {
-            lbs_status s = lbs_moments(h, b, host_out + off);
-            if (s != LBS_OK) return s;
-            off += 8 * (size_t)h->ih[b].Nz;
+            const size_t Nz = h->ih[b].Nz;
+            for (int r = 0; r < 8; ++r) std::memcpy(host_out + out + r * Nz, all.data() + in + rows[r] * Nz, 8 * Nz);
+            in += 14 * Nz;
+            out += 8 * Nz;
         }
         return LBS_OK;
     }
@@ -753,12 +788,21 @@ lbs_status lbs_get_state(lbs_handle h, int inst, void* dst, int to_host)
 {
     if (!h || inst < -1 || inst >= h->ninst) return fail(LBS_ERR_ARG, "invalid handle or instance index");
     if (!dst) return fail(LBS_ERR_ARG, "null destination");
+    const int b0 = inst < 0 ? 0 : inst, b1 = inst < 0 ? h->ninst : inst + 1;
     size_t off = 0;
-    for (int b = (inst < 0 ? 0 : inst); b < (inst < 0 ? h->ninst : inst + 1); ++b) {
-        const size_t bytes = (size_t)h->ih[b].Nz * h->ih[b].Q * h->esize;
-        CK(cudaMemcpyAsync(static_cast<unsigned char*>(dst) + off, h->idev[b].F0, bytes,
+    for (int b = b0; b < b1;) {
+        // a run of instances whose states are adjacent on the device: one copy
+        unsigned char* d = static_cast<unsigned char*>(h->idev[b].F0);
+        size_t bytes = 0;
+        int e = b;
+        do {
+            bytes += (size_t)h->ih[e].Nz * h->ih[e].Q * h->esize;
+            ++e;
+        } while (e < b1 && static_cast<unsigned char*>(h->idev[e].F0) == d + bytes);
+        CK(cudaMemcpyAsync(static_cast<unsigned char*>(dst) + off, d, bytes,
                            to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
         off += bytes;
+        b = e;
     }
     CK(cudaStreamSynchronize(h->stream));
     return LBS_OK;
@@ -768,12 +812,21 @@ lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host)
 {
     if (!h || inst < -1 || inst >= h->ninst) return fail(LBS_ERR_ARG, "invalid handle or instance index");
     if (!src) return fail(LBS_ERR_ARG, "null source");
+    const int b0 = inst < 0 ? 0 : inst, b1 = inst < 0 ? h->ninst : inst + 1;
     size_t off = 0;
-    for (int b = (inst < 0 ? 0 : inst); b < (inst < 0 ? h->ninst : inst + 1); ++b) {
-        const size_t bytes = (size_t)h->ih[b].Nz * h->ih[b].Q * h->esize;
-        CK(cudaMemcpyAsync(h->idev[b].F0, static_cast<const unsigned char*>(src) + off, bytes,
+    for (int b = b0; b < b1;) {
+        // a run of instances whose states are adjacent on the device: one copy
+        unsigned char* d = static_cast<unsigned char*>(h->idev[b].F0);
+        size_t bytes = 0;
+        int e = b;
+        do {
+            bytes += (size_t)h->ih[e].Nz * h->ih[e].Q * h->esize;
+            ++e;
+        } while (e < b1 && static_cast<unsigned char*>(h->idev[e].F0) == d + bytes);
+        CK(cudaMemcpyAsync(d, static_cast<const unsigned char*>(src) + off, bytes,
                            from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
         off += bytes;
+        b = e;
     }
     lbs_status s = analyse(h);
     if (s != LBS_OK) return s;
