@@ -20,7 +20,7 @@ from .lbs import LbsError, Solver
 _CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
 
-CANDIDATES = tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (4, 6, 8, 12, 16, 24, 32) for F in (0, 1))
+CANDIDATES = tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (4, 6, 8, 12, 16, 24, 32) for F in (0, 1, 2))
 _cache = {}
 
 

@@ -84,6 +84,10 @@ struct lbs_solver {
     int* status_all = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0;
+    // split stepping (fuse = 2): instances [0, nA) on stream, [nA, ninst) on stream2
+    int nA = 0, ntilesA = 0;
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
 };
 
@@ -187,6 +191,23 @@ static void build_tiles(lbs_solver* h, std::vector<Tile>& tiles)
         }
     }
     h->smem = smem;
+    // split point of the batch for fuse = 2: about half the tiles on each side
+    h->nA = 0;
+    h->ntilesA = 0;
+    if (h->ninst >= 2) {
+        size_t t = 0;
+        int b = 0;
+        while (b < h->ninst - 1) {
+            size_t tb = 0;
+            for (const Tile& x : tiles)
+                if (x.inst == b) ++tb;
+            if (2 * (t + tb) > tiles.size() && b > 0) break;
+            t += tb;
+            ++b;
+        }
+        h->nA = b;
+        h->ntilesA = (int)t;
+    }
 }
 
 template <typename T>
@@ -427,15 +448,37 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
 // moments, records, wall densities and W_old of the current F0 (every active instance)
 static lbs_status analyse(lbs_solver* h)
 {
-    CK(launch_stage(h->fp32, h->V, 0, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse, h->ninst, h->maxNz, h->stream));
+    CK(launch_stage(h->fp32, h->V, 0, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->ninst, h->maxNz,
+                    h->stream));
     return LBS_OK;
 }
 
+// fuse = 2: the batch's two halves advance on two streams, each with its own
+// (unfused) finalisation, so that one half's FP64 finalisation overlaps the other
+// half's stage kernel; the step forks from and joins back into the handle's stream
+static bool split(const lbs_solver* h) { return h->fuse == 2 && h->nA > 0 && h->stream2; }
+
 static lbs_status enqueue_step(lbs_solver* h)
 {
-    for (int s = 1; s <= 3; ++s) {
-        CK(launch_stage(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse, h->ninst, h->maxNz, h->stream));
+    if (!split(h)) {
+        for (int s = 1; s <= 3; ++s)
+            CK(launch_stage(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->ninst,
+                            h->maxNz, h->stream));
+        return LBS_OK;
     }
+    CK(cudaEventRecord(h->ev_fork, h->stream));
+    CK(cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));
+    // the stage kernel finds a tile's instance by its absolute index (full descriptor
+    // array, a range of tiles); the finalisation kernels take a range of instances
+    for (int s = 1; s <= 3; ++s) {
+        CK(launch_stage_only(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntilesA, h->smem, 0, h->stream));
+        CK(launch_finalize(h->fp32, s, h->d_inst, h->nA, h->maxNz, h->stream));
+        CK(launch_stage_only(h->fp32, h->V, s, h->d_inst, h->d_tiles + h->ntilesA, h->ntiles - h->ntilesA, h->smem,
+                             0, h->stream2));
+        CK(launch_finalize(h->fp32, s, h->d_inst + h->nA, h->ninst - h->nA, h->maxNz, h->stream2));
+    }
+    CK(cudaEventRecord(h->ev_join, h->stream2));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     return LBS_OK;
 }
 
@@ -556,6 +599,9 @@ lbs_status lbs_destroy(lbs_handle h)
     drop_graph(h);
     if (h->pool) cudaFree(h->pool);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (h->stream2) cudaStreamDestroy(h->stream2);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
     return LBS_OK;
 }
@@ -626,12 +672,29 @@ lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms)
     for (auto& e : ev) CK(cudaEventCreate(&e));
     double tstage = 0.0, tfin = 0.0, tstep = 0.0;
     lbs_status st = LBS_OK;
+    if (split(h)) {  // stage kernels overlap the other half's finalisation: whole steps only
+        for (long it = 0; it < nsteps && st == LBS_OK; ++it) {
+            CK(cudaEventRecord(ev[0], h->stream));
+            st = enqueue_step(h);
+            CK(cudaEventRecord(ev[6], h->stream));
+            CK(cudaEventSynchronize(ev[6]));
+            float w = 0.f;
+            CK(cudaEventElapsedTime(&w, ev[0], ev[6]));
+            tstep += w;
+        }
+        for (auto& e : ev) cudaEventDestroy(e);
+        if (st != LBS_OK) return st;
+        out_ms[0] = tstep;
+        out_ms[1] = 0.0;
+        out_ms[2] = tstep;
+        return check_status(h);
+    }
     for (long it = 0; it < nsteps && st == LBS_OK; ++it) {
         CK(cudaEventRecord(ev[0], h->stream));
         for (int s = 1; s <= 3; ++s) {
-            CK(launch_stage_only(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse, h->stream));
+            CK(launch_stage_only(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->stream));
             CK(cudaEventRecord(ev[2 * s - 1], h->stream));
-            if (!h->fuse) CK(launch_finalize(h->fp32, s, h->d_inst, h->ninst, h->maxNz, h->stream));
+            if (!(h->fuse & 1)) CK(launch_finalize(h->fp32, s, h->d_inst, h->ninst, h->maxNz, h->stream));
             CK(cudaEventRecord(ev[2 * s], h->stream));
         }
         CK(cudaEventSynchronize(ev[6]));
@@ -655,10 +718,15 @@ lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms)
 
 lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT, int fuse)
 {
-    if (!h || (V != 1 && V != 2 && V != 4) || ZT < 3 || ZT > kMaxZT || (fuse != 0 && fuse != 1))
-        return fail(LBS_ERR_ARG, "tiling needs V in {1, 2, 4}, 3 <= ZT <= 64 and fuse in {0, 1}");
+    if (!h || (V != 1 && V != 2 && V != 4) || ZT < 3 || ZT > kMaxZT || fuse < 0 || fuse > 2)
+        return fail(LBS_ERR_ARG, "tiling needs V in {1, 2, 4}, 3 <= ZT <= 64 and fuse in {0, 1, 2}");
     CK(cudaStreamSynchronize(h->stream));
     drop_graph(h);
+    if (fuse == 2 && !h->stream2) {
+        CK(cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
     h->V = V;
     h->ZT = ZT;
     h->fuse = fuse;

@@ -70,13 +70,20 @@ def test_fp32_profiles_match_oracle(params):
     assert max(errs.values()) < FP32_TOL, "profile errors: " + repr(sorted(errs.items(), key=lambda kv: -kv[1]))
 
 
-def test_batch_of_uneven_instances_matches_single_runs():
-    """A batch of instances of different Nz, Q and gas laws equals each run alone."""
+@pytest.mark.parametrize("fuse", [None, 2])
+def test_batch_of_uneven_instances_matches_single_runs(fuse):
+    """A batch of instances of different Nz, Q and gas laws equals each run alone, also
+    when its two halves step on two streams (fuse = 2; 15 steps: one 8-step graph and
+    7 directly launched steps)."""
     P = _lbs()
     ps = W.sweep(5, seed=11, nz_set=(6, 17, 24), qx_set=(3, 4, 6), qz_set=(2, 4, 5))
     dts = [oracle_of(p, None).dt for p in ps]
     dt = min(dts)
     s = solver_of(ps, dt, P.LBS_FP64)
+    if fuse is not None:
+        t = s.tiling()
+        s.set_tiling(t["V"], t["ZT"], fuse)
+        assert s.tiling()["fuse"] == fuse
     s.step(15)
     for b, p in enumerate(ps):
         o = oracle_of(p, dt)
