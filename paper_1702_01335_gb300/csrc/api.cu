@@ -45,7 +45,7 @@ namespace {
 
 struct InstHost {
     lbs_instance_desc d;
-    int Nz, Q, Qx, Qy, Qz, Nx, Ny, Nzq, nchunks, nzm_max, nzt;
+    int Nz, Q, Qx, Qy, Qz, Nx, Ny, Nzq, nchunks, nchh, nzm_max, nzt;
     double dt;
     std::vector<double> xc, xf;  // cell centres (s = -3..Nz+2, 0-based), interfaces
 };
@@ -163,10 +163,15 @@ static void build_tiles(lbs_solver* h, std::vector<Tile>& tiles)
     size_t smem = 0;
     for (int b = 0; b < h->ninst; ++b) {
         InstHost& I = h->ih[b];
-        I.nchunks = (I.Q + KC - 1) / KC;
+        // chunks never straddle p_z = 0: nchh chunks per half range of Q / 2 velocities,
+        // so that each CTA marches its velocities in their common upwind direction
+        const int Qh = I.Q / 2;
+        I.nchh = (Qh + KC - 1) / KC;
+        I.nchunks = 2 * I.nchh;
         int nzm_max = 0;
         for (int c = 0; c < I.nchunks; ++c) {
-            const int k0 = c * KC, k1 = std::min(I.Q, k0 + KC) - 1;
+            const int sg = c / I.nchh, k0 = sg * Qh + (c - sg * I.nchh) * KC;
+            const int k1 = std::min((sg + 1) * Qh, k0 + KC) - 1;
             nzm_max = std::max(nzm_max, k1 / (I.Qx * I.Qy) - k0 / (I.Qx * I.Qy) + 1);
         }
         I.nzm_max = nzm_max;
@@ -304,7 +309,9 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         D.Nz = Nz; D.Qx = I.Qx; D.Qy = I.Qy; D.Qz = I.Qz; D.Q = I.Q; D.QxQy = I.Qx * I.Qy;
         D.Nx = I.Nx; D.Ny = I.Ny; D.Nzq = I.Nzq;
         D.nchunks = I.nchunks;
-        D.bulk = ((size_t)I.Q * sizeof(T)) % 16 == 0;  // every row segment starts on 16 bytes
+        D.nchh = I.nchh;
+        // every row segment (row s, chunk start k0 in either half) starts on 16 bytes
+        D.bulk = ((size_t)(I.Q / 2) * sizeof(T)) % 16 == 0;
         D.visc_law = d.visc.law; D.Kn = d.Kn; D.visc_param = d.visc.omega_or_S; D.Pr = d.Pr;
         D.dt = I.dt; D.tol = 0.0;
         const std::vector<double>& xc = I.xc;  // xc[s + 3]
@@ -349,7 +356,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         const size_t nf = (size_t)Nz * I.Q;
         o.F1 = pool.take(nf * es); o.F2 = pool.take(nf * es);  // F0: below
         o.rec = pool.take((size_t)Nz * kRecStride * es);
-        const size_t maxch = (I.Q + kThreads - 1) / kThreads;  // chunks at V = 1, the finest tiling
+        const size_t maxch = 2 * ((I.Q / 2 + kThreads - 1) / kThreads);  // chunks at V = 1, the finest tiling
         o.partial = pool.take(maxch * Nz * kNMom * 8);
         o.flux = pool.take(maxch * 2 * 8);
         o.nw = pool.take(2 * 8);  // prof: below
@@ -384,7 +391,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
     const size_t inst_off = pool.take(sizeof(InstDev) * h->ninst);
     size_t max_tiles = 0;  // tiles of the finest tiling (V = 1, 3-cell z-tiles)
     for (int b = 0; b < h->ninst; ++b)
-        max_tiles += (size_t)((h->ih[b].Q + kThreads - 1) / kThreads) * std::max(1, h->ih[b].Nz / 3);
+        max_tiles += (size_t)(2 * ((h->ih[b].Q / 2 + kThreads - 1) / kThreads)) * std::max(1, h->ih[b].Nz / 3);
     h->max_tiles = max_tiles;
     const size_t tile_off = pool.take(sizeof(Tile) * max_tiles);
     const size_t macro_off = pool.take(8 * (size_t)h->maxNz * 8);
@@ -735,6 +742,7 @@ lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT, int fuse)
     if (tiles.size() > h->max_tiles) return fail(LBS_ERR_ARG, "tile list exceeds its buffer");
     for (int b = 0; b < h->ninst; ++b) {
         h->idev[b].nchunks = h->ih[b].nchunks;
+        h->idev[b].nchh = h->ih[b].nchh;
         h->idev[b].nzt = h->ih[b].nzt;
     }
     CK(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, h->stream));

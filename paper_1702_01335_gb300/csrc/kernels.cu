@@ -409,7 +409,10 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     const int Nz = I.Nz, Q = I.Q, Qx = I.Qx, Qy = I.Qy, Qz = I.Qz, QxQy = I.QxQy;
     const int z0 = tile.z0, zn = tile.zn;            // cells z0 .. z0+zn-1 (0-based)
     constexpr int KC = kThreads * V;
-    const int k0 = tile.chunk * KC, kend = min(Q, k0 + KC), kn = kend - k0;
+    // chunks never straddle p_z = 0: this chunk's velocities share the sign of p_z
+    const int Qh = Q >> 1, sgc = tile.chunk >= I.nchh;
+    const int k0 = sgc * Qh + (tile.chunk - sgc * I.nchh) * KC;
+    const int kend = min((sgc + 1) * Qh, k0 + KC), kn = kend - k0;
     const int zm_lo = k0 / QxQy, zm_hi = (kend - 1) / QxQy, nzm = zm_hi - zm_lo + 1;
     const int G = Qx + Qy + nzm;                     // per-cell factors held in smem
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -476,11 +479,11 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     if (STAGE > 0)
         for (int c = tid; c < zn; c += kThreads) idzs[c] = ld<T>(I.inv_dz, z0 + c);
 
-    // per-velocity constants: p, and w * psi(p) for the 13 raw moments
+    // per-velocity constants: p (and |p_z| for the fluxes), w * psi(p) for the 13 raw moments
     int ii[V], jj[V], zz[V], kl[V];
-    T px[V], py[V], pz[V];
+    T px[V], py[V], pz[V], apz[V];
     A wpsi[V][kNMom];
-    bool up[V], ok[V];
+    bool ok[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         kl[v] = tid + v * kThreads;
@@ -494,7 +497,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         py[v] = ld<T>(I.py, jj[v]);
         const T x = ld<T>(I.xi, m);
         pz[v] = sg ? -x : x;
-        up[v] = !sg;
+        apz[v] = x;
         const A w = ok[v] ? A(ld<T>(I.wx, ii[v]) * ld<T>(I.wy, jj[v]) * ld<T>(I.wz, m)) : A(0);
         const A X = px[v], Y = py[v], Z = pz[v], p2 = X * X + Y * Y + Z * Z;
         wpsi[v][0] = w;
@@ -549,9 +552,10 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     const int rbase = 3 - z0;  // smem row of cell s is s + rbase
 #pragma unroll
     for (int v = 0; v < V; ++v) {
+        if (!ok[v]) continue;  // columns past the chunk end hold no data
         T* col = Fs + kl[v];
         if (z0 < 3) {
-            if (up[v]) {  // incoming at the bottom wall: n_w times the wall equilibrium
+            if (!sgc) {  // incoming at the bottom wall: n_w times the wall equilibrium
                 const T g = T(I.nw[0]) * ld<T>(I.gwx_bot, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
                 for (int s = -3; s <= -1; ++s)
                     if (s + rbase >= 0) col[(size_t)(s + rbase) * KC] = g;
@@ -567,7 +571,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         }
         if (z0 + zn + 3 > Nz) {
             const int smax = z0 + zn + 2;
-            if (!up[v]) {
+            if (sgc) {
                 const T g = T(I.nw[1]) * ld<T>(I.gwx_top, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
                 for (int s = Nz; s <= Nz + 2; ++s)
                     if (s <= smax) col[(size_t)(s + rbase) * KC] = g;
@@ -585,40 +589,45 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
 
     __syncthreads();  // per-cell factors complete
 
-    // ---- 5. march up the z-range
+    // ---- 5. march through the z-range in the upwind direction of the chunk: up
+    // (p_z > 0) from z0, down (p_z < 0) from z0+zn-1.  At march step c the register
+    // window holds the cells s-3 .. s+2 seen from upwind (s+3 .. s-2 going down), so
+    // both directions use one stencil: the flux through the interface ahead is
+    // |p_z| weno5(w1 .. w5), the one behind was formed at the previous step, and the
+    // divergence of Eq. (flux) is (ahead - behind) / dz for the signed p_z either way.
+    const long rstep = sgc ? -(long)KC : (long)KC;
+    const T* rp = Fs + (sgc ? (size_t)(zn + 5) * KC : 0);  // window row d at step c: rp + (c + d) rstep
     T w[V][6], flm[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
 #pragma unroll
-        for (int d = 0; d < 6; ++d) w[v][d] = Fs[(size_t)d * KC + kl[v]];
-        flm[v] = pz[v] * (up[v] ? weno5<T>(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4])
-                                : weno5<T>(w[v][5], w[v][4], w[v][3], w[v][2], w[v][1]));
+        for (int d = 0; d < 6; ++d) w[v][d] = rp[d * rstep + kl[v]];
+        flm[v] = apz[v] * weno5<T>(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4]);
     }
     const T dt = T(I.dt);
-    T* outp = Fout + (size_t)z0 * Q + k0;
+    const long ostep = sgc ? -(long)Q : (long)Q;
+    T* outp = Fout + (size_t)(sgc ? z0 + zn - 1 : z0) * Q + k0;
 #pragma unroll 1  // unrolling the z-march only adds instruction-cache misses
     for (int c = 0; c < zn; ++c) {
-        const T* sc = recs + (size_t)c * kRecStride;
-        const T* gc = gsm + c * G;
+        const int cc = sgc ? zn - 1 - c : c;  // the cell within the tile
+        const T* sc = recs + (size_t)cc * kRecStride;
+        const T* gc = gsm + cc * G;
+        const T* rn = rp + (c + 6) * rstep;
         T ux = 0, uy = 0, uz = 0, i5T = 0, qx = 0, qy = 0, qz = 0, itau = 0, cS = 0, idz = 0;
         if (STAGE > 0) {
             ux = sc[R_UX]; uy = sc[R_UY]; uz = sc[R_UZ];
             qx = sc[R_QX]; qy = sc[R_QY]; qz = sc[R_QZ];
-            itau = sc[R_ITAU]; cS = sc[R_CS]; i5T = sc[R_I5T]; idz = idzs[c];
+            itau = sc[R_ITAU]; cS = sc[R_CS]; i5T = sc[R_I5T]; idz = idzs[cc];
         }
         A acc[16];
 #pragma unroll
         for (int a = 0; a < 16; ++a) acc[a] = A(0);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const T wn = Fs[(size_t)(c + 6) * KC + kl[v]];
+            const T wn = rn[kl[v]];
             T out = w[v][3];
             if (STAGE > 0) {
-                // upwind-ordered stencil of the interface s + 1/2 (mirror image for p_z < 0)
-                const bool u = up[v];
-                const T a0 = u ? w[v][1] : wn, a1 = u ? w[v][2] : w[v][5], a2 = u ? w[v][3] : w[v][4];
-                const T a3 = u ? w[v][4] : w[v][3], a4 = u ? w[v][5] : w[v][2];
-                const T flp = pz[v] * weno5<T>(a0, a1, a2, a3, a4);
+                const T flp = apz[v] * weno5<T>(w[v][1], w[v][2], w[v][3], w[v][4], w[v][5]);
                 const T f = w[v][3];
                 // Shakhov target n Gx Gy Gz (1 + S), S = cS (xi^2/(5T) - 1) xi.q
                 const T ex = px[v] - ux, ey = py[v] - uy, ez = pz[v] - uz;
@@ -637,7 +646,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 if (STAGE == 1) {
                     out = f1;
                 } else {
-                    const T fl = F0s[(size_t)c * KC + kl[v]];
+                    const T fl = F0s[(size_t)cc * KC + kl[v]];
                     out = fl + (STAGE == 2 ? T(0.25) : T(2.0 / 3.0)) * (f1 - fl);
                 }
                 if (ok[v]) outp[kl[v]] = out;
@@ -652,8 +661,8 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         }
         const A tot = reduce_scatter16<A>(acc, lane);
         const int m = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-        if ((lane & 1) == 0) red[((size_t)c * (kThreads / 32) + warp) * 16 + m] = tot;
-        outp += Q;
+        if ((lane & 1) == 0) red[((size_t)cc * (kThreads / 32) + warp) * 16 + m] = tot;
+        outp += ostep;
     }
     __syncthreads();
     for (int e = tid; e < zn * kNMom; e += kThreads) {
@@ -673,7 +682,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         double fl = 0.0;
 #pragma unroll
         for (int v = 0; v < V; ++v)
-            if (ok[v] && !up[v]) {
+            if (ok[v] && sgc) {
                 const T f1 = outval(v, 0), f2 = outval(v, 1), f3 = outval(v, 2);
                 const T g0 = T(I.ext_bot[0][0]) * f1 + T(I.ext_bot[0][1]) * f2 + T(I.ext_bot[0][2]) * f3;
                 const T g1 = T(I.ext_bot[1][0]) * g0 + T(I.ext_bot[1][1]) * f1 + T(I.ext_bot[1][2]) * f2;
@@ -686,7 +695,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         double fl = 0.0;
 #pragma unroll
         for (int v = 0; v < V; ++v)
-            if (ok[v] && up[v]) {
+            if (ok[v] && !sgc) {
                 const T f1 = outval(v, Nz - 1), f2 = outval(v, Nz - 2), f3 = outval(v, Nz - 3);
                 const T g0 = T(I.ext_top[0][0]) * f1 + T(I.ext_top[0][1]) * f2 + T(I.ext_top[0][2]) * f3;
                 const T g1 = T(I.ext_top[1][0]) * g0 + T(I.ext_top[1][1]) * f1 + T(I.ext_top[1][2]) * f2;

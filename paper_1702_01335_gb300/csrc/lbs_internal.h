@@ -35,6 +35,7 @@ struct InstDev {
     int Nz, Qx, Qy, Qz, Q, QxQy;
     int Nx, Ny, Nzq;              // per-axis expansion orders
     int nchunks, bulk;            // bulk: rows are 16-byte aligned, stage them with TMA bulk copies
+    int nchh;                     // chunks per half range of p_z (chunk c has p_z < 0 iff c >= nchh)
     int visc_law;
     double Kn, visc_param, Pr, dt, tol;
     double Dtop, Dbot;            // sum over incoming velocities of w p_z Gw (n_w = 1)
