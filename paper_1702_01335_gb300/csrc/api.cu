@@ -313,6 +313,8 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         // every row segment (row s, chunk start k0 in either half) starts on 16 bytes
         D.bulk = ((size_t)(I.Q / 2) * sizeof(T)) % 16 == 0;
         D.visc_law = d.visc.law; D.Kn = d.Kn; D.visc_param = d.visc.omega_or_S; D.Pr = d.Pr;
+        D.iKn = 1.0 / d.Kn;
+        D.isuth = d.visc.law == 1 ? 1.0 / (1.0 + d.visc.omega_or_S) : 0.0;
         D.dt = I.dt; D.tol = 0.0;
         const std::vector<double>& xc = I.xc;  // xc[s + 3]
         lagrange3(xc[Nz + 3], xc[Nz + 2], xc[Nz + 1], xc[Nz], D.ext_top[0]);

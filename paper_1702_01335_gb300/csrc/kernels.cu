@@ -238,19 +238,21 @@ __host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize
 // FP64 (the half-range ones cancel strongly for N >= 4).  Returns false for a
 // non-finite or non-positive state (a neutral state is written instead).
 template <typename T>
-__device__ bool write_record(const InstDev& I, int cell, double n, const double* u, double T_, const double* q)
+__device__ bool write_record(const InstDev& I, int cell, double n, double in, const double* u, double T_,
+                             const double* q)
 {
+    // in = 1 / n (the callers have it); FP64 divisions are costly here, so 1/T is the
+    // only other one before R_SCALE
     bool bad = !(n > 0.0) || !(T_ > 0.0) || !isfinite(n) || !isfinite(T_);
     for (int a = 0; a < 3; ++a) bad |= !isfinite(u[a]) || !isfinite(q[a]);
-    const double nn = bad ? 1.0 : n, Tc = bad ? 1.0 : T_;
+    const double nn = bad ? 1.0 : n, inn = bad ? 1.0 : in, Tc = bad ? 1.0 : T_;
     const double u0 = bad ? 0.0 : u[0], u1 = bad ? 0.0 : u[1], u2 = bad ? 0.0 : u[2];
     T* rec = static_cast<T*>(I.rec) + (size_t)cell * kRecStride;
-    const double tau = relax_time(I.visc_law, I.Kn, I.visc_param, nn, Tc);
     const double iT = 1.0 / Tc;
     rec[R_N] = T(nn); rec[R_UX] = T(u0); rec[R_UY] = T(u1); rec[R_UZ] = T(u2); rec[R_T] = T(Tc);
     rec[R_QX] = T(bad ? 0.0 : q[0]); rec[R_QY] = T(bad ? 0.0 : q[1]); rec[R_QZ] = T(bad ? 0.0 : q[2]);
-    rec[R_ITAU] = T(1.0 / tau);
-    rec[R_CS] = T((1.0 - I.Pr) / nn * iT * iT);
+    rec[R_ITAU] = T(inv_relax_time(I.visc_law, I.iKn, I.visc_param, I.isuth, nn, Tc, iT));
+    rec[R_CS] = T((1.0 - I.Pr) * inn * iT * iT);
     rec[R_I5T] = T(0.2 * iT);
     // R_SCALE multiplies the x factors so that the discrete equilibrium carries
     // exactly n: in exact arithmetic sum_i wx Gx = 1, sum_j wy Gy = 1 and the sum
@@ -274,7 +276,7 @@ __device__ bool write_record(const InstDev& I, int cell, double n, const double*
         rec[R_AY + l] = v;
         if (l <= I.Ny) s[1] += double(v) * I.wsum[1][l];
     }
-    half_coeffs_pm(u2, Tc, I.Nzq, I.alpha, I.beta, c, cm);
+    half_coeffs_pm(u2, Tc, iT, I.Nzq, I.alpha, I.beta, c, cm);
     s[2] = 0.0;
     for (int l = 0; l <= kMaxN; ++l) {
         const T vp = l <= I.Nzq ? T(c[l]) : T(0), vm = l <= I.Nzq ? T(cm[l]) : T(0);
@@ -325,7 +327,7 @@ __device__ void finalize_cell(const InstDev& I, int cell)
     I.Wnew[cell] = n;
     I.Wnew[Nz + cell] = u[0];
     I.Wnew[2 * Nz + cell] = T_;
-    bad |= !write_record<T>(I, cell, n, u, T_, q);
+    bad |= !write_record<T>(I, cell, n, in, u, T_, q);
     if (bad) atomicOr(I.status, 1);
 }
 
@@ -382,7 +384,7 @@ __global__ void records_from_macro(const InstDev* __restrict__ insts, int inst, 
     if (cell >= Nz) return;
     const double u[3] = {macro[Nz + cell], macro[2 * Nz + cell], macro[3 * Nz + cell]};
     const double q[3] = {macro[5 * Nz + cell], macro[6 * Nz + cell], macro[7 * Nz + cell]};
-    if (!write_record<T>(I, cell, macro[cell], u, macro[4 * Nz + cell], q)) atomicOr(I.status, 1);
+    if (!write_record<T>(I, cell, macro[cell], 1.0 / macro[cell], u, macro[4 * Nz + cell], q)) atomicOr(I.status, 1);
 }
 
 // ----------------------------------------------------------------------------

@@ -38,6 +38,7 @@ struct InstDev {
     int nchh;                     // chunks per half range of p_z (chunk c has p_z < 0 iff c >= nchh)
     int visc_law;
     double Kn, visc_param, Pr, dt, tol;
+    double iKn, isuth;            // 1 / Kn; Sutherland: 1 / (1 + S)
     double Dtop, Dbot;            // sum over incoming velocities of w p_z Gw (n_w = 1)
     double wsum[4][kMaxN + 1];    // sum_i w_i basis_l(p_i) of the stored (rounded) tables:
                                   // x, y, z (p_z > 0), z (p_z < 0); 1, 0, 0, ... exactly
@@ -104,12 +105,13 @@ LBS_HD void half_coeffs(double u, double T, int N, const double* alpha, const do
 // range, written in xi = -p_z >= 0).  The two share g(0) and, through
 // erfc(x) + erfc(-x) = 2, one erfc: the one of |x| is evaluated (no cancellation)
 // and the other is 2 minus it (a value in [1, 2], exact to an ulp).
-LBS_HD void half_coeffs_pm(double u, double T, int N, const double* alpha, const double* beta,
+LBS_HD void half_coeffs_pm(double u, double T, double iT, int N, const double* alpha, const double* beta,
                            double* bp, double* bm)
 {
+    // iT = 1 / T, which the caller has at hand
     double Jp[kMaxN + 1][kMaxN + 1], Jm[kMaxN + 1][kMaxN + 1];
     const int K = N;
-    const double iT = 1.0 / T, r2T = sqrt(0.5 * iT);
+    const double r2T = sqrt(0.5 * iT);
     const double g0 = exp(-0.5 * u * u * iT) * (r2T * (1.0 / sqrt(M_PI)));
     const double e = erfc(fabs(u) * r2T);  // erfc of the non-negative argument
     Jp[0][0] = u >= 0.0 ? 1.0 - 0.5 * e : 0.5 * e;  // erfc(-u / sqrt(2T)) / 2
@@ -131,6 +133,18 @@ LBS_HD void half_coeffs_pm(double u, double T, int N, const double* alpha, const
         bp[l] = Jp[l][0];
         bm[l] = Jm[l][0];
     }
+}
+
+// 1 / tau from 1 / n, 1 / T, 1 / Kn and (Sutherland) 1 / (1 + S), without a
+// division: power law n T^(1 - omega) / Kn, Sutherland n (T + S) / (Kn sqrt(T) (1 + S))
+LBS_HD double inv_relax_time(int law, double iKn, double param, double isuth, double n, double T, double iT)
+{
+    if (law == 0) {
+        if (param == 1.0) return n * iKn;
+        if (param == 0.5) return n * iKn * sqrt(T);
+        return n * iKn * pow(T, 1.0 - param);
+    }
+    return n * (T + param) * iKn * isuth * sqrt(iT);
 }
 
 // relaxation time: power law tau = Kn T^(omega-1)/n, Sutherland tau = Kn sqrt(T)(1+S)/(n(T+S))
