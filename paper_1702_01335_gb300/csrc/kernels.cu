@@ -264,6 +264,7 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     double c[kMaxN + 1], cm[kMaxN + 1], s[3];
     full_coeffs(u0, Tc, I.Nx, c);
     s[0] = 0.0;
+#pragma unroll
     for (int l = 0; l <= kMaxN; ++l) {
         const T v = l <= I.Nx ? T(c[l]) : T(0);
         rec[R_AX + l] = v;
@@ -271,6 +272,7 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     }
     full_coeffs(u1, Tc, I.Ny, c);
     s[1] = 0.0;
+#pragma unroll
     for (int l = 0; l <= kMaxN; ++l) {
         const T v = l <= I.Ny ? T(c[l]) : T(0);
         rec[R_AY + l] = v;
@@ -278,6 +280,7 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     }
     half_coeffs_pm(u2, Tc, iT, I.Nzq, I.alpha, I.beta, c, cm);
     s[2] = 0.0;
+#pragma unroll
     for (int l = 0; l <= kMaxN; ++l) {
         const T vp = l <= I.Nzq ? T(c[l]) : T(0), vm = l <= I.Nzq ? T(cm[l]) : T(0);
         rec[R_BP + l] = vp;

@@ -74,11 +74,22 @@ struct Tile { int inst, z0, zn, chunk, zt; };
 
 // a_l = int g(p; u, T) He_l(p) dp: a_0 = 1, a_1 = u, a_{l+1} = u a_l + l (T - 1) a_{l-1}
 // (from int g p He_l = u a_l + T l a_{l-1} and He_{l+1} = p He_l - l He_{l-1}).
+// Loops below run to the largest order kMaxN and test the actual order inside, so
+// that, unrolled, every array index is a constant and device code keeps the arrays
+// in registers instead of local memory.
+#if defined(__CUDACC__)
+#define LBS_UNROLL _Pragma("unroll")
+#else
+#define LBS_UNROLL
+#endif
+
 LBS_HD void full_coeffs(double u, double T, int N, double* a)
 {
     a[0] = 1.0;
-    if (N >= 1) a[1] = u;
-    for (int l = 1; l < N; ++l) a[l + 1] = u * a[l] + l * (T - 1.0) * a[l - 1];
+    a[1] = u;  // read only when N >= 1
+    LBS_UNROLL
+    for (int l = 1; l < kMaxN; ++l)
+        if (l < N) a[l + 1] = u * a[l] + l * (T - 1.0) * a[l - 1];
 }
 
 // b_l = int_0^inf g(p; u, T) pi_l(p) dp for the monic half-range polynomials,
@@ -108,30 +119,46 @@ LBS_HD void half_coeffs(double u, double T, int N, const double* alpha, const do
 LBS_HD void half_coeffs_pm(double u, double T, double iT, int N, const double* alpha, const double* beta,
                            double* bp, double* bm)
 {
-    // iT = 1 / T, which the caller has at hand
-    double Jp[kMaxN + 1][kMaxN + 1], Jm[kMaxN + 1][kMaxN + 1];
+    // iT = 1 / T, which the caller has at hand.  Rows J_{l,k} (k <= N - l) of the two
+    // recurrences; only rows l - 1 and l are kept.
     const int K = N;
     const double r2T = sqrt(0.5 * iT);
     const double g0 = exp(-0.5 * u * u * iT) * (r2T * (1.0 / sqrt(M_PI)));
     const double e = erfc(fabs(u) * r2T);  // erfc of the non-negative argument
-    Jp[0][0] = u >= 0.0 ? 1.0 - 0.5 * e : 0.5 * e;  // erfc(-u / sqrt(2T)) / 2
-    Jm[0][0] = u >= 0.0 ? 0.5 * e : 1.0 - 0.5 * e;  // erfc(u / sqrt(2T)) / 2
-    if (K >= 1) {
-        Jp[0][1] = u * Jp[0][0] + T * g0;
-        Jm[0][1] = -u * Jm[0][0] + T * g0;
-    }
-    for (int k = 1; k < K; ++k) {
-        Jp[0][k + 1] = u * Jp[0][k] + k * T * Jp[0][k - 1];
-        Jm[0][k + 1] = -u * Jm[0][k] + k * T * Jm[0][k - 1];
-    }
-    for (int l = 0; l < N; ++l)
-        for (int k = 0; k + l + 1 <= K; ++k) {
-            Jp[l + 1][k] = Jp[l][k + 1] - alpha[l] * Jp[l][k] - (l > 0 ? beta[l] * Jp[l - 1][k] : 0.0);
-            Jm[l + 1][k] = Jm[l][k + 1] - alpha[l] * Jm[l][k] - (l > 0 ? beta[l] * Jm[l - 1][k] : 0.0);
+    double Pp[kMaxN + 1], Pc[kMaxN + 1], Mp[kMaxN + 1], Mc[kMaxN + 1];
+    Pc[0] = u >= 0.0 ? 1.0 - 0.5 * e : 0.5 * e;  // erfc(-u / sqrt(2T)) / 2
+    Mc[0] = u >= 0.0 ? 0.5 * e : 1.0 - 0.5 * e;  // erfc(u / sqrt(2T)) / 2
+    Pc[1] = u * Pc[0] + T * g0;                  // used only when K >= 1
+    Mc[1] = -u * Mc[0] + T * g0;
+    LBS_UNROLL
+    for (int k = 1; k < kMaxN; ++k)
+        if (k < K) {
+            Pc[k + 1] = u * Pc[k] + k * T * Pc[k - 1];
+            Mc[k + 1] = -u * Mc[k] + k * T * Mc[k - 1];
         }
-    for (int l = 0; l <= N; ++l) {
-        bp[l] = Jp[l][0];
-        bm[l] = Jm[l][0];
+    bp[0] = Pc[0];
+    bm[0] = Mc[0];
+    LBS_UNROLL
+    for (int l = 0; l < kMaxN; ++l) {
+        if (l < N) {
+            const double al = alpha[l], be = l > 0 ? beta[l] : 0.0;
+            double Pn[kMaxN + 1], Mn[kMaxN + 1];
+            LBS_UNROLL
+            for (int k = 0; k + l + 1 <= kMaxN; ++k)
+                if (k + l + 1 <= K) {
+                    Pn[k] = Pc[k + 1] - al * Pc[k] - (l > 0 ? be * Pp[k] : 0.0);
+                    Mn[k] = Mc[k + 1] - al * Mc[k] - (l > 0 ? be * Mp[k] : 0.0);
+                }
+            LBS_UNROLL
+            for (int k = 0; k + l + 1 <= kMaxN; ++k) {
+                Pp[k] = Pc[k];
+                Pc[k] = Pn[k];
+                Mp[k] = Mc[k];
+                Mc[k] = Mn[k];
+            }
+            bp[l + 1] = Pc[0];
+            bm[l + 1] = Mc[0];
+        }
     }
 }
 
