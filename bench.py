@@ -307,7 +307,7 @@ def main():
                     "h2d_bytes_per_step": s.state_bytes(), "d2h_bytes_per_step": nprof_rows * 8,
                     "what": "lbs_set_state(all, pinned host) + lbs_step(1) + lbs_moments(all, host) "
                             "per step"},
-            "gpu_launches": {0: 9, 1: 3, 2: 18}[tuned["fuse"]] * a.steps,
+            "gpu_launches": {0: 6, 1: 3, 2: 12}[tuned["fuse"]] * a.steps,
             "clocks": clk.summary(),
         }
         if not a.no_cpu_baseline and world == 1:

@@ -189,8 +189,8 @@ lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms);
  * CTA of 128 threads updates 128*V velocities (V in {1, 2, 4}) of about ZT
  * consecutive cells (3 <= ZT <= 64).  fuse = 1 folds the per-cell and
  * per-instance finalisation into the stage kernel (the last CTA of a z-tile /
- * of an instance does it: 3 launches per step); fuse = 0 runs it as two
- * further launches per stage (cheaper for large batches); fuse = 2 does the
+ * of an instance does it: 3 launches per step); fuse = 0 runs it as one
+ * further launch per stage (cheaper for large batches); fuse = 2 does the
  * same for each half of the batch (about half the tiles each) on two streams,
  * so that one half's FP64 finalisation overlaps the other half's stage kernel
  * (the step forks from and joins back into the handle's stream; a batch of one

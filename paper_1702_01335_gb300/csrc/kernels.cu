@@ -714,7 +714,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     // that finishes last among the chunks of this z-tile finalises the tile's
     // cells; the one that finalises the instance's last z-tile does the walls
     // and the residual.  Counters are reset by their last user.
-    if (!fuse) return;  // finalize_cells / finalize_inst follow as separate launches
+    if (!fuse) return;  // finalize_cells follows as a separate launch
     __shared__ int last;
     __threadfence();
     __syncthreads();
@@ -736,19 +736,24 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
 
 // ---- separate finalisation launches (used when the stage kernel does not fuse them)
 template <typename T>
-__global__ void __launch_bounds__(32) finalize_cells(const InstDev* __restrict__ insts)
+__global__ void __launch_bounds__(32) finalize_cells(const InstDev* __restrict__ insts, int stage)
 {
+    __shared__ double red[kThreads / 32];
+    __shared__ int last;
     const InstDev& I = insts[blockIdx.y];
+    const int nblk = (I.Nz + 31) >> 5;
+    if (blockIdx.x >= nblk || *I.active == 0) return;
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= I.Nz || *I.active == 0) return;
-    finalize_cell<T>(I, cell);
-}
-
-__global__ void __launch_bounds__(128) finalize_inst(const InstDev* __restrict__ insts, int stage)
-{
-    __shared__ double red[4];
-    const InstDev& I = insts[blockIdx.x];
-    if (*I.active == 0) return;
+    if (cell < I.Nz) finalize_cell<T>(I, cell);
+    // the instance's last block to finish (threadfence ticket) forms n_w and, after
+    // stage 3, the residual; the counter is reset by its last user
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(I.icount, 1) == nblk - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) *I.icount = 0;
     finalize_instance(I, stage, red);
 }
 
@@ -808,10 +813,7 @@ static cudaError_t launch_stage_v(int stage, const InstDev* d, const Tile* t, in
 template <typename T>
 static cudaError_t launch_finalize_t(int stage, const InstDev* d_inst, int ninst, int maxNz, cudaStream_t st)
 {
-    finalize_cells<T><<<dim3((maxNz + 31) / 32, ninst), 32, 0, st>>>(d_inst);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    finalize_inst<<<ninst, 128, 0, st>>>(d_inst, stage);
+    finalize_cells<T><<<dim3((maxNz + 31) / 32, ninst), 32, 0, st>>>(d_inst, stage);
     return cudaGetLastError();
 }
 
