@@ -52,6 +52,9 @@ def parse():
                     help="V,ZT,fuse: use this stage-kernel tiling instead of the autotuner")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON cache of tile choices (default: the package's tuning_cache.json)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "tables"],
+                    help="c2: the throughput workload (default); tables: the 20 half-channel "
+                         "runs of the paper's Sec. VI tables (one GPU)")
     return ap.parse_args()
 
 
@@ -197,10 +200,94 @@ def run_reference(a):
     }), flush=True)
 
 
+def run_tables(a):
+    """The paper-reproduction workload: the 20 half-channel He / Ar runs of the Sec. VI
+    tables in one batch (16 cells, 7 x 7 x (2 x Q_n) velocities, Q_n = 7 or 30), timed
+    like the main line.  Small and latency-bound: the line reports the stage and
+    finalisation kernels' own times beside the step rate."""
+    import torch
+    from paper_1702_01335_gb300 import LBS_FP32, LBS_FP64, Instance, Solver
+    torch.cuda.set_device(0)
+    inst = [Instance(**p) for _, p in W.paper_tables()]
+    s = Solver(inst, precision=LBS_FP32 if a.precision == "f32" else LBS_FP64)
+    if a.tiling:
+        s.set_tiling(*(int(x) for x in a.tiling.split(",")))
+    st = s.torch_stream()
+    upd_step = sum(i.Nz * i.Q for i in inst)
+    s.step(a.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record(st)
+        s.step(a.steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nprof = max(3, min(500, a.steps // 10))
+    k_stage, k_fin, k_step = s.profile_steps(nprof)
+    pinned = torch.empty(s.state_bytes(), dtype=torch.uint8, pin_memory=True)
+    s.get_state_all_ptr(pinned.data_ptr(), to_host=True)
+    nrows = sum(8 * i.Nz for i in inst)
+    out_host = torch.empty(nrows, dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(3, min(500, a.steps // 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state_all_ptr(pinned.data_ptr(), from_host=True)
+        s.step(1)
+        s.moments_all_ptr(out_host.data_ptr())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    tl = s.tiling()
+    line = {
+        "metric": "cell x velocity updates/s (RK-3 steps)", "value": upd_step * a.steps / (ms * 1e-3),
+        "unit": "updates/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": a.precision, "data": "synthetic",
+        "config": {"workload": "paper tables: 20 half channels (Ar, He; delta 0.1-40; u_w sqrt 2, "
+                               "0.1 sqrt 2), Nz=16 A=0.98, Q=7x7x(2x7) or 7x7x(2x30), N_eq=6, "
+                               "Sutherland, Pr=2/3", "updates_per_step": upd_step,
+                   "l2": "state (%d KiB) resident in L2: latency-bound" % (s.state_bytes() >> 10),
+                   "tiling": {"V": tl["V"], "ZT": tl["ZT"], "fused_finalise": tl["fuse"]}},
+        "kernels": {"stage_ms_per_step": k_stage / nprof, "finalize_ms_per_step": k_fin / nprof,
+                    "profiled_step_ms": k_step / nprof},
+        "e2e": {"value": upd_step * e2e_steps / e2e_s, "unit": "updates/s",
+                "h2d_bytes_per_step": s.state_bytes(), "d2h_bytes_per_step": nrows * 8},
+        "gpu_launches": {0: 6, 1: 3, 2: 12}[tl["fuse"]] * a.steps,
+        "clocks": clk.summary(),
+    }
+    if not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_tables()
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
+def cpu_baseline_tables(seconds=12.0):
+    """The oracle on one table run (Ar, delta = 1, u_w = sqrt 2).  It has no half channel:
+    it steps the full channel of 32 cells, which costs two updates per half-channel update."""
+    from oracle.oracle import Oracle
+    label, p = [r for r in W.paper_tables() if r[0]["delta"] == 1.0][0]
+    o = Oracle(p["Qx"], p["Qy"], p["Qz"], p["N_eq"], 2 * p["Nz"], A=p["A"], Kn=p["Kn"], uw=p["u_w"],
+               Tw=p["T_w"], Pr=p["Pr"], visc_law=p["visc_law"], visc_param=p["visc_param"], dt=p["dt"])
+    o.step(1)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        o.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": p["Nz"] * 2 * p["Qx"] * p["Qy"] * p["Qz"] * n / dt, "unit": "updates/s", "cores": cores,
+            "kind": "oracle", "sample": "Ar delta=1 u_w=sqrt 2 as the full channel of 32 cells, %d RK-3 "
+                                        "steps in %.1f s, counted as half-channel updates" % (n, dt)}
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "tables":
+        return run_tables(a)
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -66,8 +66,18 @@ typedef struct { int Qx, Qy, Qz_half, N_eq; } lbs_orders;
 
 /* Grid: Nz cells (6 <= Nz <= 4096).  A = 0: uniform cells.  0 < A < 1: the
  * tanh stretching of Eqs. (stretch), (etas) mirrored onto the full channel,
- * eta_s = -atanh(A) + (s - 1/2) d_eta, d_eta = 2 atanh(A)/Nz, x = L tanh(eta)/(2A). */
-typedef struct { int Nz; double A; } lbs_grid;
+ * eta_s = -atanh(A) + (s - 1/2) d_eta, d_eta = 2 atanh(A)/Nz, x = L tanh(eta)/(2A).
+ *
+ * half = 0: the full channel -L/2 <= z <= L/2 between two diffuse walls.
+ * half = 1: only the upper half 0 <= z <= L/2 of a channel of 2 Nz cells (the
+ * same cells as cells Nz .. 2Nz-1 of the full grid with 2 Nz cells, so that the
+ * stretched grid follows Eq. (etas) on the half channel, eta_s = (s - 1/2)
+ * atanh(A)/Nz), with the bounce-back condition of the Appendix ("Boundary
+ * conditions") on the centre line z = 0: the three ghost cells below it hold the
+ * populations of cells 0, 1, 2 at the velocity with p_z and p_x reversed (the
+ * point symmetry of Couette flow about the centre line; p_y, which the paper's
+ * reduced model integrates out, is kept).  The diffuse wall stays at z = L/2. */
+typedef struct { int Nz; double A; int half; } lbs_grid;
 
 /* Viscosity law.  POWER: mu ~ T^omega_or_S, tau = Kn T^(omega-1) / n
  * (Eq. mw_tau for omega = 1).  SUTHERLAND: Eq. (sutherland_tau) with
@@ -211,6 +221,41 @@ lbs_status lbs_get_stream(lbs_handle h, void** out);
  * kind 0 = full range (sum w = 1), kind 1 = half range on (0, inf) (sum w = 1/2).
  * Needs no GPU.  LBS_ERR_ARG for Q outside 1..64. */
 lbs_status lbs_quadrature(int kind, int Q, double* nodes, double* weights);
+
+/* Couette-flow diagnostics over the half channel 0 <= z <= L/2 (L = 1), in the
+ * build's axes: the paper's normal axis x is z here, its flow axis y is x, so
+ * the paper's u_y is u_x and its T_xy is P_xz.  S cells with centres z_1..z_S
+ * (0 < z_s < 1/2) enter each formula: the upper half (cells Nz/2 .. Nz-1) of a
+ * full channel, or all Nz cells of a half channel. */
+typedef struct {
+    double u_wall;      /* u_x(L/2), quadratic extrapolation from the three cells
+                           next to the wall, Eq. (uslip_extra) */
+    double u_slip;      /* u_w - u_x(L/2), Eq. (uslip) */
+    double dudz0;       /* u_x'(0) by the three-point formula Eq. (ud0_extra) for
+                           a profile odd about the centre line */
+    double nu;          /* L u_x'(0) / (2 u_w), Eq. (vgrad) */
+    double mflow;       /* half-channel mass flow, rectangle rule in eta of Eq. (mflow),
+                           rho = n (particle mass 1) */
+    double mflow_hydro; /* rho u_w L / 4 of Eq. (mflow_hydro) with rho = 1 (the
+                           channel-average density, conserved from the initial state) */
+    double Txy;         /* P_xz averaged over the half channel, Eq. (Txy) */
+    double Txy_bal;     /* ballistic limit -rho u_w sqrt(2 T_w / pi), Eq. (Txy_bal), rho = 1 */
+    double Pi;          /* -T_xy / (u_w sqrt 2), Eq. (stress) (n_avg = 1, T_w = 1 units) */
+    double T0;          /* temperature on the centre line, Eq. (T0), for an even profile */
+} lbs_diag;
+
+/* Host-only: diagnostics from profiles prof[14][Nz] in the layout of
+ * lbs_profiles (read only), for the grid (Nz, A, half) of lbs_grid.  A = 0 takes
+ * the limit A -> 0 of the rectangle rule (equal weights 1/S).  nu, Pi are
+ * infinite or NaN when u_w = 0.  Needs no GPU.  LBS_ERR_ARG for null pointers,
+ * A outside [0, 1), half not 0 or 1, a full channel with odd Nz or fewer than 6
+ * cells in the half channel. */
+lbs_status lbs_couette_diagnostics(const double* prof, int Nz, double A, int half, double u_w,
+                                   double T_w, lbs_diag* out);
+
+/* The diagnostics of instance inst of a solver (its profiles, grid and walls);
+ * synchronises the solver's stream. */
+lbs_status lbs_diagnostics(lbs_handle h, int inst, lbs_diag* out);
 
 /* ---- Warm-start network (not in the paper: the learned initial state of the
  * batched sweep).  A perceptron n_in -> n_hidden -> n_hidden -> n_out with GELU

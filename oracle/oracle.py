@@ -12,8 +12,9 @@ Contents:
     grid of Eqs. (stretch), (etas) mirrored onto the full channel
     [-L/2, L/2], with ghost cells continuing the eta spacing;
   * `Oracle` holds one Couette problem and steps it with the scheme;
-  * `nu_center`, `pi_stress`, `t_center` are the post-processing formulas of
-    Eqs. (vgrad)/(ud0_extra), (stress)/(Txy) and (T0).
+  * `nu_center`, `pi_stress`, `t_center`, `u_slip`, `mass_flow` are the
+    post-processing formulas of Eqs. (vgrad)/(ud0_extra), (stress)/(Txy), (T0),
+    (uslip)/(uslip_extra) and (mflow) on the upper half of the full channel.
 """
 import ctypes as C
 import math
@@ -252,6 +253,32 @@ def txy_average(o, Pxz, A):
 def pi_stress(o, Pxz, uw, A):
     """Pi = -T_xy / (u_w sqrt 2), Eq. (stress), T_xy averaged by Eq. (Txy)."""
     return -txy_average(o, Pxz, A) / (uw * math.sqrt(2.0))
+
+
+def u_wall(o, ux):
+    """u_y(L/2) of Eq. (uslip_extra): the parabola through the last three cells
+    (S, S-1, S-2 of the half channel) evaluated at the wall x = L/2 = 0.5."""
+    S, x = _half(o)
+    xs, us = x[S - 3:], ux[2 * S - 3:2 * S]
+    tot = 0.0
+    for a in range(3):
+        b, c = [e for e in range(3) if e != a]
+        tot += (0.5 - xs[b]) * (0.5 - xs[c]) / ((xs[a] - xs[b]) * (xs[a] - xs[c])) * us[a]
+    return tot
+
+
+def u_slip(o, ux, uw):
+    """u_slip = u_w - u_y(L/2), Eq. (uslip)."""
+    return uw - u_wall(o, ux)
+
+
+def mass_flow(o, n, ux, A):
+    """Half-channel mass flow of Eq. (mflow): rectangle rule in eta,
+    L atanh(A) / (2 A S) sum_s rho_s u_s / cosh^2 eta_s (L = 1, rho = n)."""
+    S, _ = _half(o)
+    E = math.atanh(A)
+    eta = (np.arange(1, S + 1) - 0.5) * E / S
+    return E / (2.0 * A * S) * float(np.sum(n[S:] * ux[S:] / np.cosh(eta) ** 2))
 
 
 def t_center(o, T):

@@ -116,6 +116,7 @@ static lbs_status validate(const lbs_instance_desc& d)
     if ((long)2 * o.Qx * o.Qy * o.Qz_half > 32768) return fail(LBS_ERR_ARG, "Q = 2 Qx Qy Qz_half exceeds 32768");
     if (d.grid.Nz < 6 || d.grid.Nz > 4096) return fail(LBS_ERR_ARG, "Nz must lie in 6..4096");
     if (!(d.grid.A >= 0.0 && d.grid.A < 1.0)) return fail(LBS_ERR_ARG, "grid stretching A must lie in [0, 1)");
+    if (d.grid.half != 0 && d.grid.half != 1) return fail(LBS_ERR_ARG, "grid.half must be 0 or 1");
     if (!(d.Kn > 0.0) || !(d.T_w > 0.0) || !(d.Pr > 0.0) || !std::isfinite(d.u_w))
         return fail(LBS_ERR_ARG, "Kn, T_w and Pr must be positive and u_w finite");
     if (d.visc.law != LBS_VISC_POWER && d.visc.law != LBS_VISC_SUTHERLAND)
@@ -284,12 +285,14 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
                 t.gwz[m] += bb[l] * t.Pz[m * (I.Nzq + 1) + l];
                 t.gwz[I.Qz + m] += bb[l] * t.Pz[m * (I.Nzq + 1) + l];
             }
-        // grid
-        const int Nz = I.Nz;
+        // grid: the full channel of Nz cells, or (half) cells Nz .. 2Nz-1 of the full
+        // channel of 2Nz cells, whose centre line is the interface below cell 0
+        const int Nz = I.Nz, half = d.grid.half, Nfull = half ? 2 * Nz : Nz, s0 = half ? Nz : 0;
         I.xc.resize(Nz + 6);
-        for (int s = -3; s <= Nz + 2; ++s) I.xc[s + 3] = xpos(Nz, d.grid.A, s + 0.5);
+        for (int s = -3; s <= Nz + 2; ++s) I.xc[s + 3] = xpos(Nfull, d.grid.A, s0 + s + 0.5);
         I.xf.resize(Nz + 1);
-        for (int s = 0; s <= Nz; ++s) I.xf[s] = xpos(Nz, d.grid.A, s);
+        for (int s = 0; s <= Nz; ++s) I.xf[s] = xpos(Nfull, d.grid.A, s0 + s);
+        if (half) I.xf[0] = 0.0;  // tanh(0) exactly, whatever the rounding of -E + Nz (2E / 2Nz)
         t.idz.resize(Nz);
         double dzmin = 1e300;
         for (int s = 0; s < Nz; ++s) {
@@ -310,6 +313,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         D.Nx = I.Nx; D.Ny = I.Ny; D.Nzq = I.Nzq;
         D.nchunks = I.nchunks;
         D.nchh = I.nchh;
+        D.half = half;
         // every row segment (row s, chunk start k0 in either half) starts on 16 bytes
         D.bulk = ((size_t)(I.Q / 2) * sizeof(T)) % 16 == 0;
         D.visc_law = d.visc.law; D.Kn = d.Kn; D.visc_param = d.visc.omega_or_S; D.Pr = d.Pr;
@@ -540,6 +544,66 @@ lbs_status lbs_quadrature(int kind, int Q, double* nodes, double* weights)
         return fail(LBS_ERR_ARG, "kind must be 0 or 1 and Q in 1..64");
     if (gauss_rule(kind == 0 ? QUAD_FULL : QUAD_HALF, Q, nodes, weights))
         return fail(LBS_ERR_QUADRATURE, "Gauss rule construction failed");
+    return LBS_OK;
+}
+
+// Three-point Lagrange value at x of the samples (x_a, y_a), used for u_x(L/2) of
+// Eq. (uslip_extra).
+static double lagrange_at(double x, const double* xs, const double* ys)
+{
+    double w[3];
+    lagrange3(x, xs[0], xs[1], xs[2], w);
+    return w[0] * ys[0] + w[1] * ys[1] + w[2] * ys[2];
+}
+
+lbs_status lbs_couette_diagnostics(const double* prof, int Nz, double A, int half, double u_w, double T_w,
+                                   lbs_diag* out)
+{
+    if (!prof || !out) return fail(LBS_ERR_ARG, "null profiles or output");
+    if (!(A >= 0.0 && A < 1.0) || (half != 0 && half != 1)) return fail(LBS_ERR_ARG, "need 0 <= A < 1, half 0 or 1");
+    if (!half && (Nz % 2 != 0 || Nz < 12)) return fail(LBS_ERR_ARG, "a full channel needs an even Nz >= 12");
+    if (half && Nz < 6) return fail(LBS_ERR_ARG, "a half channel needs Nz >= 6");
+    const int S = half ? Nz : Nz / 2, s0 = Nz - S;  // cells s0 .. Nz-1 form the upper half
+    const double* n = prof + 0 * (size_t)Nz + s0;
+    const double* u = prof + 1 * (size_t)Nz + s0;
+    const double* T = prof + 4 * (size_t)Nz + s0;
+    const double* Pxz = prof + 12 * (size_t)Nz + s0;
+    // Eq. (etas) on the half channel: eta_s = (s - 1/2) atanh(A) / S, x_s = L tanh(eta_s) / (2A)
+    const double E = A > 0.0 ? std::atanh(A) : 0.0;
+    std::vector<double> x(S), wrect(S);
+    for (int s = 0; s < S; ++s) {
+        if (A > 0.0) {
+            const double eta = (s + 0.5) * E / S, c = std::cosh(eta);
+            x[s] = std::tanh(eta) / (2.0 * A);
+            wrect[s] = E / (A * S) / (c * c);  // L dx/deta at eta_s times d_eta, / (L / 2)
+        } else {
+            x[s] = (s + 0.5) / (2.0 * S);
+            wrect[s] = 1.0 / S;
+        }
+    }
+    lbs_diag d;
+    const double xw[3] = {x[S - 1], x[S - 2], x[S - 3]}, uw3[3] = {u[S - 1], u[S - 2], u[S - 3]};
+    d.u_wall = lagrange_at(0.5, xw, uw3);
+    d.u_slip = u_w - d.u_wall;
+    // odd profile u = c1 x + c3 x^3 + c5 x^5 through the first three cells: u'(0) = c1
+    const double a1 = x[0] * x[0], a2 = x[1] * x[1], a3 = x[2] * x[2];
+    d.dudz0 = a2 * a3 * u[0] / (x[0] * (a1 - a2) * (a1 - a3)) + a1 * a3 * u[1] / (x[1] * (a2 - a1) * (a2 - a3)) +
+              a1 * a2 * u[2] / (x[2] * (a3 - a1) * (a3 - a2));
+    // even profile T = c0 + c2 x^2 + c4 x^4: T(0) = c0
+    d.T0 = a2 * a3 * T[0] / ((a1 - a2) * (a1 - a3)) + a3 * a1 * T[1] / ((a2 - a1) * (a2 - a3)) +
+           a1 * a2 * T[2] / ((a3 - a1) * (a3 - a2));
+    d.nu = d.dudz0 / (2.0 * u_w);
+    double m = 0.0, t = 0.0;
+    for (int s = 0; s < S; ++s) {
+        m += wrect[s] * n[s] * u[s];
+        t += wrect[s] * Pxz[s];
+    }
+    d.mflow = 0.5 * m;  // the rectangle weights average over L/2: the integral is L/2 times that
+    d.mflow_hydro = 0.25 * u_w;
+    d.Txy = t;
+    d.Txy_bal = -u_w * std::sqrt(2.0 * T_w / 3.14159265358979323846);
+    d.Pi = -t / (u_w * std::sqrt(2.0));
+    *out = d;
     return LBS_OK;
 }
 
@@ -795,6 +859,18 @@ lbs_status lbs_profiles(lbs_handle h, int inst, double* host_out)
     if (s != LBS_OK) return s;
     CK(cudaStreamSynchronize(h->stream));
     return check_status(h);
+}
+
+lbs_status lbs_diagnostics(lbs_handle h, int inst, lbs_diag* out)
+{
+    lbs_status s = inst_ok(h, inst);
+    if (s != LBS_OK) return s;
+    if (!out) return fail(LBS_ERR_ARG, "null output");
+    const InstHost& I = h->ih[inst];
+    std::vector<double> prof(14 * (size_t)I.Nz);
+    s = lbs_profiles(h, inst, prof.data());
+    if (s != LBS_OK) return s;
+    return lbs_couette_diagnostics(prof.data(), I.Nz, I.d.grid.A, I.d.grid.half, I.d.u_w, I.d.T_w, out);
 }
 
 lbs_status lbs_moments(lbs_handle h, int inst, double* host_out)

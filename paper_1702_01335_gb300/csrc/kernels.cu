@@ -559,7 +559,15 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     for (int v = 0; v < V; ++v) {
         if (!ok[v]) continue;  // columns past the chunk end hold no data
         T* col = Fs + kl[v];
-        if (z0 < 3) {
+        if (z0 < 3 && I.half) {  // bounce-back on the centre line: ghost -1-s holds cell s
+            // at the mirrored velocity (p_z, p_x reversed: other half range, node Qx-1-i;
+            // the Gauss nodes are sorted, so p_x[Qx-1-i] = -p_x[i]).  It lies in the other
+            // sign's chunk, so it comes from the stage input in global memory.
+            const int zm = zz[v] + (sgc ? -Qz : Qz);
+            const int kmir = (zm * Qx + (Qx - 1 - ii[v])) * Qy + jj[v];
+            for (int s = 0; s < 3; ++s)
+                if (-1 - s + rbase >= 0) col[(size_t)(-1 - s + rbase) * KC] = Fin[(size_t)s * Q + kmir];
+        } else if (z0 < 3) {
             if (!sgc) {  // incoming at the bottom wall: n_w times the wall equilibrium
                 const T g = T(I.nw[0]) * ld<T>(I.gwx_bot, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
                 for (int s = -3; s <= -1; ++s)
@@ -687,7 +695,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         double fl = 0.0;
 #pragma unroll
         for (int v = 0; v < V; ++v)
-            if (ok[v] && sgc) {
+            if (ok[v] && sgc && !I.half) {  // no wall below a half channel
                 const T f1 = outval(v, 0), f2 = outval(v, 1), f3 = outval(v, 2);
                 const T g0 = T(I.ext_bot[0][0]) * f1 + T(I.ext_bot[0][1]) * f2 + T(I.ext_bot[0][2]) * f3;
                 const T g1 = T(I.ext_bot[1][0]) * g0 + T(I.ext_bot[1][1]) * f1 + T(I.ext_bot[1][2]) * f2;

@@ -39,7 +39,14 @@ class _Orders(C.Structure):
 
 
 class _Grid(C.Structure):
-    _fields_ = [("Nz", C.c_int), ("A", C.c_double)]
+    _fields_ = [("Nz", C.c_int), ("A", C.c_double), ("half", C.c_int)]
+
+
+DIAG_NAMES = ("u_wall", "u_slip", "dudz0", "nu", "mflow", "mflow_hydro", "Txy", "Txy_bal", "Pi", "T0")
+
+
+class _Diag(C.Structure):
+    _fields_ = [(k, C.c_double) for k in DIAG_NAMES]
 
 
 class _Visc(C.Structure):
@@ -56,7 +63,7 @@ EXPORTS = ("lbs_create", "lbs_batch_create", "lbs_destroy", "lbs_step", "lbs_run
            "lbs_moments", "lbs_profiles", "lbs_residual", "lbs_steps_taken", "lbs_info",
            "lbs_get_state", "lbs_set_state", "lbs_init_from_profiles", "lbs_quadrature",
            "lbs_get_stream", "lbs_profile_steps", "lbs_moments_static", "lbs_set_tiling",
-           "lbs_get_tiling", "lbs_last_error",
+           "lbs_get_tiling", "lbs_last_error", "lbs_couette_diagnostics", "lbs_diagnostics",
            # the warm-start network (bound in warmstart.py)
            "lbs_mlp_create", "lbs_mlp_destroy", "lbs_mlp_num_params", "lbs_mlp_set_params",
            "lbs_mlp_get_params", "lbs_mlp_forward", "lbs_mlp_loss_grad", "lbs_mlp_adam",
@@ -92,6 +99,9 @@ def load(build_if_missing=True):
         lib.lbs_set_state.argtypes = [P, C.c_int, P, C.c_int]
         lib.lbs_init_from_profiles.argtypes = [P, C.c_int, D]
         lib.lbs_quadrature.argtypes = [C.c_int, C.c_int, D, D]
+        lib.lbs_couette_diagnostics.argtypes = [D, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
+                                                C.POINTER(_Diag)]
+        lib.lbs_diagnostics.argtypes = [P, C.c_int, C.POINTER(_Diag)]
         lib.lbs_get_stream.argtypes = [P, H]
         lib.lbs_profile_steps.argtypes = [P, C.c_long, D]
         lib.lbs_moments_static.argtypes = [P, C.c_int, P, P]
@@ -115,6 +125,18 @@ def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def couette_diagnostics(prof, Nz, A, half, u_w, T_w=1.0):
+    """Half-channel diagnostics (host only) from profiles [14, Nz] in PROFILE_NAMES
+    order: a dict over DIAG_NAMES (see lbs_diag in include/lbs.h)."""
+    lib = load()
+    prof = np.ascontiguousarray(prof, dtype=np.float64)
+    if prof.shape != (14, Nz):
+        raise ValueError("profiles must have shape (14, Nz)")
+    d = _Diag()
+    _check(lib.lbs_couette_diagnostics(_dptr(prof), Nz, A, half, u_w, T_w, C.byref(d)))
+    return {k: getattr(d, k) for k in DIAG_NAMES}
+
+
 def quadrature(kind, Q):
     """The solver's Gauss rule (host only): kind 0 full range, 1 half range."""
     lib = load()
@@ -132,6 +154,7 @@ class Instance:
     N_eq: int = 3
     Nz: int = 32
     A: float = 0.0
+    half: int = 0
     Kn: float = 0.1
     u_w: float = 0.1
     T_w: float = 1.0
@@ -142,7 +165,7 @@ class Instance:
     cfl: float = 0.5
 
     def desc(self):
-        return _Desc(_Orders(self.Qx, self.Qy, self.Qz, self.N_eq), _Grid(self.Nz, self.A),
+        return _Desc(_Orders(self.Qx, self.Qy, self.Qz, self.N_eq), _Grid(self.Nz, self.A, self.half),
                      self.Kn, self.u_w, self.T_w, self.Pr, _Visc(self.visc_law, self.visc_param),
                      self.dt, self.cfl)
 
@@ -266,6 +289,12 @@ class Solver:
         a = np.zeros((14, Nz))
         _check(self.lib.lbs_profiles(self.h, inst, _dptr(a)))
         return dict(zip(PROFILE_NAMES, a))
+
+    def diagnostics(self, inst=0):
+        """u_slip, u'(0), nu, mass flow, T_xy, Pi, T_0 of instance inst (dict over DIAG_NAMES)."""
+        d = _Diag()
+        _check(self.lib.lbs_diagnostics(self.h, inst, C.byref(d)))
+        return {k: getattr(d, k) for k in DIAG_NAMES}
 
     def residual(self, inst=0):
         r = C.c_double()

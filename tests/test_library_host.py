@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import quadrature as oq
+from oracle.oracle import Oracle, mass_flow, nu_center, pi_stress, t_center, txy_average, u_wall
 from paper_1702_01335_gb300 import lbs as L
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -57,7 +58,7 @@ def test_bad_arguments_are_rejected():
         L.Instance(Qx=0), L.Instance(Qz=65), L.Instance(N_eq=9), L.Instance(Nz=5),
         L.Instance(Kn=0.0), L.Instance(T_w=-1.0), L.Instance(Pr=0.0), L.Instance(A=1.0),
         L.Instance(cfl=0.0, dt=0.0), L.Instance(visc_law=1, visc_param=0.0),
-        L.Instance(Qx=64, Qy=64, Qz=64),
+        L.Instance(Qx=64, Qy=64, Qz=64), L.Instance(half=2),
     ]
     for inst in bad:
         d = (L._Desc * 1)(inst.desc())
@@ -66,3 +67,49 @@ def test_bad_arguments_are_rejected():
         assert lib.lbs_last_error().decode()
     assert lib.lbs_quadrature(2, 4, None, None) == 1
     assert lib.lbs_step(None, 1) == 1
+    prof = np.zeros((14, 12))
+    for Nz, A, half in ((11, 0.5, 0), (12, 1.0, 0), (5, 0.5, 1), (12, 0.5, 3)):
+        with pytest.raises(L.LbsError):
+            L.couette_diagnostics(np.zeros((14, Nz)), Nz, A, half, 0.1)
+    assert lib.lbs_couette_diagnostics(None, 12, 0.5, 0, 0.1, 1.0, None) == 1
+    assert L.couette_diagnostics(prof, 12, 0.5, 0, 0.1)["Txy"] == 0.0
+
+
+def _smooth_profiles(Nz, x, rng):
+    """Smooth profiles with the Couette symmetry on cell centres x (n, T, P_xz even; u_x odd)."""
+    prof = np.zeros((14, Nz))
+    c = rng.uniform(0.5, 1.5, 8)
+    prof[0] = c[0] + 0.3 * c[1] * x ** 2
+    prof[1] = 0.2 * c[2] * x + 0.5 * c[3] * x ** 3 + np.sin(c[4] * x) * 0.1
+    prof[4] = c[5] + 0.4 * x ** 2 - c[6] * x ** 4 + 0.05 * np.cos(3 * x)
+    prof[12] = -0.3 * c[7] + 0.01 * x ** 2
+    prof[[2, 3, 5, 6, 7, 8, 9, 10, 11, 13]] = rng.standard_normal((10, Nz))  # not read
+    return prof
+
+
+@pytest.mark.parametrize("A", [0.0, 0.7, 0.98])
+@pytest.mark.parametrize("S", [8, 16, 33])
+def test_diagnostics_match_oracle(A, S):
+    """lbs_couette_diagnostics (its own code) against the oracle's post-processing on the
+    upper half of a full channel of 2S cells, and on the same cells given as a half channel."""
+    rng = np.random.default_rng(S)
+    o = Oracle(2, 2, 2, 1, 2 * S, A=A)
+    x = o.xc[3:3 + o.Nz]
+    prof = _smooth_profiles(2 * S, x, rng)
+    uw, Tw = 0.37, 1.3
+    for half, p in ((0, prof), (1, prof[:, S:])):
+        d = L.couette_diagnostics(p, p.shape[1], A, half, uw, Tw)
+        assert abs(d["nu"] - nu_center(o, prof[1], uw)) < 1e-11
+        assert abs(d["dudz0"] - 2 * uw * nu_center(o, prof[1], uw)) < 1e-11
+        assert abs(d["T0"] - t_center(o, prof[4])) < 1e-11
+        assert abs(d["u_wall"] - u_wall(o, prof[1])) < 1e-12
+        assert abs(d["u_slip"] - (uw - u_wall(o, prof[1]))) < 1e-12
+        if A > 0:
+            assert abs(d["Txy"] - txy_average(o, prof[12], A)) < 1e-13
+            assert abs(d["Pi"] - pi_stress(o, prof[12], uw, A)) < 1e-13
+            assert abs(d["mflow"] - mass_flow(o, prof[0], prof[1], A)) < 1e-13
+        else:  # the A -> 0 limit of the rectangle rule: the midpoint rule on uniform cells
+            assert abs(d["Txy"] - np.mean(prof[12][S:])) < 1e-13
+            assert abs(d["mflow"] - 0.5 * np.mean(prof[0][S:] * prof[1][S:])) < 1e-13
+        assert d["mflow_hydro"] == uw / 4
+        assert abs(d["Txy_bal"] + uw * np.sqrt(2 * Tw / np.pi)) < 1e-15

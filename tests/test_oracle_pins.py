@@ -14,8 +14,8 @@ import pytest
 from scipy import integrate, special, stats
 
 from oracle import quadrature as quad
-from oracle.oracle import (VISC_POWER, VISC_SUTHERLAND, Oracle, nu_center, pi_stress,
-                           t_center, weno5)
+from oracle.oracle import (VISC_POWER, VISC_SUTHERLAND, Oracle, mass_flow, nu_center, pi_stress,
+                           t_center, txy_average, u_slip, u_wall, weno5)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -330,6 +330,47 @@ def test_navier_stokes_limit(Q, N, Pr):
     assert abs(np.mean(-p["Pxz"][b] / du[b] / mu[b]) - 1) < 2e-2
     b = b[np.abs(z[b]) > 0.1]
     assert abs(np.mean(-p["qz"][b] / dT[b] / (2.5 * mu[b] / Pr)) - 1) < 2e-2
+
+
+# ------------------------------------------------------------ post-processing --
+def test_postprocessing_exact_on_polynomials():
+    """Eq. (ud0_extra) is exact for odd quintics, Eq. (T0) for even quartics and
+    Eq. (uslip_extra) for parabolas (their stated orders), on the stretched grid."""
+    o = Oracle(2, 2, 2, 1, 32, A=0.98)
+    x = o.xc[3:3 + o.Nz]
+    assert abs(x[15] + x[16]) < 1e-15 and x[16] > 0  # cells 16..31 form the upper half
+    uw = 0.3
+    ux = 0.7 * x - 2.1 * x ** 3 + 5.3 * x ** 5
+    assert abs(nu_center(o, ux, uw) - 0.7 / (2 * uw)) < 1e-11
+    T = 1.4 + 0.8 * x ** 2 - 3.0 * x ** 4
+    assert abs(t_center(o, T) - 1.4) < 1e-12
+    u = 0.2 + 1.1 * x - 0.9 * x ** 2
+    assert abs(u_wall(o, u) - (0.2 + 1.1 * 0.5 - 0.9 * 0.25)) < 1e-12
+    assert abs(u_slip(o, u, uw) - (uw - (0.2 + 0.55 - 0.225))) < 1e-12
+    # x^3 is missed by exactly the interpolation remainder prod (L/2 - x_s) over the last three cells
+    r = np.prod(0.5 - x[-3:])
+    assert abs(u_wall(o, x ** 3) - (0.125 - r)) < 1e-15 and r > 1e-9
+
+
+@pytest.mark.parametrize("A", [0.5, 0.98])
+def test_rectangle_rule_second_order(A):
+    """Eqs. (mflow) and (Txy) approximate the half-channel integrals with error
+    O(d_eta^2): the hydrodynamic profile u = 2 u_w x / L gives rho u_w L / 4
+    (Eq. mflow_hydro) and a uniform T_xy averages to itself."""
+    uw = 0.25
+    errs_m, errs_t = [], []
+    for S in (16, 32, 64):
+        o = Oracle(2, 2, 2, 1, 2 * S, A=A)
+        x = o.xc[3:3 + o.Nz]
+        errs_m.append(mass_flow(o, np.ones(2 * S), 2 * uw * x, A) - uw / 4)
+        errs_t.append(txy_average(o, np.full(2 * S, -0.37), A) + 0.37)
+    for e in (errs_m, errs_t):
+        assert abs(e[0]) < 2e-2 * (uw if e is errs_m else 1)
+        assert 3.6 < e[0] / e[1] < 4.4 and 3.6 < e[1] / e[2] < 4.4
+    # the density enters as rho = n: doubling n doubles the flow
+    o = Oracle(2, 2, 2, 1, 32, A=A)
+    x = o.xc[3:3 + o.Nz]
+    assert abs(mass_flow(o, 2 * np.ones(32), x, A) - 2 * mass_flow(o, np.ones(32), x, A)) < 1e-15
 
 
 def _paper_case(case, steps):
