@@ -213,6 +213,15 @@ lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT, int fuse);
  * CTA.  Any output pointer may be NULL. */
 lbs_status lbs_get_tiling(lbs_handle h, int* V, int* ZT, int* fuse, int* ntiles, long* smem_bytes);
 
+/* Finalisation layout (not in the paper: how the per-cell FP64 work of each stage
+ * -- moments, profiles, equilibrium coefficients -- is spread over threads).
+ * mode 1: one thread per cell; mode 2: one warp per cell (lanes share the moment
+ * sums, the x / y coefficient recurrences and the two half-range tables); mode 0
+ * (the default): mode 2 for batches of at most 608 cells, else mode 1.  Results
+ * agree to rounding (a few ulps of FP64).  *warp_out (may be NULL) receives 1 if
+ * the warp layout is in use.  Synchronises the solver's stream. */
+lbs_status lbs_set_finalize(lbs_handle h, int mode, int* warp_out);
+
 /* The CUDA stream (cudaStream_t) the handle queues its work on: the one given at
  * creation, or the stream the library created when NULL was given. */
 lbs_status lbs_get_stream(lbs_handle h, void** out);

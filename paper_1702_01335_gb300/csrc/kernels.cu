@@ -170,6 +170,31 @@ __device__ double block_sum(double v, double* red)
     return s;
 }
 
+// N block sums at once (one pair of barriers for all of them); red holds
+// N * (blockDim.x / 32) doubles.  Each sum keeps block_sum's order.
+template <int N>
+__device__ void block_sum_n(double (&v)[N], double* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) red[i * nw + w] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < nw; ++j) s += red[i * nw + j];
+        v[i] = s;
+    }
+    __syncthreads();
+}
+constexpr int kRedSlots = 8 * (kThreads / 32);  // shared doubles for block_sum_n<8> with 128 threads
+
 // Warp reduce-scatter of 16 values: afterwards lane l holds the warp total of
 // value m(l) = 8 b4 + 4 b3 + 2 b2 + b1 (b = bits of l); lanes l, l^1 agree.
 // 16 shuffles per lane instead of 16 x 5 for 16 separate butterflies.
@@ -291,47 +316,201 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     return !bad;
 }
 
-// One cell (one thread): FP64 sum of the per-chunk moment partials (written by
-// other CTAs of this launch, hence read past L1), n, u, P, T, q (Eq. qdef) from
-// the raw moments, the profiles, W for the residual, and the cell record of the
-// next stage.
-template <typename T>
-__device__ void finalize_cell(const InstDev& I, int cell)
+// Macroscopic state of a cell from its 13 raw moments (FP64): n, u, the central
+// second moments P_ab = sum p_a p_b f - n u_a u_b, T = tr P / (3n) and the heat flux
+// q_a = 1/2 sum |xi|^2 xi_a f with xi = p - u (Eq. qdef), expanded in raw moments.
+struct CellState {
+    double n, in, u[3], T, q[3], P[6];  // P: xx, yy, zz, xy, xz, yz
+};
+__device__ __forceinline__ void cell_state(const double* mom, CellState& c)
 {
-    const int Nz = I.Nz;
-    double mom[kNMom];
-    for (int a = 0; a < kNMom; ++a) mom[a] = 0.0;
-    for (int c = 0; c < I.nchunks; ++c)
-#pragma unroll
-        for (int a = 0; a < kNMom; ++a) mom[a] += __ldcg(I.partial + ((size_t)c * kNMom + a) * Nz + cell);
     const double n = mom[0], in = 1.0 / n;
-    const double u[3] = {mom[1] * in, mom[2] * in, mom[3] * in};
-    // central second moments P_ab = sum p_a p_b f - n u_a u_b
-    const double Pxx = mom[4] - n * u[0] * u[0], Pyy = mom[5] - n * u[1] * u[1];
-    const double Pzz = mom[6] - n * u[2] * u[2], Pxy = mom[7] - n * u[0] * u[1];
-    const double Pxz = mom[8] - n * u[0] * u[2], Pyz = mom[9] - n * u[1] * u[2];
-    const double T_ = (Pxx + Pyy + Pzz) * (1.0 / 3.0) * in;
-    // q_a = 1/2 sum |xi|^2 xi_a f with xi = p - u, expanded in raw moments
+    c.n = n;
+    c.in = in;
+    c.u[0] = mom[1] * in; c.u[1] = mom[2] * in; c.u[2] = mom[3] * in;
+    const double* u = c.u;
+    c.P[0] = mom[4] - n * u[0] * u[0]; c.P[1] = mom[5] - n * u[1] * u[1];
+    c.P[2] = mom[6] - n * u[2] * u[2]; c.P[3] = mom[7] - n * u[0] * u[1];
+    c.P[4] = mom[8] - n * u[0] * u[2]; c.P[5] = mom[9] - n * u[1] * u[2];
+    c.T = (c.P[0] + c.P[1] + c.P[2]) * (1.0 / 3.0) * in;
     const double M2[3][3] = {{mom[4], mom[7], mom[8]}, {mom[7], mom[5], mom[9]}, {mom[8], mom[9], mom[6]}};
     const double tr = mom[4] + mom[5] + mom[6];
     const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const double um = u[0] * mom[1] + u[1] * mom[2] + u[2] * mom[3];
-    double q[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double uM2 = u[0] * M2[0][a] + u[1] * M2[1][a] + u[2] * M2[2][a];
-        q[a] = 0.5 * (mom[10 + a] - u[a] * tr - 2.0 * uM2 + 2.0 * u[a] * um + uu * mom[1 + a] - uu * u[a] * n);
+        c.q[a] = 0.5 * (mom[10 + a] - u[a] * tr - 2.0 * uM2 + 2.0 * u[a] * um + uu * mom[1 + a] - uu * u[a] * n);
     }
-    const double vals[14] = {n, u[0], u[1], u[2], T_, q[0], q[1], q[2], Pxx, Pyy, Pzz, Pxy, Pxz, Pyz};
+}
+
+// profiles [14][Nz] and W = (n, u_x, T) of a cell; false if any value is not finite
+__device__ __forceinline__ bool store_cell(const InstDev& I, int cell, const CellState& c)
+{
+    const int Nz = I.Nz;
+    const double vals[14] = {c.n, c.u[0], c.u[1], c.u[2], c.T, c.q[0], c.q[1], c.q[2],
+                             c.P[0], c.P[1], c.P[2], c.P[3], c.P[4], c.P[5]};
     bool bad = false;
+#pragma unroll
     for (int a = 0; a < 14; ++a) {
         I.prof[(size_t)a * Nz + cell] = vals[a];
         bad |= !isfinite(vals[a]);
     }
-    I.Wnew[cell] = n;
-    I.Wnew[Nz + cell] = u[0];
-    I.Wnew[2 * Nz + cell] = T_;
-    bad |= !write_record<T>(I, cell, n, in, u, T_, q);
+    I.Wnew[cell] = c.n;
+    I.Wnew[Nz + cell] = c.u[0];
+    I.Wnew[2 * Nz + cell] = c.T;
+    return !bad;
+}
+
+// One cell (one thread): FP64 sum of the per-chunk moment partials (written by
+// other CTAs of this launch, hence read past L1), the macroscopic state, the
+// profiles, W for the residual, and the cell record of the next stage.
+template <typename T>
+__device__ void finalize_cell(const InstDev& I, int cell)
+{
+    const int Nz = I.Nz, nch = I.nchunks;
+    double mom[kNMom];
+    for (int a = 0; a < kNMom; ++a) mom[a] = 0.0;
+    // chunks in order, four at a time with every load issued before the adds (the
+    // partials come from L2: one round trip per four chunks instead of per chunk)
+    for (int c = 0; c < nch; c += 4) {
+        double p[4][kNMom];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int a = 0; a < kNMom; ++a)
+                p[j][a] = c + j < nch ? __ldcg(I.partial + ((size_t)(c + j) * kNMom + a) * Nz + cell) : 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int a = 0; a < kNMom; ++a)
+                if (c + j < nch) mom[a] += p[j][a];
+    }
+    CellState st;
+    cell_state(mom, st);
+    bool bad = !store_cell(I, cell, st);
+    bad |= !write_record<T>(I, cell, st.n, st.in, st.u, st.T, st.q);
     if (bad) atomicOr(I.status, 1);
+}
+
+// ---- one cell per warp: the same record with its FP64 work spread over the lanes.
+// FP64 instructions issue at a small fraction of the FP32 rate, so with one thread
+// per cell a small batch waits on each cell's long FP64 chain; here lane a sums
+// moment a, the two halves of the warp run the x / y coefficient recurrences and
+// the p_z > 0 / p_z < 0 half-range tables side by side, and within a half lane k
+// carries column k of the table J_{l,k} (one shuffle per row instead of the whole
+// triangle in one thread).  Large batches keep one thread per cell, where every
+// lane has a cell of its own.
+template <typename T>
+__device__ bool write_record_warp(const InstDev& I, int cell, const CellState& st, int lane)
+{
+    bool bad = !(st.n > 0.0) || !(st.T > 0.0) || !isfinite(st.n) || !isfinite(st.T);
+    for (int a = 0; a < 3; ++a) bad |= !isfinite(st.u[a]) || !isfinite(st.q[a]);
+    const double nn = bad ? 1.0 : st.n, inn = bad ? 1.0 : st.in, Tc = bad ? 1.0 : st.T;
+    const double u0 = bad ? 0.0 : st.u[0], u1 = bad ? 0.0 : st.u[1], u2 = bad ? 0.0 : st.u[2];
+    T* rec = static_cast<T*>(I.rec) + (size_t)cell * kRecStride;
+    const double iT = 1.0 / Tc;
+    if (lane == 0) {
+        rec[R_N] = T(nn); rec[R_UX] = T(u0); rec[R_UY] = T(u1); rec[R_UZ] = T(u2); rec[R_T] = T(Tc);
+        rec[R_QX] = T(bad ? 0.0 : st.q[0]); rec[R_QY] = T(bad ? 0.0 : st.q[1]); rec[R_QZ] = T(bad ? 0.0 : st.q[2]);
+        rec[R_ITAU] = T(inv_relax_time(I.visc_law, I.iKn, I.visc_param, I.isuth, nn, Tc, iT));
+        rec[R_CS] = T((1.0 - I.Pr) * inn * iT * iT);
+        rec[R_I5T] = T(0.2 * iT);
+    }
+    const int h = lane >> 4, k = lane & 15;  // half of the warp, lane within it
+    // x (h = 0) and y (h = 1) coefficients a_l (Eq. fyz); lane k keeps a_k
+    double c[kMaxN + 1];
+    const int Nh = h ? I.Ny : I.Nx;
+    full_coeffs(h ? u1 : u0, Tc, Nh, c);
+    double ck = 0.0;
+#pragma unroll
+    for (int l = 0; l <= kMaxN; ++l)
+        if (l == k) ck = c[l];
+    double sxy = 0.0;  // this lane's term of sum_l c_l W_l (the R_SCALE sums, as in write_record)
+    if (k <= kMaxN) {
+        const T v = k <= Nh ? T(ck) : T(0);
+        rec[(h ? R_AY : R_AX) + k] = v;
+        if (k <= Nh) sxy = double(v) * I.wsum[h][k];
+    }
+    // z: half h = 0 the p_z > 0 range (drift u2), h = 1 the p_z < 0 range written in
+    // xi = -p_z >= 0 (drift -u2).  Both share g(0) and one erfc (erfc(x) + erfc(-x) = 2).
+    const int K = I.Nzq;
+    const double r2T = sqrt(0.5 * iT);
+    const double g0 = exp(-0.5 * u2 * u2 * iT) * (r2T * (1.0 / sqrt(M_PI)));
+    const double e = erfc(fabs(u2) * r2T);
+    const double us = h ? -u2 : u2;
+    const double J00 = (u2 >= 0.0) != (h == 1) ? 1.0 - 0.5 * e : 0.5 * e;  // erfc(-us / sqrt(2T)) / 2
+    // J_{0,k}: the half-line Gaussian moments M_k, M_{k+1} = us M_k + k T M_{k-1}
+    double mp = J00, mc = us * J00 + Tc * g0;
+    double Jc = k == 0 ? J00 : (k == 1 ? mc : 0.0);
+#pragma unroll
+    for (int kk = 1; kk < kMaxN; ++kk)
+        if (kk < K) {
+            const double mn = us * mc + kk * Tc * mp;
+            mp = mc;
+            mc = mn;
+            if (k == kk + 1) Jc = mn;
+        }
+    // rows J_{l+1,k} = J_{l,k+1} - alpha_l J_{l,k} - beta_l J_{l-1,k}; b_l = J_{l,0}.
+    // Column k holds a valid entry for k <= K - l; the others never reach column 0.
+    double Jp = 0.0, b[kMaxN + 1];
+    b[0] = Jc;
+#pragma unroll
+    for (int l = 0; l < kMaxN; ++l) {
+        b[l + 1] = 0.0;
+        if (l < K) {
+            const double up = __shfl_down_sync(0xffffffffu, Jc, 1, 16);
+            const double Jn = up - I.alpha[l] * Jc - (l > 0 ? I.beta[l] * Jp : 0.0);
+            Jp = Jc;
+            Jc = Jn;
+            b[l + 1] = Jc;
+        }
+    }
+    double sz = 0.0;
+    if (k == 0) {
+#pragma unroll
+        for (int l = 0; l <= kMaxN; ++l) {
+            const T v = l <= K ? T(b[l]) : T(0);
+            rec[(h ? R_BM : R_BP) + l] = v;
+            if (l <= K) sz += double(v) * I.wsum[2 + h][l];
+        }
+    }
+    // R_SCALE = n / (s_x s_y s_z) (see write_record)
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) sxy += __shfl_xor_sync(0xffffffffu, sxy, o, 16);
+    const double sx = __shfl_sync(0xffffffffu, sxy, 0), sy = __shfl_sync(0xffffffffu, sxy, 16);
+    const double s2 = __shfl_sync(0xffffffffu, sz, 0) + __shfl_sync(0xffffffffu, sz, 16);
+    if (lane == 0) rec[R_SCALE] = T(nn / (sx * sy * s2));
+    return !bad;
+}
+
+template <typename T>
+__device__ void finalize_cell_warp(const InstDev& I, int cell, int lane)
+{
+    const int Nz = I.Nz, nch = I.nchunks, am = lane & 15, h = lane >> 4;
+    // moment am: lanes am and 16 + am sum the even and the odd chunks (loads four
+    // chunks ahead), then add the two halves
+    double part = 0.0;
+    if (am < kNMom)
+        for (int c = h; c < nch; c += 8) {
+            double p[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                p[j] = c + 2 * j < nch ? __ldcg(I.partial + ((size_t)(c + 2 * j) * kNMom + am) * Nz + cell) : 0.0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (c + 2 * j < nch) part += p[j];
+        }
+    part += __shfl_down_sync(0xffffffffu, part, 16);
+    double mom[kNMom];
+#pragma unroll
+    for (int a = 0; a < kNMom; ++a) mom[a] = __shfl_sync(0xffffffffu, part, a);
+    CellState st;
+    cell_state(mom, st);
+    bool bad = false;
+    if (lane == 0) bad = !store_cell(I, cell, st);
+    bad |= !write_record_warp<T>(I, cell, st, lane);
+    if (bad && lane == 0) atomicOr(I.status, 1);
 }
 
 // One instance (whole CTA): wall densities n_w from the outgoing wall fluxes
@@ -339,33 +518,41 @@ __device__ void finalize_cell(const InstDev& I, int cell)
 // and retirement; after the analysis pass W_old = W.
 __device__ void finalize_instance(const InstDev& I, int stage, double* red)
 {
+    // red: kRedSlots doubles.  The wall fluxes and (stage 3) the residual's sums
+    // ||W_new - W_old||^2, ||W_old||^2 for n, u_x, T are reduced together.
     const int t = threadIdx.x, Nz = I.Nz;
-    double fb = 0.0, ft = 0.0;
+    double v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = 0.0;
     for (int c = t; c < I.nchunks; c += blockDim.x) {
-        fb += __ldcg(I.flux_part + 2 * c);
-        ft += __ldcg(I.flux_part + 2 * c + 1);
+        v[0] += __ldcg(I.flux_part + 2 * c);
+        v[1] += __ldcg(I.flux_part + 2 * c + 1);
     }
-    fb = block_sum(fb, red);
-    ft = block_sum(ft, red);
+    if (stage == 3) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            for (int s = t; s < Nz; s += blockDim.x) {
+                const double wn = __ldcg(I.Wnew + a * Nz + s), wo = I.Wold[a * Nz + s];
+                v[2 + 2 * a] += (wn - wo) * (wn - wo);
+                v[3 + 2 * a] += wo * wo;
+            }
+        block_sum_n<8>(v, red);
+    } else {
+        double w[2] = {v[0], v[1]};
+        block_sum_n<2>(w, red);
+        v[0] = w[0];
+        v[1] = w[1];
+    }
     if (t == 0) {
-        I.nw[0] = -fb / I.Dbot;
-        I.nw[1] = -ft / I.Dtop;
+        I.nw[0] = -v[0] / I.Dbot;
+        I.nw[1] = -v[1] / I.Dtop;
         if (!isfinite(I.nw[0]) || !isfinite(I.nw[1])) atomicOr(I.status, 1);
     }
     if (stage == 3) {
         double R = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            double d = 0.0, o = 0.0;
-            for (int s = t; s < Nz; s += blockDim.x) {
-                const double wn = __ldcg(I.Wnew + a * Nz + s), wo = I.Wold[a * Nz + s];
-                d += (wn - wo) * (wn - wo);
-                o += wo * wo;
-            }
-            d = block_sum(d, red);
-            o = block_sum(o, red);
-            R = fmax(R, sqrt(d) / fmax(sqrt(o), 1e-30));
-        }
-        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < 3; ++a) R = fmax(R, sqrt(v[2 + 2 * a]) / fmax(sqrt(v[3 + 2 * a]), 1e-30));
+        // every W_old read above is complete (block_sum_n ends with a barrier)
         for (int e = t; e < 3 * Nz; e += blockDim.x) I.Wold[e] = __ldcg(I.Wnew + e);
         if (t == 0) {
             *I.res = R;
@@ -406,7 +593,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     typedef typename Acc<T>::type A;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ double wall_red[kThreads / 32];
+    __shared__ double wall_red[kRedSlots];
     const Tile tile = tiles[blockIdx.x];
     const InstDev& I = insts[tile.inst];
     if (*I.active == 0) return;
@@ -730,7 +917,11 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (tid < zn) finalize_cell<T>(I, z0 + tid);
+    if (I.fin_warp) {
+        for (int c = tid >> 5; c < zn; c += kThreads / 32) finalize_cell_warp<T>(I, z0 + c, tid & 31);
+    } else if (tid < zn) {
+        finalize_cell<T>(I, z0 + tid);
+    }
     if (tid == 0) I.zcount[tile.zt] = 0;
     __threadfence();
     __syncthreads();
@@ -746,7 +937,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
 template <typename T>
 __global__ void __launch_bounds__(32) finalize_cells(const InstDev* __restrict__ insts, int stage)
 {
-    __shared__ double red[kThreads / 32];
+    __shared__ double red[kRedSlots];
     __shared__ int last;
     const InstDev& I = insts[blockIdx.y];
     const int nblk = (I.Nz + 31) >> 5;
@@ -755,6 +946,27 @@ __global__ void __launch_bounds__(32) finalize_cells(const InstDev* __restrict__
     if (cell < I.Nz) finalize_cell<T>(I, cell);
     // the instance's last block to finish (threadfence ticket) forms n_w and, after
     // stage 3, the residual; the counter is reset by its last user
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(I.icount, 1) == nblk - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) *I.icount = 0;
+    finalize_instance(I, stage, red);
+}
+
+// the same with one warp per cell (4 cells per block of 128 threads)
+template <typename T>
+__global__ void __launch_bounds__(128) finalize_cells_warp(const InstDev* __restrict__ insts, int stage)
+{
+    __shared__ double red[kRedSlots];
+    __shared__ int last;
+    const InstDev& I = insts[blockIdx.y];
+    const int nblk = (I.Nz + 3) >> 2;
+    if (blockIdx.x >= nblk || *I.active == 0) return;
+    const int cell = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (cell < I.Nz) finalize_cell_warp<T>(I, cell, threadIdx.x & 31);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(I.icount, 1) == nblk - 1;
@@ -819,9 +1031,13 @@ static cudaError_t launch_stage_v(int stage, const InstDev* d, const Tile* t, in
 }
 
 template <typename T>
-static cudaError_t launch_finalize_t(int stage, const InstDev* d_inst, int ninst, int maxNz, cudaStream_t st)
+static cudaError_t launch_finalize_t(int stage, const InstDev* d_inst, int ninst, int maxNz, int fin_warp,
+                                     cudaStream_t st)
 {
-    finalize_cells<T><<<dim3((maxNz + 31) / 32, ninst), 32, 0, st>>>(d_inst, stage);
+    if (fin_warp)
+        finalize_cells_warp<T><<<dim3((maxNz + 3) / 4, ninst), 128, 0, st>>>(d_inst, stage);
+    else
+        finalize_cells<T><<<dim3((maxNz + 31) / 32, ninst), 32, 0, st>>>(d_inst, stage);
     return cudaGetLastError();
 }
 
@@ -843,20 +1059,21 @@ cudaError_t launch_stage_only(int fp32, int V, int stage, const InstDev* d_inst,
 }
 
 // the separate finalisation launches of an unfused stage
-cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int ninst, int maxNz, cudaStream_t st)
+cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int ninst, int maxNz, int fin_warp,
+                            cudaStream_t st)
 {
-    return fp32 ? launch_finalize_t<float>(stage, d_inst, ninst, maxNz, st)
-                : launch_finalize_t<double>(stage, d_inst, ninst, maxNz, st);
+    return fp32 ? launch_finalize_t<float>(stage, d_inst, ninst, maxNz, fin_warp, st)
+                : launch_finalize_t<double>(stage, d_inst, ninst, maxNz, fin_warp, st);
 }
 
 // one RK stage (stage 1..3) or the analysis pass (stage 0); without fusion the
 // finalisation follows as two more launches
 cudaError_t launch_stage(int fp32, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
-                         int ntiles, size_t smem, int fuse, int ninst, int maxNz, cudaStream_t st)
+                         int ntiles, size_t smem, int fuse, int ninst, int maxNz, int fin_warp, cudaStream_t st)
 {
     cudaError_t e = launch_stage_only(fp32, V, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
     if (e != cudaSuccess || fuse) return e;
-    return launch_finalize(fp32, stage, d_inst, ninst, maxNz, st);
+    return launch_finalize(fp32, stage, d_inst, ninst, maxNz, fin_warp, st);
 }
 
 cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,

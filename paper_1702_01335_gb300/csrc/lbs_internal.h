@@ -37,6 +37,7 @@ struct InstDev {
     int nchunks, bulk;            // bulk: rows are 16-byte aligned, stage them with TMA bulk copies
     int nchh;                     // chunks per half range of p_z (chunk c has p_z < 0 iff c >= nchh)
     int half;                     // 1: half channel, bounce-back ghosts below cell 0 (no bottom wall)
+    int fin_warp;                 // finalisation with one warp per cell (small batches) instead of one thread
     int visc_law;
     double Kn, visc_param, Pr, dt, tol;
     double iKn, isuth;            // 1 / Kn; Sutherland: 1 / (1 + S)

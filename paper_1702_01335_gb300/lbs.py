@@ -64,6 +64,7 @@ EXPORTS = ("lbs_create", "lbs_batch_create", "lbs_destroy", "lbs_step", "lbs_run
            "lbs_get_state", "lbs_set_state", "lbs_init_from_profiles", "lbs_quadrature",
            "lbs_get_stream", "lbs_profile_steps", "lbs_moments_static", "lbs_set_tiling",
            "lbs_get_tiling", "lbs_last_error", "lbs_couette_diagnostics", "lbs_diagnostics",
+           "lbs_set_finalize",
            # the warm-start network (bound in warmstart.py)
            "lbs_mlp_create", "lbs_mlp_destroy", "lbs_mlp_num_params", "lbs_mlp_set_params",
            "lbs_mlp_get_params", "lbs_mlp_forward", "lbs_mlp_loss_grad", "lbs_mlp_adam",
@@ -102,6 +103,7 @@ def load(build_if_missing=True):
         lib.lbs_couette_diagnostics.argtypes = [D, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
                                                 C.POINTER(_Diag)]
         lib.lbs_diagnostics.argtypes = [P, C.c_int, C.POINTER(_Diag)]
+        lib.lbs_set_finalize.argtypes = [P, C.c_int, C.POINTER(C.c_int)]
         lib.lbs_get_stream.argtypes = [P, H]
         lib.lbs_profile_steps.argtypes = [P, C.c_long, D]
         lib.lbs_moments_static.argtypes = [P, C.c_int, P, P]
@@ -289,6 +291,12 @@ class Solver:
         a = np.zeros((14, Nz))
         _check(self.lib.lbs_profiles(self.h, inst, _dptr(a)))
         return dict(zip(PROFILE_NAMES, a))
+
+    def set_finalize(self, mode):
+        """0 auto, 1 one thread per cell, 2 one warp per cell; returns True if the warp layout is used."""
+        w = C.c_int()
+        _check(self.lib.lbs_set_finalize(self.h, int(mode), C.byref(w)))
+        return bool(w.value)
 
     def diagnostics(self, inst=0):
         """u_slip, u'(0), nu, mass flow, T_xy, Pi, T_0 of instance inst (dict over DIAG_NAMES)."""

@@ -183,8 +183,10 @@ def test_c2_full_size_sampled_parity():
     P = _lbs()
     ref = oracle_of(W.C2, None)
     ref.step(4)
-    for prec, tol in ((P.LBS_FP64, FP64_TOL), (P.LBS_FP32, FP32_TOL)):
+    # finalisation mode 1 is the layout of the benchmark's 256-replica batch
+    for prec, tol, mode in ((P.LBS_FP64, FP64_TOL, 1), (P.LBS_FP64, FP64_TOL, 2), (P.LBS_FP32, FP32_TOL, 1)):
         s = solver_of([W.C2] * 16, ref.dt, prec)
+        assert s.set_finalize(mode) == (mode == 2)
         s.step(4)
         errs = [max(profile_errors(s.profiles(b), ref.profiles()).values()) for b in (0, 7, 15)]
         assert max(errs) < tol, (prec, errs)
@@ -207,19 +209,43 @@ def test_c3_high_kn_fp32_free_molecular_bound():
     assert np.all(np.abs(p["Pxz"]) <= W.C3["u_w"] * math.sqrt(2 / math.pi) * 1.01)
 
 
+@pytest.mark.parametrize("fin", [1, 2])
 @pytest.mark.parametrize("V,ZT,fuse", [(1, 3, 1), (2, 7, 0), (4, 64, 1), (4, 5, 0)])
-def test_tiling_does_not_change_results(V, ZT, fuse):
+def test_tiling_does_not_change_results(V, ZT, fuse, fin):
     """Every work decomposition of the stage kernel, with the finalisation folded in
-    or launched apart, gives the oracle's state."""
+    or launched apart, one thread or one warp per cell, gives the oracle's state."""
     P = _lbs()
     o = oracle_of(RAGGED, dt=None)
     s = solver_of(RAGGED, o.dt, P.LBS_FP64)
     s.set_tiling(V, ZT, fuse)
+    s.set_finalize(fin)
     t = s.tiling()
     assert t["V"] == V and t["ZT"] == ZT and t["fuse"] == fuse
     o.step(15)
     s.step(15)
     assert rel_err(gpu_f(s, o), o.f[3:3 + o.Nz]) < FP64_TOL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_finalize_layouts_agree(prec):
+    """One thread per cell and one warp per cell give the same states to rounding
+    (FP64: ulps, grown by the dynamics to ~1e-13 in 30 steps; FP32 storage: the FP32
+    rounding of the records), for a batch
+    mixing a full and a half channel."""
+    P = _lbs()
+    from paper_1702_01335_gb300 import Instance, Solver
+    p = P.LBS_FP64 if prec == "fp64" else P.LBS_FP32
+    inst = [Instance(dt=0.002, **RAGGED), Instance(dt=0.002, half=1, **dict(RAGGED, Nz=20))]
+    a, b = Solver(inst, precision=p), Solver(inst, precision=p)
+    assert not a.set_finalize(1) and b.set_finalize(2)
+    a.step(30)
+    b.step(30)
+    tol = FP64_TOL if prec == "fp64" else 1e-5
+    for i in range(2):
+        fa, fb = a.get_state(i).astype(np.float64), b.get_state(i).astype(np.float64)
+        assert rel_err(fb, fa) < tol, i
+        errs = profile_errors(b.profiles(i), a.profiles(i), uw=RAGGED["u_w"])
+        assert max(errs.values()) < tol, errs
 
 
 def test_autotuner_picks_a_valid_tiling():
