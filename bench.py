@@ -209,9 +209,13 @@ def run_tables(a):
     from paper_1702_01335_gb300 import LBS_FP32, LBS_FP64, Instance, Solver
     torch.cuda.set_device(0)
     inst = [Instance(**p) for _, p in W.paper_tables()]
+    from paper_1702_01335_gb300.autotune import DEFAULT_CACHE, autotune
     s = Solver(inst, precision=LBS_FP32 if a.precision == "f32" else LBS_FP64)
     if a.tiling:
         s.set_tiling(*(int(x) for x in a.tiling.split(",")))
+    else:
+        autotune(s, candidates=tuple((V, ZT, F) for V in (1, 2) for ZT in (4, 6, 8, 16) for F in (0, 1)),
+                 steps=20, cache_file=a.tuning_cache or DEFAULT_CACHE)
     st = s.torch_stream()
     upd_step = sum(i.Nz * i.Q for i in inst)
     s.step(a.warmup)

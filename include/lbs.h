@@ -200,13 +200,15 @@ lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms);
  * consecutive cells (3 <= ZT <= 64).  fuse = 1 folds the per-cell and
  * per-instance finalisation into the stage kernel (the last CTA of a z-tile /
  * of an instance does it: 3 launches per step); fuse = 0 runs it as one
- * further launch per stage (cheaper for large batches); fuse = 2 does the
+ * further launch per stage; fuse = 2 does the
  * same for each half of the batch (about half the tiles each) on two streams,
  * so that one half's FP64 finalisation overlaps the other half's stage kernel
  * (the step forks from and joins back into the handle's stream; a batch of one
- * instance steps as with fuse = 0).  Used by the tile autotuner.  Waits for the
- * handle's stream and recomputes the moment partials of the current state.
- * LBS_ERR_ARG outside the ranges. */
+ * instance steps as with fuse = 0).  Used by the tile autotuner.  Without a call
+ * a solver starts with V = 1, ZT = 4 below 2^22 cell x velocity updates per step
+ * and V = 4, ZT = 12 above, fuse = 0.  Waits for the handle's stream and
+ * recomputes the moment partials of the current state.  LBS_ERR_ARG outside the
+ * ranges. */
 lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT, int fuse);
 
 /* Current tiling: V, ZT, fuse, number of stage CTAs, dynamic shared memory per

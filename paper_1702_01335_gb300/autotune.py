@@ -81,6 +81,9 @@ def autotune(solver, candidates=CANDIDATES, steps=3, cache_file=None, verbose=Fa
     solver.set_tiling(best["V"], best["ZT"], best["fuse"])
     _cache[key] = res
     if cache_file:
+        # entries of other kernel versions can never hit again
+        cur = kernel_hash() + ":"
+        disk = {k: v for k, v in disk.items() if k.startswith(cur)}
         disk[key] = res
         tmp = cache_file + ".tmp"
         with open(tmp, "w") as f:

@@ -644,9 +644,11 @@ lbs_status lbs_batch_create(lbs_handle* out, const lbs_instance_desc* desc, int 
     long work = 0;
     for (int b = 0; b < n; ++b)
         work += (long)desc[b].grid.Nz * 2 * desc[b].orders.Qx * desc[b].orders.Qy * desc[b].orders.Qz_half;
-    h->V = work >= (1L << 22) ? 2 : 1;
-    h->ZT = work >= (1L << 22) ? 16 : 4;
-    h->fuse = work >= (1L << 22) ? 0 : 1;
+    // untuned default: small batches are latency-bound (short z-tiles, one velocity per
+    // thread, more CTAs); large ones take the throughput tiling.  Finalisation apart.
+    h->V = work >= (1L << 22) ? 4 : 1;
+    h->ZT = work >= (1L << 22) ? 12 : 4;
+    h->fuse = 0;
     if (cuda_stream) {
         h->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
