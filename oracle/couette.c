@@ -11,6 +11,13 @@
  * paper's y), y is the transverse direction (the paper's z, kept here as a
  * third full-range Gauss-Hermite axis instead of being integrated out).
  *
+ * Reduced model (cfg.reduced = 1; Sec. III, Eqs. reduced_def, boltz_red,
+ * phieq, sred_def): y is integrated out.  The index j then selects the field,
+ * j = 0: phi = int f dp_y, j = 1: chi = int f p_y^2 dp_y (Qy = 2, p_y unused),
+ * both on the (p_x, p_z) nodes, relaxing to phi_eq (1 + S_phi) and
+ * chi_eq (1 + S_chi) with chi_eq = T phi_eq.  The transverse velocity and heat
+ * flux vanish in Couette flow and are not carried.
+ *
  * Storage: f[(s + 2) * Q + k] for cells s = -2 .. Nz+3 (three ghost cells per
  * side); k = ((sg * Qz + m) * Qx + i) * Qy + j, with p = (px[i], py[j], pz)
  * and pz = +xi[m] for sg = 0, -xi[m] for sg = 1.  f holds the discrete
@@ -41,6 +48,7 @@ typedef struct {
     int periodic;             /* 1: periodic in z instead of walls (tests)     */
     int weno_linear;          /* 1: ideal weights only (tests of the linear    */
                               /*    structure; not the paper's scheme)          */
+    int reduced;              /* 1: the phi / chi model (Qy = 2: j = field)    */
     double Kn, uw, Tw, Pr, visc_param, dt;
     const double *px, *wx;    /* [Qx] full-range nodes / weights (sum 1)      */
     const double *py, *wy;    /* [Qy]                                         */
@@ -111,10 +119,15 @@ static void axis_factors(const oracle_cfg *c, double ux, double uy, double uz, d
         for (int l = 0; l <= c->Nx; ++l) s += ax[l] * c->Hx[i * (c->Nx + 1) + l];
         Gx[i] = c->wx[i] * s;
     }
-    for (int j = 0; j < c->Qy; ++j) {
-        double s = 0.0;
-        for (int l = 0; l <= c->Ny; ++l) s += ay[l] * c->Hy[j * (c->Ny + 1) + l];
-        Gy[j] = c->wy[j] * s;
+    if (c->reduced) {  /* phi_eq carries no y factor; chi_eq = T phi_eq */
+        Gy[0] = 1.0;
+        Gy[1] = T;
+    } else {
+        for (int j = 0; j < c->Qy; ++j) {
+            double s = 0.0;
+            for (int l = 0; l <= c->Ny; ++l) s += ay[l] * c->Hy[j * (c->Ny + 1) + l];
+            Gy[j] = c->wy[j] * s;
+        }
     }
     /* half range: p > 0 uses g(p; uz), p < 0 uses g(-p; uz) = g(p; -uz)    */
     half_moments(uz, T, c->Nzq, Mp);
@@ -155,7 +168,15 @@ void oracle_equilibrium(const oracle_cfg *c, const double *mom, int with_S, doub
         int sg, m, i, j;
         vel_of(c, k, p, &sg, &m, &i, &j);
         double base = n * Gx[i] * Gy[j] * (sg == 0 ? Gzp[m] : Gzm[m]);
-        if (with_S && c->shakhov) {
+        if (with_S && c->shakhov && c->reduced) {
+            /* Eq. (sred_def): the y-averages of S over the Maxwellian in p_y,
+             * with weight 1 (phi) or p_y^2 / T (chi); u_y = q_y = 0          */
+            double ex = p[0] - u[0], ez = p[2] - u[2];
+            double xq = ex * q[0] + ez * q[2];
+            double off = (j == 0) ? 0.8 : 0.4;
+            double S = cS * ((ex * ex + ez * ez) / (5.0 * T) - off) * xq;
+            feq[k] = base * (1.0 + S);
+        } else if (with_S && c->shakhov) {
             double xi2 = 0.0, xq = 0.0;
             for (int a = 0; a < 3; ++a) {
                 double x = p[a] - u[a];
@@ -175,8 +196,14 @@ void oracle_equilibrium(const oracle_cfg *c, const double *mom, int with_S, doub
 /* Moments, Eq. (qdef):  out = {n, ux, uy, uz, T, qx, qy, qz,            */
 /*                              Pxx, Pyy, Pzz, Pxy, Pxz, Pyz}             */
 /* ------------------------------------------------------------------ */
+static void reduced_moments(const oracle_cfg *c, const double *f, double *out);
+
 void oracle_cell_moments(const oracle_cfg *c, const double *f, double *out)
 {
+    if (c->reduced) {
+        reduced_moments(c, f, out);
+        return;
+    }
     int Q = nvel(c);
     double n = 0.0, nu[3] = {0, 0, 0};
     for (int k = 0; k < Q; ++k) {
@@ -205,6 +232,48 @@ void oracle_cell_moments(const oracle_cfg *c, const double *f, double *out)
     out[5] = q[0]; out[6] = q[1]; out[7] = q[2];
     out[8] = P[0][0]; out[9] = P[1][1]; out[10] = P[2][2];
     out[11] = P[0][1]; out[12] = P[0][2]; out[13] = P[1][2];
+}
+
+/* Moments of the reduced model: the p_y integrals are carried by chi.
+ * n = sum phi, n u = sum p phi (u_y = 0); P_ab = sum xi_a xi_b phi for a, b in
+ * {x, z}, P_yy = sum chi, P_xy = P_yz = 0; q_a = 1/2 sum (xi_x^2 + xi_z^2) xi_a phi
+ * + 1/2 sum xi_a chi, q_y = 0; T = tr P / (3n).                             */
+static void reduced_moments(const oracle_cfg *c, const double *f, double *out)
+{
+    int Q = nvel(c);
+    double n = 0.0, nux = 0.0, nuz = 0.0;
+    for (int k = 0; k < Q; ++k) {
+        double p[3]; int sg, m, i, j;
+        vel_of(c, k, p, &sg, &m, &i, &j);
+        if (j != 0) continue;
+        n += f[k];
+        nux += p[0] * f[k];
+        nuz += p[2] * f[k];
+    }
+    double ux = nux / n, uz = nuz / n;
+    double Pxx = 0, Pzz = 0, Pxz = 0, Pyy = 0, qx = 0, qz = 0;
+    for (int k = 0; k < Q; ++k) {
+        double p[3]; int sg, m, i, j;
+        vel_of(c, k, p, &sg, &m, &i, &j);
+        double ex = p[0] - ux, ez = p[2] - uz;
+        if (j == 0) {
+            Pxx += ex * ex * f[k];
+            Pzz += ez * ez * f[k];
+            Pxz += ex * ez * f[k];
+            qx += 0.5 * (ex * ex + ez * ez) * ex * f[k];
+            qz += 0.5 * (ex * ex + ez * ez) * ez * f[k];
+        } else {
+            Pyy += f[k];
+            qx += 0.5 * ex * f[k];
+            qz += 0.5 * ez * f[k];
+        }
+    }
+    out[0] = n;
+    out[1] = ux; out[2] = 0.0; out[3] = uz;
+    out[4] = (Pxx + Pyy + Pzz) / (3.0 * n);
+    out[5] = qx; out[6] = 0.0; out[7] = qz;
+    out[8] = Pxx; out[9] = Pyy; out[10] = Pzz;
+    out[11] = 0.0; out[12] = Pxz; out[13] = 0.0;
 }
 
 /* Relaxation time: Eq. (mw_tau) generalised to mu ~ T^omega (Sec. VI), or
@@ -312,10 +381,12 @@ void oracle_apply_walls(const oracle_cfg *c, double *F, double *nw)
             F[ROW(s) * Q + k] = l1 * F[ROW(s - 1) * Q + k] + l2 * F[ROW(s - 2) * Q + k] +
                                 l3 * F[ROW(s - 3) * Q + k];
     }
+    /* mass flux: every population in the full model, phi alone in the reduced one */
     double phi = 0.0, D = 0.0;
     for (int k = 0; k < half; ++k) {
         double p[3]; int sg, m, i, j;
         vel_of(c, k, p, &sg, &m, &i, &j);
+        if (c->reduced && j != 0) continue;
         phi += iface_flux(c, F, Nz, k, p[2]);
     }
     double momw[8] = {1.0, c->uw, 0.0, 0.0, c->Tw, 0.0, 0.0, 0.0};
@@ -323,6 +394,7 @@ void oracle_apply_walls(const oracle_cfg *c, double *F, double *nw)
     for (int k = half; k < Q; ++k) {
         double p[3]; int sg, m, i, j;
         vel_of(c, k, p, &sg, &m, &i, &j);
+        if (c->reduced && j != 0) continue;
         D += p[2] * Fw[k];
     }
     double nwt = -phi / D;
@@ -341,6 +413,7 @@ void oracle_apply_walls(const oracle_cfg *c, double *F, double *nw)
     for (int k = half; k < Q; ++k) {
         double p[3]; int sg, m, i, j;
         vel_of(c, k, p, &sg, &m, &i, &j);
+        if (c->reduced && j != 0) continue;
         phi += iface_flux(c, F, 0, k, p[2]);
     }
     momw[1] = -c->uw;
@@ -348,6 +421,7 @@ void oracle_apply_walls(const oracle_cfg *c, double *F, double *nw)
     for (int k = 0; k < half; ++k) {
         double p[3]; int sg, m, i, j;
         vel_of(c, k, p, &sg, &m, &i, &j);
+        if (c->reduced && j != 0) continue;
         D += p[2] * Fw[k];
     }
     double nwb = -phi / D;
@@ -486,6 +560,10 @@ void oracle_interface_sums(const oracle_cfg *c, const double *F, double *out)
             double p[3]; int sg, m, i, j;
             vel_of(c, k, p, &sg, &m, &i, &j);
             double fl = flux[s * Q + k];
+            if (c->reduced && j == 1) {  /* chi carries the p_y^2 / 2 of the energy */
+                a3 += 0.5 * fl;
+                continue;
+            }
             a0 += fl;
             a1 += p[0] * fl;
             a2 += p[2] * fl;

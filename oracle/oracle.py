@@ -53,7 +53,7 @@ def build(force=False):
 class _Cfg(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("Nz", "Qx", "Qy", "Qz", "Nx", "Ny", "Nzq",
                                        "visc_law", "collisions", "shakhov", "periodic",
-                                       "weno_linear")] + \
+                                       "weno_linear", "reduced")] + \
                [(n, C.c_double) for n in ("Kn", "uw", "Tw", "Pr", "visc_param", "dt")] + \
                [(n, C.POINTER(C.c_double)) for n in ("px", "wx", "py", "wy", "xi", "wz",
                                                      "Hx", "Hy", "Pz", "cz", "xc", "xf")]
@@ -109,16 +109,27 @@ class Oracle:
     the equilibrium order N_eq (clipped per axis to Q_a - 1), Nz cells, the
     stretching A, Kn, u_w, T_w, Pr, the viscosity law (power with omega, or
     Sutherland with S) and the time step dt.
+
+    reduced=True (or Qy=0) selects the phi / chi model of Sec. III: the transverse
+    axis is integrated out and j in {0, 1} indexes phi and chi on the (p_x, p_z)
+    nodes (Qy = 2 in the storage order, weights w_x w_z, p_y unused).
     """
 
     def __init__(self, Qx, Qy, Qz, N_eq, Nz, A=0.0, Kn=0.1, uw=0.1, Tw=1.0, Pr=1.0,
                  visc_law=VISC_POWER, visc_param=1.0, dt=None, cfl=0.5,
-                 collisions=True, shakhov=True, periodic=False, weno_linear=False):
+                 collisions=True, shakhov=True, periodic=False, weno_linear=False, reduced=False):
+        self.reduced = bool(reduced or Qy == 0)
+        if self.reduced:
+            Qy = 2
         self.Qx, self.Qy, self.Qz, self.Nz = Qx, Qy, Qz, Nz
         self.Q = 2 * Qx * Qy * Qz
         self.Nx, self.Ny, self.Nzq = min(N_eq, Qx - 1), min(N_eq, Qy - 1), min(N_eq, Qz - 1)
         self.px, self.wx = quad.full_range_rule(Qx)
-        self.py, self.wy = quad.full_range_rule(Qy)
+        if self.reduced:
+            self.Ny = 0
+            self.py, self.wy = np.zeros(2), np.ones(2)
+        else:
+            self.py, self.wy = quad.full_range_rule(Qy)
         self.xi, self.wz = quad.half_range_rule(Qz)
         self.Hx = np.ascontiguousarray(quad.hermite_table(self.px, self.Nx))
         self.Hy = np.ascontiguousarray(quad.hermite_table(self.py, self.Ny))
@@ -131,6 +142,7 @@ class Oracle:
         self.dt = dt
         self.cfg = _Cfg(Nz, Qx, Qy, Qz, self.Nx, self.Ny, self.Nzq, visc_law,
                         int(collisions), int(shakhov), int(periodic), int(weno_linear),
+                        int(self.reduced),
                         Kn, uw, Tw, Pr, visc_param, dt,
                         *[_ptr(a) for a in (self.px, self.wx, self.py, self.wy, self.xi, self.wz,
                                             self.Hx, self.Hy, self.Pz, self.cz, self.xc, self.xf)])

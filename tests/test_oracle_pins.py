@@ -282,6 +282,72 @@ def test_parallel_axis_invariance(axis):
         assert np.abs(res[(False, 7)][k] - res[(False, 9)][k]).max() < 1e-3 * scale, k
 
 
+# ------------------------------------------------------------- reduced model --
+def _y_integrals(o3):
+    """phi = sum_j f_j and chi = sum_j p_y,j^2 f_j of a full-model state (weights absorbed),
+    in the reduced model's storage order (j = 0: phi, 1: chi)."""
+    f = o3.f.reshape(o3.Nz + 6, 2, o3.Qz, o3.Qx, o3.Qy)
+    phi = f.sum(axis=-1)
+    chi = (f * o3.py ** 2).sum(axis=-1)
+    return np.stack([phi, chi], axis=-1).reshape(o3.Nz + 6, -1)
+
+
+@pytest.mark.parametrize("A,visc", [(0.0, VISC_POWER), (0.9, VISC_SUTHERLAND)])
+def test_reduced_model_is_the_y_integral_of_the_full_model(A, visc):
+    """Eqs. (reduced_def), (boltz_red): with the linear reconstruction the phi / chi model
+    evolves exactly as the y-integrals int f dp_y, int p_y^2 f dp_y of the full model.
+    With Q_y = 7 and N_y = 4 the y-quadrature of the truncated equilibrium times (1 + S)
+    and p_y^2 is exact, so the two agree to rounding -- an equilibrium, S_phi / S_chi,
+    moment, wall or flux mistake in either would show."""
+    kw = dict(A=A, Kn=0.2, uw=0.4, Tw=1.1, Pr=2 / 3, visc_law=visc, visc_param=0.5 if visc == 0 else 0.5239,
+              dt=0.002, weno_linear=True)
+    full = Oracle(5, 7, 6, 4, 14, **kw)
+    red = Oracle(5, 0, 6, 4, 14, **kw)
+    assert red.reduced and red.Q == 2 * 5 * 2 * 6
+    full.step(60)
+    red.step(60)
+    ref = _y_integrals(full)[3:3 + 14]
+    assert np.abs(red.f[3:3 + 14] - ref).max() < 1e-13 * np.abs(ref).max()
+    pf, pr = full.profiles(), red.profiles()
+    for k in ("n", "ux", "uz", "T", "qx", "qz", "Pxx", "Pyy", "Pzz", "Pxz"):
+        scale = max(np.abs(pf[k]).max(), 1e-3)
+        assert np.abs(pf[k] - pr[k]).max() < 1e-12 * scale, k
+
+
+def test_reduced_shakhov_terms_are_y_averages():
+    """Eq. (sred_def): S_phi and S_chi are the averages of the Shakhov factor S of
+    Eq. (sdef) over the Maxwellian in p_y, with weights 1 and p_y^2 / T (checked by
+    quadrature of S itself, u_y = q_y = 0)."""
+    o = Oracle(4, 0, 4, 3, 8, Pr=0.3)
+    n, u, T, q = 1.3, np.array([0.2, 0.0, -0.1]), 1.4, np.array([0.05, 0.0, -0.07])
+    ratio = o.equilibrium(n, u, T, q, with_S=True) / o.equilibrium(n, u, T, q, with_S=False) - 1.0
+    p = o.velocities()
+    cS = (1 - 0.3) / (n * T * T)
+    for k in range(o.Q):
+        ex, ez, j = p[k, 0] - u[0], p[k, 2] - u[2], k % 2
+        def S(py):
+            xi2 = ex * ex + py * py + ez * ez
+            return cS * (xi2 / (5 * T) - 1) * (ex * q[0] + ez * q[2])
+        g = lambda py: math.exp(-py * py / (2 * T)) / math.sqrt(2 * math.pi * T)
+        wgt = (lambda py: 1.0) if j == 0 else (lambda py: py * py / T)
+        ref = integrate.quad(lambda py: g(py) * wgt(py) * S(py), -np.inf, np.inf, epsabs=1e-14)[0]
+        assert abs(ratio[k] - ref) < 1e-12 * max(1.0, abs(ref)), k
+
+
+def test_reduced_model_printed_values():
+    """The phi / chi model is the paper's own: Ar, delta = 1, u_w = sqrt 2 on the
+    HHLB(6;7) x HLB(6;7) set gives the printed nu = 0.484, Pi = 0.3720, T_0 = 1.561."""
+    case = json.load(open(os.path.join(GOLDEN, "paper_tables.json")))["cases"][0]
+    delta = case["delta"]
+    o = Oracle(7, 0, 7, 6, 32, A=0.98, Kn=1 / (delta * math.sqrt(2)), uw=case["uw"], Pr=2 / 3,
+               visc_law=VISC_SUTHERLAND, visc_param=case["S"], dt=5e-4)
+    o.step(14000)
+    p = o.profiles()
+    assert abs(nu_center(o, p["ux"], case["uw"]) - case["nu"]) <= 1.0e-3
+    assert abs(pi_stress(o, p["Pxz"], case["uw"], 0.98) / case["Pi"] - 1) < 1e-3
+    assert abs(t_center(o, p["T"]) / case["T0"] - 1) < 1e-3
+
+
 def test_free_molecular_closed_form():
     """tau = infinity: n = 1, u = 0, T = T_w + u_w^2/3, P_xx = T_w + u_w^2, P_yy = P_zz = T_w,
     P_xz = -u_w sqrt(2 T_w / pi) (the ballistic stress of Eq. Txy_bal), q = 0."""
