@@ -11,6 +11,16 @@
  * nodes on y, and a half-range Gauss-Hermite rule with Qz_half nodes on each
  * semi-axis of z: Q = 2 * Qx * Qy * Qz_half velocities (Sec. III).
  *
+ * Reduced model (Qy = 0).  The paper's own model (Sec. III, Eqs. reduced_def,
+ * boltz_red, phieq, sred_def) integrates the transverse momentum out: two
+ * distributions phi = int f dp_y and chi = int p_y^2 f dp_y on the (p_x, p_z)
+ * nodes relax to phi_eq (1 + S_phi) and chi_eq (1 + S_chi), chi_eq = T phi_eq.
+ * They are stored as a velocity set with Qy = 2 (j = 0: phi, j = 1: chi), so
+ * Q = 4 * Qx * Qz_half and every layout below applies with Qy = 2.  The
+ * transverse velocity and heat flux vanish in Couette flow and are not carried;
+ * the profiles report u_y = q_y = P_xy = P_yz = 0 and P_yy = sum chi.  A batch
+ * is either all reduced or all full.
+ *
  * Scheme (one time step = lbs_step(h, 1)): the RK-3 TVD stages of Eq. (rk3)
  * applied to L[F] of Eq. (L_def): WENO-5 advection along z (Eqs. flux,
  * weno5_flux, weno5_omega, weno_sigma, Table weno), relaxation to the
@@ -60,8 +70,9 @@ typedef enum { LBS_FP64 = 0, LBS_FP32_STORE_FP64_ACC = 1 } lbs_precision;
 
 /* Velocity-set orders.  N_eq is the order of the truncated Hermite expansion
  * of the equilibrium; each axis uses min(N_eq, Q_a - 1) (Sec. III; Q_a = Qz_half
- * on the wall-normal axis).  Limits: 1 <= Qx, Qy <= 64, 1 <= Qz_half <= 64,
- * 0 <= N_eq <= 8, Q <= 32768. */
+ * on the wall-normal axis).  Limits: 1 <= Qx <= 64, Qy = 0 (the reduced phi /
+ * chi model above) or 1 <= Qy <= 64, 1 <= Qz_half <= 64, 0 <= N_eq <= 8,
+ * Q <= 32768. */
 typedef struct { int Qx, Qy, Qz_half, N_eq; } lbs_orders;
 
 /* Grid: Nz cells (6 <= Nz <= 4096).  A = 0: uniform cells.  0 < A < 1: the
@@ -105,7 +116,8 @@ lbs_status lbs_create(lbs_handle* out, lbs_orders ord, lbs_grid grid, double Kn,
 
 /* Create a batch of n >= 1 independent instances that advance together in
  * the same launches (shared precision and stream).  desc[n] is read only
- * during the call. */
+ * during the call.  LBS_ERR_ARG, in addition to lbs_create's cases, for a batch
+ * that mixes reduced (Qy = 0) and full instances. */
 lbs_status lbs_batch_create(lbs_handle* out, const lbs_instance_desc* desc, int n,
                             lbs_precision prec, void* cuda_stream);
 

@@ -14,9 +14,9 @@
 #include "lbs_internal.h"
 
 namespace lbs {
-cudaError_t launch_stage(int fp32, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
+cudaError_t launch_stage(int fp32, int red, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
                          int ntiles, size_t smem, int fuse, int ninst, int maxNz, int fin_warp, cudaStream_t st);
-cudaError_t launch_stage_only(int fp32, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
+cudaError_t launch_stage_only(int fp32, int red, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
                               int ntiles, size_t smem, int fuse, cudaStream_t st);
 cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int ninst, int maxNz, int fin_warp,
                             cudaStream_t st);
@@ -47,6 +47,7 @@ namespace {
 struct InstHost {
     lbs_instance_desc d;
     int Nz, Q, Qx, Qy, Qz, Nx, Ny, Nzq, nchunks, nchh, nzm_max, nzt;
+    bool reduced;  // the phi / chi model (lbs_orders.Qy = 0)
     double dt;
     std::vector<double> xc, xf;  // cell centres (s = -3..Nz+2, 0-based), interfaces
 };
@@ -70,6 +71,7 @@ struct lbs_solver {
     bool own_stream = false;
     int fp32 = 0, esize = 8, V = 1, ZT = 16, fuse = 1, ninst = 0, maxNz = 0;
     int fin_mode = 0, fin_warp = 0;  // finalisation: 0 auto, 1 thread per cell, 2 warp per cell
+    int reduced = 0;                 // the batch runs the phi / chi model (all instances alike)
     std::vector<InstHost> ih;
     std::vector<InstDev> idev;
     InstDev* d_inst = nullptr;
@@ -111,11 +113,12 @@ int lbs::record_error(int status, const char* msg) { return fail(static_cast<lbs
 static lbs_status validate(const lbs_instance_desc& d)
 {
     const lbs_orders& o = d.orders;
-    if (o.Qx < 1 || o.Qx > kMaxQ1D || o.Qy < 1 || o.Qy > kMaxQ1D || o.Qz_half < 1 ||
+    if (o.Qx < 1 || o.Qx > kMaxQ1D || o.Qy < 0 || o.Qy > kMaxQ1D || o.Qz_half < 1 ||
         o.Qz_half > kMaxQ1D)
-        return fail(LBS_ERR_ARG, "velocity orders must lie in 1..64");
+        return fail(LBS_ERR_ARG, "velocity orders must lie in 1..64 (Qy = 0: the reduced model)");
     if (o.N_eq < 0 || o.N_eq > kMaxN) return fail(LBS_ERR_ARG, "N_eq must lie in 0..8");
-    if ((long)2 * o.Qx * o.Qy * o.Qz_half > 32768) return fail(LBS_ERR_ARG, "Q = 2 Qx Qy Qz_half exceeds 32768");
+    if ((long)2 * o.Qx * std::max(o.Qy, 2) * o.Qz_half > 32768)
+        return fail(LBS_ERR_ARG, "Q = 2 Qx Qy Qz_half exceeds 32768");
     if (d.grid.Nz < 6 || d.grid.Nz > 4096) return fail(LBS_ERR_ARG, "Nz must lie in 6..4096");
     if (!(d.grid.A >= 0.0 && d.grid.A < 1.0)) return fail(LBS_ERR_ARG, "grid stretching A must lie in [0, 1)");
     if (d.grid.half != 0 && d.grid.half != 1) return fail(LBS_ERR_ARG, "grid.half must be 0 or 1");
@@ -257,11 +260,12 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         I.d = d;
         I.Nz = d.grid.Nz;
         I.Qx = d.orders.Qx;
-        I.Qy = d.orders.Qy;
+        I.reduced = d.orders.Qy == 0;
+        I.Qy = I.reduced ? 2 : d.orders.Qy;  // reduced: j = 0 phi, j = 1 chi
         I.Qz = d.orders.Qz_half;
         I.Q = 2 * I.Qx * I.Qy * I.Qz;
         I.Nx = std::min(d.orders.N_eq, I.Qx - 1);
-        I.Ny = std::min(d.orders.N_eq, I.Qy - 1);
+        I.Ny = I.reduced ? 1 : std::min(d.orders.N_eq, I.Qy - 1);
         I.Nzq = std::min(d.orders.N_eq, I.Qz - 1);
         h->maxNz = std::max(h->maxNz, I.Nz);
     }
@@ -274,15 +278,22 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         t.px.resize(I.Qx); t.wx.resize(I.Qx); t.py.resize(I.Qy); t.wy.resize(I.Qy);
         t.xi.resize(I.Qz); t.wz.resize(I.Qz);
         if (gauss_rule(QUAD_FULL, I.Qx, t.px.data(), t.wx.data()) ||
-            gauss_rule(QUAD_FULL, I.Qy, t.py.data(), t.wy.data()) ||
+            (!I.reduced && gauss_rule(QUAD_FULL, I.Qy, t.py.data(), t.wy.data())) ||
             gauss_rule(QUAD_HALF, I.Qz, t.xi.data(), t.wz.data()))
             return fail(LBS_ERR_QUADRATURE, "Gauss rule construction failed");
+        if (I.reduced) {  // phi and chi on the same (p_x, p_z) node: no y node, weight 1
+            t.py.assign(2, 0.0);
+            t.wy.assign(2, 1.0);
+        }
         for (double v : t.wz)
             if (!(v > 0.0) || !std::isfinite(v)) return fail(LBS_ERR_QUADRATURE, "non-positive half-range weight");
         recurrence(QUAD_HALF, kMaxN + 2, t.alpha, t.beta);
         t.Hx.resize(I.Qx * (I.Nx + 1)); t.Hy.resize(I.Qy * (I.Ny + 1)); t.Pz.resize(I.Qz * (I.Nzq + 1));
         hermite_basis(t.px.data(), I.Qx, I.Nx, t.Hx.data());
-        hermite_basis(t.py.data(), I.Qy, I.Ny, t.Hy.data());
+        if (I.reduced)  // Gy_j = a_j: the record's y coefficients are the factors (1, T)
+            t.Hy = {1.0, 0.0, 0.0, 1.0};
+        else
+            hermite_basis(t.py.data(), I.Qy, I.Ny, t.Hy.data());
         half_basis(t.xi.data(), I.Qz, I.Nzq, t.alpha, t.beta, t.Pz.data());
         // wall equilibria per axis (n = 1, T = T_w, u = +-u_w along x, q = 0)
         double a[kMaxN + 1], bb[kMaxN + 1];
@@ -293,9 +304,14 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         full_coeffs(-d.u_w, d.T_w, I.Nx, a);
         for (int i = 0; i < I.Qx; ++i)
             for (int l = 0; l <= I.Nx; ++l) t.gxb[i] += a[l] * t.Hx[i * (I.Nx + 1) + l];
-        full_coeffs(0.0, d.T_w, I.Ny, a);
-        for (int j = 0; j < I.Qy; ++j)
-            for (int l = 0; l <= I.Ny; ++l) t.gwy[j] += a[l] * t.Hy[j * (I.Ny + 1) + l];
+        if (I.reduced) {  // phi_w and chi_w = T_w phi_w
+            t.gwy[0] = 1.0;
+            t.gwy[1] = d.T_w;
+        } else {
+            full_coeffs(0.0, d.T_w, I.Ny, a);
+            for (int j = 0; j < I.Qy; ++j)
+                for (int l = 0; l <= I.Ny; ++l) t.gwy[j] += a[l] * t.Hy[j * (I.Ny + 1) + l];
+        }
         half_coeffs(0.0, d.T_w, I.Nzq, t.alpha.data(), t.beta.data(), bb);
         for (int m = 0; m < I.Qz; ++m)
             for (int l = 0; l <= I.Nzq; ++l) {
@@ -331,6 +347,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         D.nchunks = I.nchunks;
         D.nchh = I.nchh;
         D.half = half;
+        D.reduced = I.reduced;
         // every row segment (row s, chunk start k0 in either half) starts on 16 bytes
         D.bulk = ((size_t)(I.Q / 2) * sizeof(T)) % 16 == 0;
         D.visc_law = d.visc.law; D.Kn = d.Kn; D.visc_param = d.visc.omega_or_S; D.Pr = d.Pr;
@@ -349,6 +366,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         double sxt = 0, sxb = 0, sy = 0, szp = 0, szm = 0;
         for (int i = 0; i < I.Qx; ++i) { sxt += wx[i] * gxt[i]; sxb += wx[i] * gxb[i]; }
         for (int j = 0; j < I.Qy; ++j) sy += wy[j] * gwy[j];
+        if (I.reduced) sy = gwy[0];  // mass is carried by phi alone
         for (int m = 0; m < I.Qz; ++m) {
             szp += wz[m] * xi[m] * gwz[m];
             szm += wz[m] * (-xi[m]) * gwz[I.Qz + m];
@@ -363,6 +381,10 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
                 for (int i = 0; i < I.Qx; ++i) D.wsum[0][l] += wx[i] * Hx[i * (I.Nx + 1) + l];
             for (int l = 0; l <= I.Ny; ++l)
                 for (int j = 0; j < I.Qy; ++j) D.wsum[1][l] += wy[j] * Hy[j * (I.Ny + 1) + l];
+            if (I.reduced) {  // the mass sum of R_SCALE counts phi (factor a_0) only
+                D.wsum[1][0] = 1.0;
+                D.wsum[1][1] = 0.0;
+            }
             for (int l = 0; l <= I.Nzq; ++l)
                 for (int m = 0; m < I.Qz; ++m) D.wsum[2][l] += wz[m] * Pz[m * (I.Nzq + 1) + l];
             for (int l = 0; l <= I.Nzq; ++l) D.wsum[3][l] = D.wsum[2][l];
@@ -479,7 +501,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
 // moments, records, wall densities and W_old of the current F0 (every active instance)
 static lbs_status analyse(lbs_solver* h)
 {
-    CK(launch_stage(h->fp32, h->V, 0, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->ninst, h->maxNz,
+    CK(launch_stage(h->fp32, h->reduced, h->V, 0, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->ninst, h->maxNz,
                     h->fin_warp, h->stream));
     return LBS_OK;
 }
@@ -493,7 +515,7 @@ static lbs_status enqueue_step(lbs_solver* h)
 {
     if (!split(h)) {
         for (int s = 1; s <= 3; ++s)
-            CK(launch_stage(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->ninst,
+            CK(launch_stage(h->fp32, h->reduced, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->ninst,
                             h->maxNz, h->fin_warp, h->stream));
         return LBS_OK;
     }
@@ -502,9 +524,9 @@ static lbs_status enqueue_step(lbs_solver* h)
     // the stage kernel finds a tile's instance by its absolute index (full descriptor
     // array, a range of tiles); the finalisation kernels take a range of instances
     for (int s = 1; s <= 3; ++s) {
-        CK(launch_stage_only(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntilesA, h->smem, 0, h->stream));
+        CK(launch_stage_only(h->fp32, h->reduced, h->V, s, h->d_inst, h->d_tiles, h->ntilesA, h->smem, 0, h->stream));
         CK(launch_finalize(h->fp32, s, h->d_inst, h->nA, h->maxNz, h->fin_warp, h->stream));
-        CK(launch_stage_only(h->fp32, h->V, s, h->d_inst, h->d_tiles + h->ntilesA, h->ntiles - h->ntilesA, h->smem,
+        CK(launch_stage_only(h->fp32, h->reduced, h->V, s, h->d_inst, h->d_tiles + h->ntilesA, h->ntiles - h->ntilesA, h->smem,
                              0, h->stream2));
         CK(launch_finalize(h->fp32, s, h->d_inst + h->nA, h->ninst - h->nA, h->maxNz, h->fin_warp, h->stream2));
     }
@@ -634,8 +656,11 @@ lbs_status lbs_batch_create(lbs_handle* out, const lbs_instance_desc* desc, int 
     for (int b = 0; b < n; ++b) {
         lbs_status s = validate(desc[b]);
         if (s != LBS_OK) return fail(s, "instance " + std::to_string(b) + ": " + g_err);
+        if ((desc[b].orders.Qy == 0) != (desc[0].orders.Qy == 0))
+            return fail(LBS_ERR_ARG, "a batch cannot mix the reduced (Qy = 0) and the full velocity models");
     }
     lbs_solver* h = new lbs_solver();
+    h->reduced = desc[0].orders.Qy == 0;
     if (cudaGetDevice(&h->device) != cudaSuccess) h->device = 0;
     h->fp32 = prec == LBS_FP32_STORE_FP64_ACC;
     h->esize = h->fp32 ? 4 : 8;
@@ -643,7 +668,8 @@ lbs_status lbs_batch_create(lbs_handle* out, const lbs_instance_desc* desc, int 
     h->ih.resize(n);
     long work = 0;
     for (int b = 0; b < n; ++b)
-        work += (long)desc[b].grid.Nz * 2 * desc[b].orders.Qx * desc[b].orders.Qy * desc[b].orders.Qz_half;
+        work += (long)desc[b].grid.Nz * 2 * desc[b].orders.Qx * std::max(desc[b].orders.Qy, 2) *
+                desc[b].orders.Qz_half;
     // untuned default: small batches are latency-bound (short z-tiles, one velocity per
     // thread, more CTAs); large ones take the throughput tiling.  Finalisation apart.
     h->V = work >= (1L << 22) ? 4 : 1;
@@ -785,7 +811,7 @@ lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms)
     for (long it = 0; it < nsteps && st == LBS_OK; ++it) {
         CK(cudaEventRecord(ev[0], h->stream));
         for (int s = 1; s <= 3; ++s) {
-            CK(launch_stage_only(h->fp32, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->stream));
+            CK(launch_stage_only(h->fp32, h->reduced, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->stream));
             CK(cudaEventRecord(ev[2 * s - 1], h->stream));
             if (!(h->fuse & 1)) CK(launch_finalize(h->fp32, s, h->d_inst, h->ninst, h->maxNz, h->fin_warp, h->stream));
             CK(cudaEventRecord(ev[2 * s], h->stream));

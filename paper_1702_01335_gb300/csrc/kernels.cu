@@ -295,7 +295,12 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
         rec[R_AX + l] = v;
         if (l <= I.Nx) s[0] += double(v) * I.wsum[0][l];
     }
-    full_coeffs(u1, Tc, I.Ny, c);
+    if (I.reduced) {  // y factors of phi and chi: 1 and T (basis: the identity on j)
+        c[0] = 1.0;
+        c[1] = Tc;
+    } else {
+        full_coeffs(u1, Tc, I.Ny, c);
+    }
     s[1] = 0.0;
 #pragma unroll
     for (int l = 0; l <= kMaxN; ++l) {
@@ -422,6 +427,10 @@ __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& s
     double c[kMaxN + 1];
     const int Nh = h ? I.Ny : I.Nx;
     full_coeffs(h ? u1 : u0, Tc, Nh, c);
+    if (h && I.reduced) {  // y factors of phi and chi: 1 and T (basis: the identity on j)
+        c[0] = 1.0;
+        c[1] = Tc;
+    }
     double ck = 0.0;
 #pragma unroll
     for (int l = 0; l <= kMaxN; ++l)
@@ -578,15 +587,16 @@ __global__ void records_from_macro(const InstDev* __restrict__ insts, int inst, 
 }
 
 // ----------------------------------------------------------------------------
-// stage_kernel<T, V, STAGE>: STAGE 1..3 are the RK stages; STAGE 0 only
-// analyses F0 (moments and wall fluxes) without writing F.
+// stage_kernel<T, V, STAGE, RED>: STAGE 1..3 are the RK stages; STAGE 0 only
+// analyses F0 (moments and wall fluxes) without writing F.  RED selects the
+// phi / chi model (Sec. III, Eqs. boltz_red, sred_def): j = 0 is phi, j = 1 chi.
 // ----------------------------------------------------------------------------
 // Minimum resident CTAs per SM requested from the register allocator: the
 // per-velocity register window grows with V; the rarely taken finalisation
 // path may spill instead of lowering occupancy.
 template <int V> struct MinBlocks { static constexpr int value = V == 1 ? 8 : V == 2 ? 6 : 3; };
 
-template <typename T, int V, int STAGE>
+template <typename T, int V, int STAGE, bool RED>
 __global__ void __launch_bounds__(kThreads, MinBlocks<V>::value)
 stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, int fuse)
 {
@@ -697,6 +707,19 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         wpsi[v][4] = w * X * X; wpsi[v][5] = w * Y * Y; wpsi[v][6] = w * Z * Z;
         wpsi[v][7] = w * X * Y; wpsi[v][8] = w * X * Z; wpsi[v][9] = w * Y * Z;
         wpsi[v][10] = w * p2 * X; wpsi[v][11] = w * p2 * Y; wpsi[v][12] = w * p2 * Z;
+        if (RED) {
+            // p_y = 0 on both fields.  chi = int p_y^2 f dp_y carries the p_y^2 moments:
+            // sum chi -> sum p_y^2 f, sum p_a chi -> sum p_y^2 p_a f (a = x, z), nothing else.
+            // py[v] then holds -(the Shakhov offset of Eq. sred_def): -4/5 for phi, -2/5 for chi.
+            if (jj[v] == 1) {
+#pragma unroll
+                for (int a = 0; a < kNMom; ++a) wpsi[v][a] = A(0);
+                wpsi[v][5] = w;
+                wpsi[v][10] = w * X;
+                wpsi[v][12] = w * Z;
+            }
+            py[v] = jj[v] ? T(-0.4) : T(-0.8);
+        }
     }
 
     // ---- 3. wait for the copies (bounded); a CTA whose copies never land flags
@@ -829,11 +852,19 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             if (STAGE > 0) {
                 const T flp = apz[v] * weno5<T>(w[v][1], w[v][2], w[v][3], w[v][4], w[v][5]);
                 const T f = w[v][3];
-                // Shakhov target n Gx Gy Gz (1 + S), S = cS (xi^2/(5T) - 1) xi.q
-                const T ex = px[v] - ux, ey = py[v] - uy, ez = pz[v] - uz;
-                const T xi2 = ex * ex + ey * ey + ez * ez;
-                const T xq = ex * qx + ey * qy + ez * qz;
-                const T S = cS * (xi2 * i5T - T(1)) * xq;
+                // Shakhov target n Gx Gy Gz (1 + S), S = cS (xi^2/(5T) - 1) xi.q; in the
+                // phi / chi model (Eq. sred_def) S = cS ((xi_x^2 + xi_z^2)/(5T) - 4/5 or 2/5) xi.q
+                // with u_y = q_y = 0, and Gy = 1 (phi) or T (chi) from the record
+                T S;
+                if (RED) {
+                    const T ex = px[v] - ux, ez = pz[v] - uz;
+                    S = cS * ((ex * ex + ez * ez) * i5T + py[v]) * (ex * qx + ez * qz);
+                } else {
+                    const T ex = px[v] - ux, ey = py[v] - uy, ez = pz[v] - uz;
+                    const T xi2 = ex * ex + ey * ey + ez * ez;
+                    const T xq = ex * qx + ey * qy + ez * qz;
+                    S = cS * (xi2 * i5T - T(1)) * xq;
+                }
                 const T geq = gc[ii[v]] * gc[Qx + jj[v]] * gc[Qx + Qy + zz[v] - zm_lo];
                 // the advection and relaxation increments nearly cancel near a steady
                 // state: combine them first, then add to f once
@@ -994,7 +1025,9 @@ __global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ in
         for (int l = 0; l <= I.Nzq; ++l) gz += rc[(sg ? R_BM : R_BP) + l] * ld<T>(I.Pz, m * (I.Nzq + 1) + l);
         const T x = ld<T>(I.xi, m);
         const T ex = ld<T>(I.px, i) - rc[R_UX], ey = ld<T>(I.py, j) - rc[R_UY], ez = (sg ? -x : x) - rc[R_UZ];
-        const T S = rc[R_CS] * ((ex * ex + ey * ey + ez * ez) * rc[R_I5T] - T(1)) *
+        const T S = I.reduced ? rc[R_CS] * ((ex * ex + ez * ez) * rc[R_I5T] - (j ? T(0.4) : T(0.8))) *
+                                    (ex * rc[R_QX] + ez * rc[R_QZ])
+                              : rc[R_CS] * ((ex * ex + ey * ey + ez * ez) * rc[R_I5T] - T(1)) *
                     (ex * rc[R_QX] + ey * rc[R_QY] + ez * rc[R_QZ]);
         F[k] = rc[R_SCALE] * gx * gy * gz * (T(1) + S);
     }
@@ -1007,27 +1040,35 @@ size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int nhx, int 
     return stage_smem(zn, KC, G, fp32 ? 4 : 8, fp32 ? 4 : 8, stage >= 2, nhx, nhy, npz).total;
 }
 
-template <typename T, int V, int STAGE>
+template <typename T, int V, int STAGE, bool RED>
 static cudaError_t launch_stage_t(const InstDev* d_inst, const Tile* d_tiles, int ntiles, size_t smem,
                                   int fuse, cudaStream_t st)
 {
-    auto kfn = stage_kernel<T, V, STAGE>;
+    auto kfn = stage_kernel<T, V, STAGE, RED>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kfn<<<ntiles, kThreads, smem, st>>>(d_inst, d_tiles, fuse);
     return cudaGetLastError();
 }
 
-template <typename T, int V>
-static cudaError_t launch_stage_v(int stage, const InstDev* d, const Tile* t, int n, size_t smem, int fuse,
+template <typename T, int V, bool RED>
+static cudaError_t launch_stage_r(int stage, const InstDev* d, const Tile* t, int n, size_t smem, int fuse,
                                   cudaStream_t st)
 {
     switch (stage) {
-        case 0: return launch_stage_t<T, V, 0>(d, t, n, smem, fuse, st);
-        case 1: return launch_stage_t<T, V, 1>(d, t, n, smem, fuse, st);
-        case 2: return launch_stage_t<T, V, 2>(d, t, n, smem, fuse, st);
-        default: return launch_stage_t<T, V, 3>(d, t, n, smem, fuse, st);
+        case 0: return launch_stage_t<T, V, 0, RED>(d, t, n, smem, fuse, st);
+        case 1: return launch_stage_t<T, V, 1, RED>(d, t, n, smem, fuse, st);
+        case 2: return launch_stage_t<T, V, 2, RED>(d, t, n, smem, fuse, st);
+        default: return launch_stage_t<T, V, 3, RED>(d, t, n, smem, fuse, st);
     }
+}
+
+template <typename T, int V>
+static cudaError_t launch_stage_v(int red, int stage, const InstDev* d, const Tile* t, int n, size_t smem,
+                                  int fuse, cudaStream_t st)
+{
+    return red ? launch_stage_r<T, V, true>(stage, d, t, n, smem, fuse, st)
+               : launch_stage_r<T, V, false>(stage, d, t, n, smem, fuse, st);
 }
 
 template <typename T>
@@ -1042,18 +1083,18 @@ static cudaError_t launch_finalize_t(int stage, const InstDev* d_inst, int ninst
 }
 
 // the stage kernel alone
-cudaError_t launch_stage_only(int fp32, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
+cudaError_t launch_stage_only(int fp32, int red, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
                               int ntiles, size_t smem, int fuse, cudaStream_t st)
 {
     cudaError_t e;
     if (fp32) {
-        if (V == 1) e = launch_stage_v<float, 1>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
-        else if (V == 2) e = launch_stage_v<float, 2>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
-        else e = launch_stage_v<float, 4>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+        if (V == 1) e = launch_stage_v<float, 1>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+        else if (V == 2) e = launch_stage_v<float, 2>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+        else e = launch_stage_v<float, 4>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
     } else {
-        if (V == 1) e = launch_stage_v<double, 1>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
-        else if (V == 2) e = launch_stage_v<double, 2>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
-        else e = launch_stage_v<double, 4>(stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+        if (V == 1) e = launch_stage_v<double, 1>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+        else if (V == 2) e = launch_stage_v<double, 2>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+        else e = launch_stage_v<double, 4>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
     }
     return e;
 }
@@ -1068,10 +1109,10 @@ cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int nins
 
 // one RK stage (stage 1..3) or the analysis pass (stage 0); without fusion the
 // finalisation follows as two more launches
-cudaError_t launch_stage(int fp32, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
+cudaError_t launch_stage(int fp32, int red, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
                          int ntiles, size_t smem, int fuse, int ninst, int maxNz, int fin_warp, cudaStream_t st)
 {
-    cudaError_t e = launch_stage_only(fp32, V, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+    cudaError_t e = launch_stage_only(fp32, red, V, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
     if (e != cudaSuccess || fuse) return e;
     return launch_finalize(fp32, stage, d_inst, ninst, maxNz, fin_warp, st);
 }

@@ -38,6 +38,7 @@ struct InstDev {
     int nchh;                     // chunks per half range of p_z (chunk c has p_z < 0 iff c >= nchh)
     int half;                     // 1: half channel, bounce-back ghosts below cell 0 (no bottom wall)
     int fin_warp;                 // finalisation with one warp per cell (small batches) instead of one thread
+    int reduced;                  // 1: the phi / chi model (Qy = 2: j = 0 phi, j = 1 chi; p_y unused)
     int visc_law;
     double Kn, visc_param, Pr, dt, tol;
     double iKn, isuth;            // 1 / Kn; Sutherland: 1 / (1 + S)

@@ -48,6 +48,12 @@ __global__ void __launch_bounds__(128) static_partials(const InstDev* __restrict
         const double w = double(static_cast<const T*>(I.wx)[i]) * double(static_cast<const T*>(I.wy)[j]) *
                          double(static_cast<const T*>(I.wz)[m]);
         const double g = w * double(f[(size_t)cell * Q + k]);
+        if (I.reduced && j == 1) {  // chi = int p_y^2 f dp_y: the p_y^2 moments only
+            acc[5] += g;
+            acc[10] += g * X;
+            acc[12] += g * Z;
+            continue;
+        }
         const double p2 = X * X + Y * Y + Z * Z;
         acc[0] += g;
         acc[1] += g * X; acc[2] += g * Y; acc[3] += g * Z;

@@ -173,7 +173,8 @@ class Instance:
 
     @property
     def Q(self):
-        return 2 * self.Qx * self.Qy * self.Qz
+        """Stored values per cell (Qy = 0, the phi / chi model: two fields per node)."""
+        return 2 * self.Qx * (self.Qy if self.Qy else 2) * self.Qz
 
 
 def _torch_stream():

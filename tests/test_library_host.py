@@ -58,13 +58,17 @@ def test_bad_arguments_are_rejected():
         L.Instance(Qx=0), L.Instance(Qz=65), L.Instance(N_eq=9), L.Instance(Nz=5),
         L.Instance(Kn=0.0), L.Instance(T_w=-1.0), L.Instance(Pr=0.0), L.Instance(A=1.0),
         L.Instance(cfl=0.0, dt=0.0), L.Instance(visc_law=1, visc_param=0.0),
-        L.Instance(Qx=64, Qy=64, Qz=64), L.Instance(half=2),
+        L.Instance(Qx=64, Qy=64, Qz=64), L.Instance(half=2), L.Instance(Qy=-1),
     ]
     for inst in bad:
         d = (L._Desc * 1)(inst.desc())
         st = lib.lbs_batch_create(C.byref(h), d, 1, 0, None)
         assert st == 1, inst
         assert lib.lbs_last_error().decode()
+    mixed = (L._Desc * 2)(L.Instance(Qy=0).desc(), L.Instance().desc())
+    assert lib.lbs_batch_create(C.byref(h), mixed, 2, 0, None) == 1
+    assert "mix" in lib.lbs_last_error().decode()
+    assert L.Instance(Qy=0, Qx=5, Qz=6).Q == 4 * 5 * 6
     assert lib.lbs_quadrature(2, 4, None, None) == 1
     assert lib.lbs_step(None, 1) == 1
     prof = np.zeros((14, 12))

@@ -37,17 +37,18 @@ TABLE_DELTAS = (0.1, 1.0, 10.0, 20.0, 40.0)
 TABLE_RUN = {0.01: (100, 2.5e-4), 0.1: (30, 2.5e-4)}   # delta -> (Q_n, dt); else (7, 5e-4)
 
 
-def paper_tables():
+def paper_tables(reduced=False):
     """The 20 half-channel runs of the Sec. VI tables as (label, instance parameters)
     pairs, gas-major, then delta, then u_w = sqrt 2 before 0.1 sqrt 2; the label holds
-    gas, delta and u_w."""
+    gas, delta and u_w.  reduced=True: the paper's phi / chi model (Qy = 0) instead of
+    the 3D set with Q_y = 7."""
     out = []
     for gas in ("Ar", "He"):
         for d in TABLE_DELTAS:
             Qn, dt = TABLE_RUN.get(d, (7, 5e-4))
             for uw in (2.0 ** 0.5, 0.1 * 2.0 ** 0.5):
                 out.append((dict(gas=gas, delta=d, uw=uw),
-                            dict(Qx=7, Qy=7, Qz=Qn, N_eq=6, Nz=16, A=0.98, half=1, Kn=1.0 / (d * 2.0 ** 0.5),
+                            dict(Qx=7, Qy=0 if reduced else 7, Qz=Qn, N_eq=6, Nz=16, A=0.98, half=1, Kn=1.0 / (d * 2.0 ** 0.5),
                                  u_w=uw, T_w=1.0, Pr=2.0 / 3.0, visc_law=1, visc_param=SUTHERLAND_S[gas],
                                  dt=dt)))
     return out
