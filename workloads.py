@@ -14,6 +14,8 @@ plain dict of instance parameters with the field names of
       channel: 16 cells stretched with A = 0.98, 7 x 7 x (2 x Q_n) velocities with
       N_eq = 6, Sutherland viscosity, Pr = 2/3, delta = 1/(Kn sqrt 2) in
       {0.1, 1, 10, 20, 40}, u_w in {sqrt 2, 0.1 sqrt 2}; Q_n and dt from Table sharipov
+  luo_runs()  the low-Mach runs of Sec. IV (Table luo): phi / chi model, Qx = 2,
+      BGK, tau = k / sqrt 2, u_w = 1e-5, half channel with S = 64 or 32, A = 0.98
   sweep(n, seed)  instances drawn like the batched Kn / wall-speed / gas-law sweep:
       Kn log-uniform in [0.01, 100], u_w uniform in [0.05, 1], T_w = 1, Pr = 2/3,
       first half mu ~ T^omega (omega uniform in [0.5, 1]), second half Sutherland
@@ -51,6 +53,23 @@ def paper_tables(reduced=False):
                             dict(Qx=7, Qy=0 if reduced else 7, Qz=Qn, N_eq=6, Nz=16, A=0.98, half=1, Kn=1.0 / (d * 2.0 ** 0.5),
                                  u_w=uw, T_w=1.0, Pr=2.0 / 3.0, visc_law=1, visc_param=SUTHERLAND_S[gas],
                                  dt=dt)))
+    return out
+
+
+# Sec. IV (Table luo): the low-Mach runs.  k -> (N, Q_n, S); k = 10 needs Q_n = 80,
+# above the solver's per-axis limit of 64, and is left out.
+LUO_RUNS = {0.03: (3, 4, 64), 0.1: (6, 7, 32), 1.0: (6, 21, 32)}
+
+
+def luo_runs(u_w=1e-5):
+    """The low-Mach half-channel runs of Sec. IV as (label, instance parameters): the
+    phi / chi model with the HLB(1;2) rule along the flow (Qx = 2), the half-range
+    order and grid of Table luo (A = 0.98), BGK (Pr = 1), tau = k / sqrt 2 (the power
+    law with omega = 1 gives Kn / n, and n = 1 to O(u_w^2)), u_w = 1e-5, T_w = 1."""
+    out = []
+    for k, (N, Qn, S) in LUO_RUNS.items():
+        out.append((dict(k=k), dict(Qx=2, Qy=0, Qz=Qn, N_eq=N, Nz=S, A=0.98, half=1, Kn=k / 2.0 ** 0.5,
+                                    u_w=u_w, T_w=1.0, Pr=1.0, visc_law=0, visc_param=1.0)))
     return out
 
 
