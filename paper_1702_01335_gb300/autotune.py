@@ -24,10 +24,14 @@ CANDIDATES = tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (4, 6, 8, 12, 16, 24,
 _cache = {}
 
 
+_KERNEL_SOURCES = ("kernels.cuh", "kernels.cu", "lbs_internal.h", "stage_f32_full.cu", "stage_f32_red.cu",
+                   "stage_f64_full.cu", "stage_f64_red.cu")
+
+
 def kernel_hash():
     """Hash of the stage kernel's sources: a cached choice is ignored once they change."""
     h = hashlib.sha256()
-    for f in ("kernels.cu", "lbs_internal.h"):
+    for f in _KERNEL_SOURCES:
         h.update(open(os.path.join(_CSRC, f), "rb").read())
     return h.hexdigest()[:16]
 

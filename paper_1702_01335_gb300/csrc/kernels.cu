@@ -1,968 +1,9 @@
-// CUDA kernels of one RK-3 stage of the mixed-quadrature Shakhov scheme.
-//
-// Per stage (Eq. rk3 around Eq. L_def):
-//   stage_kernel     one CTA per tile = (instance, z-range of <= 64 cells,
-//                    velocity chunk of 128*V velocities).  The rows of F_in
-//                    the tile needs (its cells and a 3-cell halo each side) and
-//                    its rows of F_l are staged into shared memory by TMA bulk
-//                    copies (one cp.async.bulk per row, one mbarrier).  While
-//                    they land, the CTA evaluates the per-axis factors of the
-//                    truncated Hermite equilibrium (Sec. III) of its cells.
-//                    Ghost rows are then built in shared memory: outgoing
-//                    populations by the quadratic extrapolation of the
-//                    Appendix, incoming ones as n_w times the wall equilibrium.
-//                    Each thread marches up the z-range for its V velocities
-//                    with a register window: WENO-5 interface fluxes (Eqs.
-//                    weno5_flux - weno_sigma, Table weno), the divergence of
-//                    Eq. (flux), relaxation to n G_x G_y G_z (1 + S) and the
-//                    Shu-Osher combine; it stores F_out and accumulates the raw
-//                    moments of F_out (FP32 within a warp in FP32 mode, FP64
-//                    across warps and chunks).  Tiles that end at a wall also
-//                    reduce the outgoing WENO flux of F_out through the wall.
-//                    Finalisation needs no further launch: the CTA that ends
-//                    last among the chunks of a z-tile (threadfence tickets)
-//                    sums their partials in FP64 per cell, forms n, u, P, T, q
-//                    (Eq. qdef) and tau, and writes the cell records of the
-//                    next stage; the one that completes an instance's last
-//                    z-tile forms the wall densities n_w (zero net mass flux,
-//                    Appendix) and, after the third stage, the residual.
-//
-// Storage: F[s][k] for interior cells s = 0..Nz-1 (no ghost rows), velocity
-// k = ((sg*Qz + m)*Qx + i)*Qy + j fastest, holding f_k / w_k.
-#include <cuda_runtime.h>
-
-#include <cstdint>
-
-#include "lbs_internal.h"
+// Finalisation and seeding kernels and the launchers of every kernel of the
+// scheme (the device code shared with the stage kernel is in kernels.cuh; the
+// stage kernel's instantiations are in the stage_*.cu translation units).
+#include "kernels.cuh"
 
 namespace lbs {
-
-template <typename T> struct Acc { typedef double type; };
-template <> struct Acc<float> { typedef float type; };
-
-constexpr uint32_t kSpinLimit = 1u << 26;  // bounded mbarrier waits (~seconds)
-
-// ---- PTX helpers: mbarrier and bulk global -> shared copies ------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_barrier_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// WENO-5 reconstruction of five upwind-ordered values (no advection factor).
-// The weights are scale free, so they are formed from r_q = sigma_q / max
-// sigma; an r_q below kTiny counts as vanishing and the weights of Table
-// (weno) apply (proportional to the ideal weights over the vanishing set).
-template <typename T>
-__device__ __forceinline__ T weno5(T v0, T v1, T v2, T v3, T v4)
-{
-    const T kTiny = sizeof(T) == 8 ? T(1e-150) : T(1e-18);
-    const T c1 = v0 * T(1.0 / 3.0) - v1 * T(7.0 / 6.0) + v2 * T(11.0 / 6.0);
-    const T c2 = -v1 * T(1.0 / 6.0) + v2 * T(5.0 / 6.0) + v3 * T(1.0 / 3.0);
-    const T c3 = v2 * T(1.0 / 3.0) + v3 * T(5.0 / 6.0) - v4 * T(1.0 / 6.0);
-    T a = v0 - T(2) * v1 + v2, b = v0 - T(4) * v1 + T(3) * v2;
-    const T s1 = T(13.0 / 12.0) * a * a + T(0.25) * b * b;
-    a = v1 - T(2) * v2 + v3;
-    b = v1 - v3;
-    const T s2 = T(13.0 / 12.0) * a * a + T(0.25) * b * b;
-    a = v2 - T(2) * v3 + v4;
-    b = T(3) * v2 - T(4) * v3 + v4;
-    const T s3 = T(13.0 / 12.0) * a * a + T(0.25) * b * b;
-    const T smax = fmax(s1, fmax(s2, s3));
-    T w1, w2, w3;
-    if (smax == T(0)) {
-        w1 = T(0.1); w2 = T(0.6); w3 = T(0.3);
-    } else {
-        const T inv = T(1) / smax;
-        const T r1 = s1 * inv, r2 = s2 * inv, r3 = s3 * inv;
-        const bool z1 = r1 < kTiny, z2 = r2 < kTiny, z3 = r3 < kTiny;
-        if (z1 | z2 | z3) {
-            w1 = z1 ? T(0.1) : T(0); w2 = z2 ? T(0.6) : T(0); w3 = z3 ? T(0.3) : T(0);
-        } else {
-            w1 = T(0.1) / (r1 * r1); w2 = T(0.6) / (r2 * r2); w3 = T(0.3) / (r3 * r3);
-        }
-    }
-    return (w1 * c1 + w2 * c2 + w3 * c3) / (w1 + w2 + w3);
-}
-
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// FP32 form: the same weights with sigma_q^2 floored at 1e-37 (branch free,
-// hardware reciprocals).  As sigma_q -> 0 the floor gives exactly the limits
-// of Table (weno); it changes nothing while sigma_q^2 > 1e-30, i.e. for
-// differences above the FP32 resolution of O(1) normalised populations.  The
-// candidate reconstructions are written as v2 plus corrections made of
-// differences (c_q = v2 + e_q / 6), so a constant stencil gives exactly its
-// value (the incoming ghosts at a wall: the flux is then exactly the wall
-// Maxwellian's, as Table weno implies) and the rounded weights only multiply the
-// small corrections.
-template <>
-__device__ __forceinline__ float weno5<float>(float v0, float v1, float v2, float v3, float v4)
-{
-    const float d0 = v0 - v2, d1 = v1 - v2, d3 = v3 - v2, d4 = v4 - v2;
-    const float e1 = fmaf(2.f, d0, -7.f * d1);   // 6 (c1 - v2)
-    const float e2 = fmaf(2.f, d3, -d1);         // 6 (c2 - v2)
-    const float e3 = fmaf(5.f, d3, -d4);         // 6 (c3 - v2)
-    float a = d0 - 2.f * d1, b = fmaf(-4.f, d1, d0);          // v0-2v1+v2, v0-4v1+3v2
-    const float s1 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
-    a = d1 + d3;                                             // v1-2v2+v3
-    b = d1 - d3;                                             // v1-v3
-    const float s2 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
-    a = fmaf(-2.f, d3, d4);                                  // v2-2v3+v4
-    b = fmaf(-4.f, d3, d4);                                  // 3v2-4v3+v4
-    const float s3 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
-    const float w1 = 0.1f * rcp_approx(fmaf(s1, s1, 1e-37f));
-    const float w2 = 0.6f * rcp_approx(fmaf(s2, s2, 1e-37f));
-    const float w3 = 0.3f * rcp_approx(fmaf(s3, s3, 1e-37f));
-    const float inv = (1.f / 6.f) * rcp_approx(w1 + w2 + w3);
-    return fmaf(fmaf(w1, e1, fmaf(w2, e2, w3 * e3)), inv, v2);
-}
-
-template <typename T>
-__device__ __forceinline__ T ld(const void* p, int i) { return static_cast<const T*>(p)[i]; }
-
-// Block-wide FP64 sum (all threads get the result); deterministic order.
-__device__ double block_sum(double v, double* red)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int i = 0; i < nw; ++i) s += red[i];
-    __syncthreads();
-    return s;
-}
-
-// N block sums at once (one pair of barriers for all of them); red holds
-// N * (blockDim.x / 32) doubles.  Each sum keeps block_sum's order.
-template <int N>
-__device__ void block_sum_n(double (&v)[N], double* red)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int i = 0; i < N; ++i) red[i * nw + w] = v[i];
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < nw; ++j) s += red[i * nw + j];
-        v[i] = s;
-    }
-    __syncthreads();
-}
-constexpr int kRedSlots = 8 * (kThreads / 32);  // shared doubles for block_sum_n<8> with 128 threads
-
-// Warp reduce-scatter of 16 values: afterwards lane l holds the warp total of
-// value m(l) = 8 b4 + 4 b3 + 2 b2 + b1 (b = bits of l); lanes l, l^1 agree.
-// 16 shuffles per lane instead of 16 x 5 for 16 separate butterflies.
-template <typename A>
-__device__ __forceinline__ A reduce_scatter16(A (&v)[16], int lane)
-{
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const bool hi = lane & 16;
-        const A send = hi ? v[i] : v[i + 8], keep = hi ? v[i + 8] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const bool hi = lane & 8;
-        const A send = hi ? v[i] : v[i + 4], keep = hi ? v[i + 4] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool hi = lane & 4;
-        const A send = hi ? v[i] : v[i + 2], keep = hi ? v[i + 2] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    {
-        const bool hi = lane & 2;
-        const A send = hi ? v[0] : v[1], keep = hi ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
-
-// shared-memory layout of a stage CTA (offsets in bytes): staged F_in rows,
-// F_l rows, the cell records and the Hermite basis tables (all by bulk copy),
-// the evaluated per-axis factors, 1/dz, and the per-warp moment sums.
-struct StageSmem {
-    size_t fin, f0, rec, hx, hy, pz, g, idz, red, total;
-};
-__host__ __device__ inline size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
-__host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize, int asize, bool withF0,
-                                                int nhx, int nhy, int npz)
-{
-    StageSmem L;
-    size_t o = 0;
-    L.fin = o; o += (size_t)(zn + 6) * KC * esize;
-    L.f0 = o; o += withF0 ? (size_t)zn * KC * esize : 0;
-    L.rec = o; o += (size_t)zn * kRecStride * esize;
-    L.hx = o; o += pad16((size_t)nhx * esize);
-    L.hy = o; o += pad16((size_t)nhy * esize);
-    L.pz = o; o += pad16((size_t)npz * esize);
-    L.g = o; o += pad16((size_t)zn * G * esize);
-    L.idz = o; o += pad16((size_t)zn * esize);
-    L.red = o; o += (size_t)zn * (kThreads / 32) * 16 * asize;
-    L.total = o;
-    return L;
-}
-
-// ----------------------------------------------------------------------------
-// Cell record from a macroscopic state: scalars and the coefficients a_l, b_l
-// of the truncated Hermite equilibrium (Sec. III, Eqs. fyz, Fmn_def), FP64.
-// Returns false for a non-finite or non-positive state (a neutral state is
-// written instead).
-// ----------------------------------------------------------------------------
-// Cell record of a macroscopic state: the scalars and the coefficients a_l, b_l
-// of the truncated Hermite equilibrium (Sec. III, Eqs. fyz, Fmn_def), computed in
-// FP64 (the half-range ones cancel strongly for N >= 4).  Returns false for a
-// non-finite or non-positive state (a neutral state is written instead).
-template <typename T>
-__device__ bool write_record(const InstDev& I, int cell, double n, double in, const double* u, double T_,
-                             const double* q)
-{
-    // in = 1 / n (the callers have it); FP64 divisions are costly here, so 1/T is the
-    // only other one before R_SCALE
-    bool bad = !(n > 0.0) || !(T_ > 0.0) || !isfinite(n) || !isfinite(T_);
-    for (int a = 0; a < 3; ++a) bad |= !isfinite(u[a]) || !isfinite(q[a]);
-    const double nn = bad ? 1.0 : n, inn = bad ? 1.0 : in, Tc = bad ? 1.0 : T_;
-    const double u0 = bad ? 0.0 : u[0], u1 = bad ? 0.0 : u[1], u2 = bad ? 0.0 : u[2];
-    T* rec = static_cast<T*>(I.rec) + (size_t)cell * kRecStride;
-    const double iT = 1.0 / Tc;
-    rec[R_N] = T(nn); rec[R_UX] = T(u0); rec[R_UY] = T(u1); rec[R_UZ] = T(u2); rec[R_T] = T(Tc);
-    rec[R_QX] = T(bad ? 0.0 : q[0]); rec[R_QY] = T(bad ? 0.0 : q[1]); rec[R_QZ] = T(bad ? 0.0 : q[2]);
-    rec[R_ITAU] = T(inv_relax_time(I.visc_law, I.iKn, I.visc_param, I.isuth, nn, Tc, iT));
-    rec[R_CS] = T((1.0 - I.Pr) * inn * iT * iT);
-    rec[R_I5T] = T(0.2 * iT);
-    // R_SCALE multiplies the x factors so that the discrete equilibrium carries
-    // exactly n: in exact arithmetic sum_i wx Gx = 1, sum_j wy Gy = 1 and the sum
-    // over both half ranges of wz Gz = 1 (orthogonality of the bases); with
-    // coefficients and bases rounded to the storage type the sums miss by a few
-    // ulps of the same sign every step, which would let FP32 runs drift in mass.
-    // The sums are sum_l c_l W_l with the stored coefficients c_l and the
-    // weighted sums W_l of the stored basis tables (computed at set-up).
-    double c[kMaxN + 1], cm[kMaxN + 1], s[3];
-    full_coeffs(u0, Tc, I.Nx, c);
-    s[0] = 0.0;
-#pragma unroll
-    for (int l = 0; l <= kMaxN; ++l) {
-        const T v = l <= I.Nx ? T(c[l]) : T(0);
-        rec[R_AX + l] = v;
-        if (l <= I.Nx) s[0] += double(v) * I.wsum[0][l];
-    }
-    if (I.reduced) {  // y factors of phi and chi: 1 and T (basis: the identity on j)
-        c[0] = 1.0;
-        c[1] = Tc;
-    } else {
-        full_coeffs(u1, Tc, I.Ny, c);
-    }
-    s[1] = 0.0;
-#pragma unroll
-    for (int l = 0; l <= kMaxN; ++l) {
-        const T v = l <= I.Ny ? T(c[l]) : T(0);
-        rec[R_AY + l] = v;
-        if (l <= I.Ny) s[1] += double(v) * I.wsum[1][l];
-    }
-    half_coeffs_pm(u2, Tc, iT, I.Nzq, I.alpha, I.beta, c, cm);
-    s[2] = 0.0;
-#pragma unroll
-    for (int l = 0; l <= kMaxN; ++l) {
-        const T vp = l <= I.Nzq ? T(c[l]) : T(0), vm = l <= I.Nzq ? T(cm[l]) : T(0);
-        rec[R_BP + l] = vp;
-        rec[R_BM + l] = vm;
-        if (l <= I.Nzq) s[2] += double(vp) * I.wsum[2][l] + double(vm) * I.wsum[3][l];
-    }
-    rec[R_SCALE] = T(nn / (s[0] * s[1] * s[2]));
-    return !bad;
-}
-
-// Macroscopic state of a cell from its 13 raw moments (FP64): n, u, the central
-// second moments P_ab = sum p_a p_b f - n u_a u_b, T = tr P / (3n) and the heat flux
-// q_a = 1/2 sum |xi|^2 xi_a f with xi = p - u (Eq. qdef), expanded in raw moments.
-struct CellState {
-    double n, in, u[3], T, q[3], P[6];  // P: xx, yy, zz, xy, xz, yz
-};
-__device__ __forceinline__ void cell_state(const double* mom, CellState& c)
-{
-    const double n = mom[0], in = 1.0 / n;
-    c.n = n;
-    c.in = in;
-    c.u[0] = mom[1] * in; c.u[1] = mom[2] * in; c.u[2] = mom[3] * in;
-    const double* u = c.u;
-    c.P[0] = mom[4] - n * u[0] * u[0]; c.P[1] = mom[5] - n * u[1] * u[1];
-    c.P[2] = mom[6] - n * u[2] * u[2]; c.P[3] = mom[7] - n * u[0] * u[1];
-    c.P[4] = mom[8] - n * u[0] * u[2]; c.P[5] = mom[9] - n * u[1] * u[2];
-    c.T = (c.P[0] + c.P[1] + c.P[2]) * (1.0 / 3.0) * in;
-    const double M2[3][3] = {{mom[4], mom[7], mom[8]}, {mom[7], mom[5], mom[9]}, {mom[8], mom[9], mom[6]}};
-    const double tr = mom[4] + mom[5] + mom[6];
-    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const double um = u[0] * mom[1] + u[1] * mom[2] + u[2] * mom[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double uM2 = u[0] * M2[0][a] + u[1] * M2[1][a] + u[2] * M2[2][a];
-        c.q[a] = 0.5 * (mom[10 + a] - u[a] * tr - 2.0 * uM2 + 2.0 * u[a] * um + uu * mom[1 + a] - uu * u[a] * n);
-    }
-}
-
-// profiles [14][Nz] and W = (n, u_x, T) of a cell; false if any value is not finite
-__device__ __forceinline__ bool store_cell(const InstDev& I, int cell, const CellState& c)
-{
-    const int Nz = I.Nz;
-    const double vals[14] = {c.n, c.u[0], c.u[1], c.u[2], c.T, c.q[0], c.q[1], c.q[2],
-                             c.P[0], c.P[1], c.P[2], c.P[3], c.P[4], c.P[5]};
-    bool bad = false;
-#pragma unroll
-    for (int a = 0; a < 14; ++a) {
-        I.prof[(size_t)a * Nz + cell] = vals[a];
-        bad |= !isfinite(vals[a]);
-    }
-    I.Wnew[cell] = c.n;
-    I.Wnew[Nz + cell] = c.u[0];
-    I.Wnew[2 * Nz + cell] = c.T;
-    return !bad;
-}
-
-// One cell (one thread): FP64 sum of the per-chunk moment partials (written by
-// other CTAs of this launch, hence read past L1), the macroscopic state, the
-// profiles, W for the residual, and the cell record of the next stage.
-template <typename T>
-__device__ void finalize_cell(const InstDev& I, int cell)
-{
-    const int Nz = I.Nz, nch = I.nchunks;
-    double mom[kNMom];
-    for (int a = 0; a < kNMom; ++a) mom[a] = 0.0;
-    // chunks in order, four at a time with every load issued before the adds (the
-    // partials come from L2: one round trip per four chunks instead of per chunk)
-    for (int c = 0; c < nch; c += 4) {
-        double p[4][kNMom];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int a = 0; a < kNMom; ++a)
-                p[j][a] = c + j < nch ? __ldcg(I.partial + ((size_t)(c + j) * kNMom + a) * Nz + cell) : 0.0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int a = 0; a < kNMom; ++a)
-                if (c + j < nch) mom[a] += p[j][a];
-    }
-    CellState st;
-    cell_state(mom, st);
-    bool bad = !store_cell(I, cell, st);
-    bad |= !write_record<T>(I, cell, st.n, st.in, st.u, st.T, st.q);
-    if (bad) atomicOr(I.status, 1);
-}
-
-// ---- one cell per warp: the same record with its FP64 work spread over the lanes.
-// FP64 instructions issue at a small fraction of the FP32 rate, so with one thread
-// per cell a small batch waits on each cell's long FP64 chain; here lane a sums
-// moment a, the two halves of the warp run the x / y coefficient recurrences and
-// the p_z > 0 / p_z < 0 half-range tables side by side, and within a half lane k
-// carries column k of the table J_{l,k} (one shuffle per row instead of the whole
-// triangle in one thread).  Large batches keep one thread per cell, where every
-// lane has a cell of its own.
-template <typename T>
-__device__ bool write_record_warp(const InstDev& I, int cell, const CellState& st, int lane)
-{
-    bool bad = !(st.n > 0.0) || !(st.T > 0.0) || !isfinite(st.n) || !isfinite(st.T);
-    for (int a = 0; a < 3; ++a) bad |= !isfinite(st.u[a]) || !isfinite(st.q[a]);
-    const double nn = bad ? 1.0 : st.n, inn = bad ? 1.0 : st.in, Tc = bad ? 1.0 : st.T;
-    const double u0 = bad ? 0.0 : st.u[0], u1 = bad ? 0.0 : st.u[1], u2 = bad ? 0.0 : st.u[2];
-    T* rec = static_cast<T*>(I.rec) + (size_t)cell * kRecStride;
-    const double iT = 1.0 / Tc;
-    if (lane == 0) {
-        rec[R_N] = T(nn); rec[R_UX] = T(u0); rec[R_UY] = T(u1); rec[R_UZ] = T(u2); rec[R_T] = T(Tc);
-        rec[R_QX] = T(bad ? 0.0 : st.q[0]); rec[R_QY] = T(bad ? 0.0 : st.q[1]); rec[R_QZ] = T(bad ? 0.0 : st.q[2]);
-        rec[R_ITAU] = T(inv_relax_time(I.visc_law, I.iKn, I.visc_param, I.isuth, nn, Tc, iT));
-        rec[R_CS] = T((1.0 - I.Pr) * inn * iT * iT);
-        rec[R_I5T] = T(0.2 * iT);
-    }
-    const int h = lane >> 4, k = lane & 15;  // half of the warp, lane within it
-    // x (h = 0) and y (h = 1) coefficients a_l (Eq. fyz); lane k keeps a_k
-    double c[kMaxN + 1];
-    const int Nh = h ? I.Ny : I.Nx;
-    full_coeffs(h ? u1 : u0, Tc, Nh, c);
-    if (h && I.reduced) {  // y factors of phi and chi: 1 and T (basis: the identity on j)
-        c[0] = 1.0;
-        c[1] = Tc;
-    }
-    double ck = 0.0;
-#pragma unroll
-    for (int l = 0; l <= kMaxN; ++l)
-        if (l == k) ck = c[l];
-    double sxy = 0.0;  // this lane's term of sum_l c_l W_l (the R_SCALE sums, as in write_record)
-    if (k <= kMaxN) {
-        const T v = k <= Nh ? T(ck) : T(0);
-        rec[(h ? R_AY : R_AX) + k] = v;
-        if (k <= Nh) sxy = double(v) * I.wsum[h][k];
-    }
-    // z: half h = 0 the p_z > 0 range (drift u2), h = 1 the p_z < 0 range written in
-    // xi = -p_z >= 0 (drift -u2).  Both share g(0) and one erfc (erfc(x) + erfc(-x) = 2).
-    const int K = I.Nzq;
-    const double r2T = sqrt(0.5 * iT);
-    const double g0 = exp(-0.5 * u2 * u2 * iT) * (r2T * (1.0 / sqrt(M_PI)));
-    const double e = erfc(fabs(u2) * r2T);
-    const double us = h ? -u2 : u2;
-    const double J00 = (u2 >= 0.0) != (h == 1) ? 1.0 - 0.5 * e : 0.5 * e;  // erfc(-us / sqrt(2T)) / 2
-    // J_{0,k}: the half-line Gaussian moments M_k, M_{k+1} = us M_k + k T M_{k-1}
-    double mp = J00, mc = us * J00 + Tc * g0;
-    double Jc = k == 0 ? J00 : (k == 1 ? mc : 0.0);
-#pragma unroll
-    for (int kk = 1; kk < kMaxN; ++kk)
-        if (kk < K) {
-            const double mn = us * mc + kk * Tc * mp;
-            mp = mc;
-            mc = mn;
-            if (k == kk + 1) Jc = mn;
-        }
-    // rows J_{l+1,k} = J_{l,k+1} - alpha_l J_{l,k} - beta_l J_{l-1,k}; b_l = J_{l,0}.
-    // Column k holds a valid entry for k <= K - l; the others never reach column 0.
-    double Jp = 0.0, b[kMaxN + 1];
-    b[0] = Jc;
-#pragma unroll
-    for (int l = 0; l < kMaxN; ++l) {
-        b[l + 1] = 0.0;
-        if (l < K) {
-            const double up = __shfl_down_sync(0xffffffffu, Jc, 1, 16);
-            const double Jn = up - I.alpha[l] * Jc - (l > 0 ? I.beta[l] * Jp : 0.0);
-            Jp = Jc;
-            Jc = Jn;
-            b[l + 1] = Jc;
-        }
-    }
-    double sz = 0.0;
-    if (k == 0) {
-#pragma unroll
-        for (int l = 0; l <= kMaxN; ++l) {
-            const T v = l <= K ? T(b[l]) : T(0);
-            rec[(h ? R_BM : R_BP) + l] = v;
-            if (l <= K) sz += double(v) * I.wsum[2 + h][l];
-        }
-    }
-    // R_SCALE = n / (s_x s_y s_z) (see write_record)
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) sxy += __shfl_xor_sync(0xffffffffu, sxy, o, 16);
-    const double sx = __shfl_sync(0xffffffffu, sxy, 0), sy = __shfl_sync(0xffffffffu, sxy, 16);
-    const double s2 = __shfl_sync(0xffffffffu, sz, 0) + __shfl_sync(0xffffffffu, sz, 16);
-    if (lane == 0) rec[R_SCALE] = T(nn / (sx * sy * s2));
-    return !bad;
-}
-
-template <typename T>
-__device__ void finalize_cell_warp(const InstDev& I, int cell, int lane)
-{
-    const int Nz = I.Nz, nch = I.nchunks, am = lane & 15, h = lane >> 4;
-    // moment am: lanes am and 16 + am sum the even and the odd chunks (loads four
-    // chunks ahead), then add the two halves
-    double part = 0.0;
-    if (am < kNMom)
-        for (int c = h; c < nch; c += 8) {
-            double p[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                p[j] = c + 2 * j < nch ? __ldcg(I.partial + ((size_t)(c + 2 * j) * kNMom + am) * Nz + cell) : 0.0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (c + 2 * j < nch) part += p[j];
-        }
-    part += __shfl_down_sync(0xffffffffu, part, 16);
-    double mom[kNMom];
-#pragma unroll
-    for (int a = 0; a < kNMom; ++a) mom[a] = __shfl_sync(0xffffffffu, part, a);
-    CellState st;
-    cell_state(mom, st);
-    bool bad = false;
-    if (lane == 0) bad = !store_cell(I, cell, st);
-    bad |= !write_record_warp<T>(I, cell, st, lane);
-    if (bad && lane == 0) atomicOr(I.status, 1);
-}
-
-// One instance (whole CTA): wall densities n_w from the outgoing wall fluxes
-// (zero net mass flux, Appendix); after stage 3 the residual, the step count
-// and retirement; after the analysis pass W_old = W.
-__device__ void finalize_instance(const InstDev& I, int stage, double* red)
-{
-    // red: kRedSlots doubles.  The wall fluxes and (stage 3) the residual's sums
-    // ||W_new - W_old||^2, ||W_old||^2 for n, u_x, T are reduced together.
-    const int t = threadIdx.x, Nz = I.Nz;
-    double v[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = 0.0;
-    for (int c = t; c < I.nchunks; c += blockDim.x) {
-        v[0] += __ldcg(I.flux_part + 2 * c);
-        v[1] += __ldcg(I.flux_part + 2 * c + 1);
-    }
-    if (stage == 3) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            for (int s = t; s < Nz; s += blockDim.x) {
-                const double wn = __ldcg(I.Wnew + a * Nz + s), wo = I.Wold[a * Nz + s];
-                v[2 + 2 * a] += (wn - wo) * (wn - wo);
-                v[3 + 2 * a] += wo * wo;
-            }
-        block_sum_n<8>(v, red);
-    } else {
-        double w[2] = {v[0], v[1]};
-        block_sum_n<2>(w, red);
-        v[0] = w[0];
-        v[1] = w[1];
-    }
-    if (t == 0) {
-        I.nw[0] = -v[0] / I.Dbot;
-        I.nw[1] = -v[1] / I.Dtop;
-        if (!isfinite(I.nw[0]) || !isfinite(I.nw[1])) atomicOr(I.status, 1);
-    }
-    if (stage == 3) {
-        double R = 0.0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) R = fmax(R, sqrt(v[2 + 2 * a]) / fmax(sqrt(v[3 + 2 * a]), 1e-30));
-        // every W_old read above is complete (block_sum_n ends with a barrier)
-        for (int e = t; e < 3 * Nz; e += blockDim.x) I.Wold[e] = __ldcg(I.Wnew + e);
-        if (t == 0) {
-            *I.res = R;
-            *I.steps += 1;
-            if (!(R == R)) atomicOr(I.status, 1);
-            if (I.tol > 0.0 && R < I.tol) *I.active = 0;
-        }
-    } else if (stage == 0) {
-        for (int e = t; e < 3 * Nz; e += blockDim.x) I.Wold[e] = __ldcg(I.Wnew + e);
-    }
-}
-
-// records from given macroscopic profiles macro[8][Nz] = n, ux, uy, uz, T, qx, qy, qz
-template <typename T>
-__global__ void records_from_macro(const InstDev* __restrict__ insts, int inst, const double* __restrict__ macro)
-{
-    const InstDev& I = insts[inst];
-    const int Nz = I.Nz, cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= Nz) return;
-    const double u[3] = {macro[Nz + cell], macro[2 * Nz + cell], macro[3 * Nz + cell]};
-    const double q[3] = {macro[5 * Nz + cell], macro[6 * Nz + cell], macro[7 * Nz + cell]};
-    if (!write_record<T>(I, cell, macro[cell], 1.0 / macro[cell], u, macro[4 * Nz + cell], q)) atomicOr(I.status, 1);
-}
-
-// ----------------------------------------------------------------------------
-// stage_kernel<T, V, STAGE, RED>: STAGE 1..3 are the RK stages; STAGE 0 only
-// analyses F0 (moments and wall fluxes) without writing F.  RED selects the
-// phi / chi model (Sec. III, Eqs. boltz_red, sred_def): j = 0 is phi, j = 1 chi.
-// ----------------------------------------------------------------------------
-// Minimum resident CTAs per SM requested from the register allocator: the
-// per-velocity register window grows with V; the rarely taken finalisation
-// path may spill instead of lowering occupancy.
-template <int V> struct MinBlocks { static constexpr int value = V == 1 ? 8 : V == 2 ? 6 : 3; };
-
-template <typename T, int V, int STAGE, bool RED>
-__global__ void __launch_bounds__(kThreads, MinBlocks<V>::value)
-stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, int fuse)
-{
-    typedef typename Acc<T>::type A;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ double wall_red[kRedSlots];
-    const Tile tile = tiles[blockIdx.x];
-    const InstDev& I = insts[tile.inst];
-    if (*I.active == 0) return;
-
-    const int Nz = I.Nz, Q = I.Q, Qx = I.Qx, Qy = I.Qy, Qz = I.Qz, QxQy = I.QxQy;
-    const int z0 = tile.z0, zn = tile.zn;            // cells z0 .. z0+zn-1 (0-based)
-    constexpr int KC = kThreads * V;
-    // chunks never straddle p_z = 0: this chunk's velocities share the sign of p_z
-    const int Qh = Q >> 1, sgc = tile.chunk >= I.nchh;
-    const int k0 = sgc * Qh + (tile.chunk - sgc * I.nchh) * KC;
-    const int kend = min((sgc + 1) * Qh, k0 + KC), kn = kend - k0;
-    const int zm_lo = k0 / QxQy, zm_hi = (kend - 1) / QxQy, nzm = zm_hi - zm_lo + 1;
-    const int G = Qx + Qy + nzm;                     // per-cell factors held in smem
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr bool kF0 = STAGE >= 2;
-
-    const int nhx = Qx * (I.Nx + 1), nhy = Qy * (I.Ny + 1), npz = Qz * (I.Nzq + 1);
-    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(A), kF0, nhx, nhy, npz);
-    T* Fs = reinterpret_cast<T*>(smem_raw + L.fin);   // rows: cells z0-3 .. z0+zn+2
-    T* F0s = reinterpret_cast<T*>(smem_raw + L.f0);   // rows: cells z0 .. z0+zn-1
-    T* recs = reinterpret_cast<T*>(smem_raw + L.rec); // records of cells z0 .. z0+zn-1
-    T* hxs = reinterpret_cast<T*>(smem_raw + L.hx);
-    T* hys = reinterpret_cast<T*>(smem_raw + L.hy);
-    T* pzs = reinterpret_cast<T*>(smem_raw + L.pz);
-    T* gsm = reinterpret_cast<T*>(smem_raw + L.g);
-    T* idzs = reinterpret_cast<T*>(smem_raw + L.idz);
-    A* red = reinterpret_cast<A*>(smem_raw + L.red);
-
-    const T* Fin = static_cast<const T*>(STAGE <= 1 ? I.F0 : STAGE == 2 ? I.F1 : I.F2);
-    T* Fout = static_cast<T*>(STAGE == 1 ? I.F1 : STAGE == 2 ? I.F2 : I.F0);
-    const T* F0g = static_cast<const T*>(I.F0);
-    const int s_lo = max(0, z0 - 3), s_hi = min(Nz - 1, z0 + zn + 2);
-
-    // ---- 1. stage the input rows, the cell records and the basis tables
-    //         (TMA bulk copies; plain loads if the rows are not 16-byte aligned)
-    const T* Rg = static_cast<const T*>(I.rec) + (size_t)z0 * kRecStride;
-    const size_t rec_bytes = (size_t)zn * kRecStride * sizeof(T);
-    if (I.bulk) {
-        if (tid == 0) {
-            mbar_init(&bar, 1);
-            fence_barrier_init();
-        }
-        __syncthreads();
-        if (tid == 0) {
-            const uint32_t bytes = kn * sizeof(T);
-            uint32_t total = bytes * ((s_hi - s_lo + 1) + (kF0 ? zn : 0));
-            if (STAGE > 0)
-                total += rec_bytes + pad16(nhx * sizeof(T)) + pad16(nhy * sizeof(T)) + pad16(npz * sizeof(T));
-            mbar_expect_tx(&bar, total);
-            for (int s = s_lo; s <= s_hi; ++s)
-                bulk_g2s(Fs + (size_t)(s - z0 + 3) * KC, Fin + (size_t)s * Q + k0, bytes, &bar);
-            if (kF0)
-                for (int c = 0; c < zn; ++c)
-                    bulk_g2s(F0s + (size_t)c * KC, F0g + (size_t)(z0 + c) * Q + k0, bytes, &bar);
-            if (STAGE > 0) {
-                bulk_g2s(recs, Rg, rec_bytes, &bar);
-                bulk_g2s(hxs, I.Hx, pad16(nhx * sizeof(T)), &bar);  // tables are padded to 16 bytes
-                bulk_g2s(hys, I.Hy, pad16(nhy * sizeof(T)), &bar);
-                bulk_g2s(pzs, I.Pz, pad16(npz * sizeof(T)), &bar);
-            }
-        }
-    } else {
-        for (int s = s_lo; s <= s_hi; ++s)
-            for (int kl = tid; kl < kn; kl += kThreads) Fs[(size_t)(s - z0 + 3) * KC + kl] = Fin[(size_t)s * Q + k0 + kl];
-        if (kF0)
-            for (int c = 0; c < zn; ++c)
-                for (int kl = tid; kl < kn; kl += kThreads) F0s[(size_t)c * KC + kl] = F0g[(size_t)(z0 + c) * Q + k0 + kl];
-        if (STAGE > 0) {
-            for (int e = tid; e < zn * kRecStride; e += kThreads) recs[e] = Rg[e];
-            for (int e = tid; e < nhx; e += kThreads) hxs[e] = ld<T>(I.Hx, e);
-            for (int e = tid; e < nhy; e += kThreads) hys[e] = ld<T>(I.Hy, e);
-            for (int e = tid; e < npz; e += kThreads) pzs[e] = ld<T>(I.Pz, e);
-        }
-    }
-    if (STAGE > 0)
-        for (int c = tid; c < zn; c += kThreads) idzs[c] = ld<T>(I.inv_dz, z0 + c);
-
-    // per-velocity constants: p (and |p_z| for the fluxes), w * psi(p) for the 13 raw moments
-    int ii[V], jj[V], zz[V], kl[V];
-    T px[V], py[V], pz[V], apz[V];
-    A wpsi[V][kNMom];
-    bool ok[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        kl[v] = tid + v * kThreads;
-        ok[v] = kl[v] < kn;
-        const int kc = ok[v] ? k0 + kl[v] : kend - 1;
-        jj[v] = kc % Qy;
-        ii[v] = (kc / Qy) % Qx;
-        zz[v] = kc / QxQy;
-        const int sg = zz[v] >= Qz, m = zz[v] - sg * Qz;
-        px[v] = ld<T>(I.px, ii[v]);
-        py[v] = ld<T>(I.py, jj[v]);
-        const T x = ld<T>(I.xi, m);
-        pz[v] = sg ? -x : x;
-        apz[v] = x;
-        const A w = ok[v] ? A(ld<T>(I.wx, ii[v]) * ld<T>(I.wy, jj[v]) * ld<T>(I.wz, m)) : A(0);
-        const A X = px[v], Y = py[v], Z = pz[v], p2 = X * X + Y * Y + Z * Z;
-        wpsi[v][0] = w;
-        wpsi[v][1] = w * X; wpsi[v][2] = w * Y; wpsi[v][3] = w * Z;
-        wpsi[v][4] = w * X * X; wpsi[v][5] = w * Y * Y; wpsi[v][6] = w * Z * Z;
-        wpsi[v][7] = w * X * Y; wpsi[v][8] = w * X * Z; wpsi[v][9] = w * Y * Z;
-        wpsi[v][10] = w * p2 * X; wpsi[v][11] = w * p2 * Y; wpsi[v][12] = w * p2 * Z;
-        if (RED) {
-            // p_y = 0 on both fields.  chi = int p_y^2 f dp_y carries the p_y^2 moments:
-            // sum chi -> sum p_y^2 f, sum p_a chi -> sum p_y^2 p_a f (a = x, z), nothing else.
-            // py[v] then holds -(the Shakhov offset of Eq. sred_def): -4/5 for phi, -2/5 for chi.
-            if (jj[v] == 1) {
-#pragma unroll
-                for (int a = 0; a < kNMom; ++a) wpsi[v][a] = A(0);
-                wpsi[v][5] = w;
-                wpsi[v][10] = w * X;
-                wpsi[v][12] = w * Z;
-            }
-            py[v] = jj[v] ? T(-0.4) : T(-0.8);
-        }
-    }
-
-    // ---- 3. wait for the copies (bounded); a CTA whose copies never land flags
-    //         the instance and leaves once they are no longer in flight
-    int late = 0;
-    if (I.bulk) {
-        uint32_t spins = 0;
-        while (!mbar_try_wait(&bar, 0)) {
-            if (++spins > kSpinLimit) { late = 1; break; }
-        }
-    }
-    if (__syncthreads_or(late)) {
-        if (tid == 0) atomicOr(I.status, 2);
-        uint32_t spins = 0;
-        while (!mbar_try_wait(&bar, 0) && ++spins < kSpinLimit) {
-        }
-        return;
-    }
-
-    // ---- 4a. per-cell factors of the truncated Hermite equilibrium (Sec. III)
-    //          from the staged records: n*Gx[i], Gy[j], Gz[zm] for this chunk's zm
-    if (STAGE > 0) {
-        for (int e = tid; e < zn * G; e += kThreads) {
-            const int c = e / G, r = e - c * G;
-            const T* rc = recs + (size_t)c * kRecStride;
-            T g = 0;
-            if (r < Qx) {
-                const T* h = hxs + r * (I.Nx + 1);
-                for (int l = 0; l <= I.Nx; ++l) g += rc[R_AX + l] * h[l];
-                g *= rc[R_SCALE];
-            } else if (r < Qx + Qy) {
-                const T* h = hys + (r - Qx) * (I.Ny + 1);
-                for (int l = 0; l <= I.Ny; ++l) g += rc[R_AY + l] * h[l];
-            } else {
-                const int zm = zm_lo + r - Qx - Qy, sg = zm >= Qz, m = zm - sg * Qz;
-                const T* h = pzs + m * (I.Nzq + 1);
-                const T* b = rc + (sg ? R_BM : R_BP);
-                for (int l = 0; l <= I.Nzq; ++l) g += b[l] * h[l];
-            }
-            gsm[e] = g;
-        }
-    }
-
-    // ---- 4b. ghost rows (each thread fills only its own columns)
-    const int rbase = 3 - z0;  // smem row of cell s is s + rbase
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        if (!ok[v]) continue;  // columns past the chunk end hold no data
-        T* col = Fs + kl[v];
-        if (z0 < 3 && I.half) {  // bounce-back on the centre line: ghost -1-s holds cell s
-            // at the mirrored velocity (p_z, p_x reversed: other half range, node Qx-1-i;
-            // the Gauss nodes are sorted, so p_x[Qx-1-i] = -p_x[i]).  It lies in the other
-            // sign's chunk, so it comes from the stage input in global memory.
-            const int zm = zz[v] + (sgc ? -Qz : Qz);
-            const int kmir = (zm * Qx + (Qx - 1 - ii[v])) * Qy + jj[v];
-            for (int s = 0; s < 3; ++s)
-                if (-1 - s + rbase >= 0) col[(size_t)(-1 - s + rbase) * KC] = Fin[(size_t)s * Q + kmir];
-        } else if (z0 < 3) {
-            if (!sgc) {  // incoming at the bottom wall: n_w times the wall equilibrium
-                const T g = T(I.nw[0]) * ld<T>(I.gwx_bot, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
-                for (int s = -3; s <= -1; ++s)
-                    if (s + rbase >= 0) col[(size_t)(s + rbase) * KC] = g;
-            } else {      // outgoing: quadratic extrapolation (Appendix)
-                const T f1 = col[(size_t)(0 + rbase) * KC], f2 = col[(size_t)(1 + rbase) * KC],
-                        f3 = col[(size_t)(2 + rbase) * KC];
-                const T g0 = T(I.ext_bot[0][0]) * f1 + T(I.ext_bot[0][1]) * f2 + T(I.ext_bot[0][2]) * f3;
-                const T g1 = T(I.ext_bot[1][0]) * g0 + T(I.ext_bot[1][1]) * f1 + T(I.ext_bot[1][2]) * f2;
-                if (-1 + rbase >= 0) col[(size_t)(-1 + rbase) * KC] = g0;
-                if (-2 + rbase >= 0) col[(size_t)(-2 + rbase) * KC] = g1;
-                if (-3 + rbase >= 0) col[(size_t)(-3 + rbase) * KC] = g1;  // never read for p_z < 0
-            }
-        }
-        if (z0 + zn + 3 > Nz) {
-            const int smax = z0 + zn + 2;
-            if (sgc) {
-                const T g = T(I.nw[1]) * ld<T>(I.gwx_top, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
-                for (int s = Nz; s <= Nz + 2; ++s)
-                    if (s <= smax) col[(size_t)(s + rbase) * KC] = g;
-            } else {
-                const T f1 = col[(size_t)(Nz - 1 + rbase) * KC], f2 = col[(size_t)(Nz - 2 + rbase) * KC],
-                        f3 = col[(size_t)(Nz - 3 + rbase) * KC];
-                const T g0 = T(I.ext_top[0][0]) * f1 + T(I.ext_top[0][1]) * f2 + T(I.ext_top[0][2]) * f3;
-                const T g1 = T(I.ext_top[1][0]) * g0 + T(I.ext_top[1][1]) * f1 + T(I.ext_top[1][2]) * f2;
-                if (Nz <= smax) col[(size_t)(Nz + rbase) * KC] = g0;
-                if (Nz + 1 <= smax) col[(size_t)(Nz + 1 + rbase) * KC] = g1;
-                if (Nz + 2 <= smax) col[(size_t)(Nz + 2 + rbase) * KC] = g1;  // never read for p_z > 0
-            }
-        }
-    }
-
-    __syncthreads();  // per-cell factors complete
-
-    // ---- 5. march through the z-range in the upwind direction of the chunk: up
-    // (p_z > 0) from z0, down (p_z < 0) from z0+zn-1.  At march step c the register
-    // window holds the cells s-3 .. s+2 seen from upwind (s+3 .. s-2 going down), so
-    // both directions use one stencil: the flux through the interface ahead is
-    // |p_z| weno5(w1 .. w5), the one behind was formed at the previous step, and the
-    // divergence of Eq. (flux) is (ahead - behind) / dz for the signed p_z either way.
-    const long rstep = sgc ? -(long)KC : (long)KC;
-    const T* rp = Fs + (sgc ? (size_t)(zn + 5) * KC : 0);  // window row d at step c: rp + (c + d) rstep
-    T w[V][6], flm[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-#pragma unroll
-        for (int d = 0; d < 6; ++d) w[v][d] = rp[d * rstep + kl[v]];
-        flm[v] = apz[v] * weno5<T>(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4]);
-    }
-    const T dt = T(I.dt);
-    const long ostep = sgc ? -(long)Q : (long)Q;
-    T* outp = Fout + (size_t)(sgc ? z0 + zn - 1 : z0) * Q + k0;
-#pragma unroll 1  // unrolling the z-march only adds instruction-cache misses
-    for (int c = 0; c < zn; ++c) {
-        const int cc = sgc ? zn - 1 - c : c;  // the cell within the tile
-        const T* sc = recs + (size_t)cc * kRecStride;
-        const T* gc = gsm + cc * G;
-        const T* rn = rp + (c + 6) * rstep;
-        T ux = 0, uy = 0, uz = 0, i5T = 0, qx = 0, qy = 0, qz = 0, itau = 0, cS = 0, idz = 0;
-        if (STAGE > 0) {
-            ux = sc[R_UX]; uy = sc[R_UY]; uz = sc[R_UZ];
-            qx = sc[R_QX]; qy = sc[R_QY]; qz = sc[R_QZ];
-            itau = sc[R_ITAU]; cS = sc[R_CS]; i5T = sc[R_I5T]; idz = idzs[cc];
-        }
-        A acc[16];
-#pragma unroll
-        for (int a = 0; a < 16; ++a) acc[a] = A(0);
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const T wn = rn[kl[v]];
-            T out = w[v][3];
-            if (STAGE > 0) {
-                const T flp = apz[v] * weno5<T>(w[v][1], w[v][2], w[v][3], w[v][4], w[v][5]);
-                const T f = w[v][3];
-                // Shakhov target n Gx Gy Gz (1 + S), S = cS (xi^2/(5T) - 1) xi.q; in the
-                // phi / chi model (Eq. sred_def) S = cS ((xi_x^2 + xi_z^2)/(5T) - 4/5 or 2/5) xi.q
-                // with u_y = q_y = 0, and Gy = 1 (phi) or T (chi) from the record
-                T S;
-                if (RED) {
-                    const T ex = px[v] - ux, ez = pz[v] - uz;
-                    S = cS * ((ex * ex + ez * ez) * i5T + py[v]) * (ex * qx + ez * qz);
-                } else {
-                    const T ex = px[v] - ux, ey = py[v] - uy, ez = pz[v] - uz;
-                    const T xi2 = ex * ex + ey * ey + ez * ez;
-                    const T xq = ex * qx + ey * qy + ez * qz;
-                    S = cS * (xi2 * i5T - T(1)) * xq;
-                }
-                const T geq = gc[ii[v]] * gc[Qx + jj[v]] * gc[Qx + Qy + zz[v] - zm_lo];
-                // the advection and relaxation increments nearly cancel near a steady
-                // state: combine them first, then add to f once
-                const T Lv = -(flp - flm[v]) * idz - (f - geq * (T(1) + S)) * itau;
-                const T f1 = f + dt * Lv;
-                // Shu-Osher combine written as F_l + b (f1 - F_l): identical to
-                // (1 - b) F_l + b f1, but a rounded b only scales the increment
-                // (with b = 2/3 the two rounded weights would not add up to 1 and
-                // would scale the whole state every step)
-                if (STAGE == 1) {
-                    out = f1;
-                } else {
-                    const T fl = F0s[(size_t)cc * KC + kl[v]];
-                    out = fl + (STAGE == 2 ? T(0.25) : T(2.0 / 3.0)) * (f1 - fl);
-                }
-                if (ok[v]) outp[kl[v]] = out;
-                flm[v] = flp;
-            }
-#pragma unroll
-            for (int d = 0; d < 5; ++d) w[v][d] = w[v][d + 1];
-            w[v][5] = wn;
-            const A o = ok[v] ? A(out) : A(0);  // columns past the chunk hold no data
-#pragma unroll
-            for (int a = 0; a < kNMom; ++a) acc[a] += o * wpsi[v][a];
-        }
-        const A tot = reduce_scatter16<A>(acc, lane);
-        const int m = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-        if ((lane & 1) == 0) red[((size_t)cc * (kThreads / 32) + warp) * 16 + m] = tot;
-        outp += ostep;
-    }
-    __syncthreads();
-    for (int e = tid; e < zn * kNMom; e += kThreads) {
-        const int c = e / kNMom, a = e - c * kNMom;
-        A s = A(0);
-#pragma unroll
-        for (int q = 0; q < kThreads / 32; ++q) s += red[((size_t)c * (kThreads / 32) + q) * 16 + a];
-        I.partial[((size_t)tile.chunk * kNMom + a) * Nz + z0 + c] = double(s);
-    }
-
-    // ---- 6. outgoing WENO flux of F_out through the wall interfaces (for n_w).
-    // Each thread re-reads the outputs it wrote itself (STAGE 0: its input rows).
-    auto outval = [&](int v, int cell) -> T {
-        return STAGE == 0 ? Fs[(size_t)(cell + rbase) * KC + kl[v]] : Fout[(size_t)cell * Q + k0 + kl[v]];
-    };
-    if (z0 == 0) {  // bottom: p_z < 0 leaves through s = -1/2
-        double fl = 0.0;
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-            if (ok[v] && sgc && !I.half) {  // no wall below a half channel
-                const T f1 = outval(v, 0), f2 = outval(v, 1), f3 = outval(v, 2);
-                const T g0 = T(I.ext_bot[0][0]) * f1 + T(I.ext_bot[0][1]) * f2 + T(I.ext_bot[0][2]) * f3;
-                const T g1 = T(I.ext_bot[1][0]) * g0 + T(I.ext_bot[1][1]) * f1 + T(I.ext_bot[1][2]) * f2;
-                fl += double(wpsi[v][0]) * double(pz[v] * weno5<T>(f3, f2, f1, g0, g1));
-            }
-        fl = block_sum(fl, wall_red);
-        if (tid == 0) I.flux_part[tile.chunk * 2 + 0] = fl;
-    }
-    if (z0 + zn == Nz) {  // top: p_z > 0 leaves through s = Nz - 1/2
-        double fl = 0.0;
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-            if (ok[v] && !sgc) {
-                const T f1 = outval(v, Nz - 1), f2 = outval(v, Nz - 2), f3 = outval(v, Nz - 3);
-                const T g0 = T(I.ext_top[0][0]) * f1 + T(I.ext_top[0][1]) * f2 + T(I.ext_top[0][2]) * f3;
-                const T g1 = T(I.ext_top[1][0]) * g0 + T(I.ext_top[1][1]) * f1 + T(I.ext_top[1][2]) * f2;
-                fl += double(wpsi[v][0]) * double(pz[v] * weno5<T>(f3, f2, f1, g0, g1));
-            }
-        fl = block_sum(fl, wall_red);
-        if (tid == 0) I.flux_part[tile.chunk * 2 + 1] = fl;
-    }
-
-    // ---- 7. (fuse != 0) finalisation without extra launches (threadfence tickets): the CTA
-    // that finishes last among the chunks of this z-tile finalises the tile's
-    // cells; the one that finalises the instance's last z-tile does the walls
-    // and the residual.  Counters are reset by their last user.
-    if (!fuse) return;  // finalize_cells follows as a separate launch
-    __shared__ int last;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) last = atomicAdd(I.zcount + tile.zt, 1) == I.nchunks - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (I.fin_warp) {
-        for (int c = tid >> 5; c < zn; c += kThreads / 32) finalize_cell_warp<T>(I, z0 + c, tid & 31);
-    } else if (tid < zn) {
-        finalize_cell<T>(I, z0 + tid);
-    }
-    if (tid == 0) I.zcount[tile.zt] = 0;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) last = atomicAdd(I.icount, 1) == I.nzt - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (tid == 0) *I.icount = 0;
-    finalize_instance(I, STAGE, wall_red);
-}
 
 // ---- separate finalisation launches (used when the stage kernel does not fuse them)
 template <typename T>
@@ -1040,37 +81,6 @@ size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int nhx, int 
     return stage_smem(zn, KC, G, fp32 ? 4 : 8, fp32 ? 4 : 8, stage >= 2, nhx, nhy, npz).total;
 }
 
-template <typename T, int V, int STAGE, bool RED>
-static cudaError_t launch_stage_t(const InstDev* d_inst, const Tile* d_tiles, int ntiles, size_t smem,
-                                  int fuse, cudaStream_t st)
-{
-    auto kfn = stage_kernel<T, V, STAGE, RED>;
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kfn<<<ntiles, kThreads, smem, st>>>(d_inst, d_tiles, fuse);
-    return cudaGetLastError();
-}
-
-template <typename T, int V, bool RED>
-static cudaError_t launch_stage_r(int stage, const InstDev* d, const Tile* t, int n, size_t smem, int fuse,
-                                  cudaStream_t st)
-{
-    switch (stage) {
-        case 0: return launch_stage_t<T, V, 0, RED>(d, t, n, smem, fuse, st);
-        case 1: return launch_stage_t<T, V, 1, RED>(d, t, n, smem, fuse, st);
-        case 2: return launch_stage_t<T, V, 2, RED>(d, t, n, smem, fuse, st);
-        default: return launch_stage_t<T, V, 3, RED>(d, t, n, smem, fuse, st);
-    }
-}
-
-template <typename T, int V>
-static cudaError_t launch_stage_v(int red, int stage, const InstDev* d, const Tile* t, int n, size_t smem,
-                                  int fuse, cudaStream_t st)
-{
-    return red ? launch_stage_r<T, V, true>(stage, d, t, n, smem, fuse, st)
-               : launch_stage_r<T, V, false>(stage, d, t, n, smem, fuse, st);
-}
-
 template <typename T>
 static cudaError_t launch_finalize_t(int stage, const InstDev* d_inst, int ninst, int maxNz, int fin_warp,
                                      cudaStream_t st)
@@ -1086,17 +96,11 @@ static cudaError_t launch_finalize_t(int stage, const InstDev* d_inst, int ninst
 cudaError_t launch_stage_only(int fp32, int red, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
                               int ntiles, size_t smem, int fuse, cudaStream_t st)
 {
-    cudaError_t e;
-    if (fp32) {
-        if (V == 1) e = launch_stage_v<float, 1>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
-        else if (V == 2) e = launch_stage_v<float, 2>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
-        else e = launch_stage_v<float, 4>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
-    } else {
-        if (V == 1) e = launch_stage_v<double, 1>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
-        else if (V == 2) e = launch_stage_v<double, 2>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
-        else e = launch_stage_v<double, 4>(red, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
-    }
-    return e;
+    if (fp32)
+        return red ? launch_stage_f32_red(V, stage, d_inst, d_tiles, ntiles, smem, fuse, st)
+                   : launch_stage_f32_full(V, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
+    return red ? launch_stage_f64_red(V, stage, d_inst, d_tiles, ntiles, smem, fuse, st)
+               : launch_stage_f64_full(V, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
 }
 
 // the separate finalisation launches of an unfused stage

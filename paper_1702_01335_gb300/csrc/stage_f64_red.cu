@@ -1,0 +1,14 @@
+// Stage kernel instantiations for double storage, the reduced phi / chi model
+// (all V and stages); one translation unit per (storage type, model) so that
+// the four compile in parallel.
+#include "kernels.cuh"
+
+namespace lbs {
+
+cudaError_t launch_stage_f64_red(int V, int stage, const InstDev* d, const Tile* t, int n, size_t smem,
+                                 int fuse, cudaStream_t st)
+{
+    return launch_stage_m<double, true>(V, stage, d, t, n, smem, fuse, st);
+}
+
+}  // namespace lbs
