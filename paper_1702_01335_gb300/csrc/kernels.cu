@@ -5,13 +5,27 @@
 
 namespace lbs {
 
+// The instance descriptor copied into shared memory by the whole block at once: the
+// finalisation's fields (pointers, orders, wall sums) are then one shared load
+// away instead of an L2 round trip each, at first use, inside the FP64 chains.
+static __device__ __forceinline__ const InstDev& stage_descriptor(const InstDev* g, InstDev* s)
+{
+    static_assert(sizeof(InstDev) % 8 == 0, "descriptor copied in 8-byte words");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(g);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(s);
+    for (int e = threadIdx.x; e < (int)(sizeof(InstDev) / 8); e += blockDim.x) dst[e] = src[e];
+    __syncthreads();
+    return *s;
+}
+
 // ---- separate finalisation launches (used when the stage kernel does not fuse them)
 template <typename T>
 __global__ void __launch_bounds__(32) finalize_cells(const InstDev* __restrict__ insts, int stage)
 {
     __shared__ double red[kRedSlots];
     __shared__ int last;
-    const InstDev& I = insts[blockIdx.y];
+    __shared__ InstDev sI;
+    const InstDev& I = stage_descriptor(insts + blockIdx.y, &sI);
     const int nblk = (I.Nz + 31) >> 5;
     if (blockIdx.x >= nblk || *I.active == 0) return;
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -34,7 +48,8 @@ __global__ void __launch_bounds__(128) finalize_cells_warp(const InstDev* __rest
 {
     __shared__ double red[kRedSlots];
     __shared__ int last;
-    const InstDev& I = insts[blockIdx.y];
+    __shared__ InstDev sI;
+    const InstDev& I = stage_descriptor(insts + blockIdx.y, &sI);
     const int nblk = (I.Nz + 3) >> 2;
     if (blockIdx.x >= nblk || *I.active == 0) return;
     const int cell = blockIdx.x * 4 + (threadIdx.x >> 5);

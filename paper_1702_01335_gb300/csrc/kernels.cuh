@@ -413,6 +413,13 @@ __device__ void finalize_cell(const InstDev& I, int cell)
 template <typename T>
 __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& st, int lane)
 {
+    // the half-range recurrence coefficients, loaded ahead of the chain that needs them
+    double al[kMaxN], be[kMaxN];
+#pragma unroll
+    for (int l = 0; l < kMaxN; ++l) {
+        al[l] = I.alpha[l];
+        be[l] = I.beta[l];
+    }
     bool bad = !(st.n > 0.0) || !(st.T > 0.0) || !isfinite(st.n) || !isfinite(st.T);
     for (int a = 0; a < 3; ++a) bad |= !isfinite(st.u[a]) || !isfinite(st.q[a]);
     const double nn = bad ? 1.0 : st.n, inn = bad ? 1.0 : st.in, Tc = bad ? 1.0 : st.T;
@@ -473,7 +480,7 @@ __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& s
         b[l + 1] = 0.0;
         if (l < K) {
             const double up = __shfl_down_sync(0xffffffffu, Jc, 1, 16);
-            const double Jn = up - I.alpha[l] * Jc - (l > 0 ? I.beta[l] * Jp : 0.0);
+            const double Jn = up - al[l] * Jc - (l > 0 ? be[l] * Jp : 0.0);
             Jp = Jc;
             Jc = Jn;
             b[l + 1] = Jc;
