@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="lbs", choices=["lbs", "reference"])
     ap.add_argument("--batch", type=int, default=BATCH)
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--precision", default=None, choices=["f32", "f64"],
+                    help="default f32; f64 for the low-Mach workload, whose deviations FP32 does not resolve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-steady", action="store_true",
                     help="skip the time-to-steady-state comparison (plain vs batched vs warm-started)")
@@ -52,12 +53,16 @@ def parse():
                     help="V,ZT,fuse: use this stage-kernel tiling instead of the autotuner")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON cache of tile choices (default: the package's tuning_cache.json)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "tables"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "tables", "luo"],
                     help="c2: the throughput workload (default); tables: the 20 half-channel "
-                         "runs of the paper's Sec. VI tables (one GPU)")
+                         "runs of the paper's Sec. VI tables; luo: the low-Mach runs of Sec. IV "
+                         "(Table luo); the last two on one GPU")
     ap.add_argument("--model", default="full", choices=["full", "reduced"],
                     help="tables workload: the 3D velocity set (Q_y = 7) or the paper's phi / chi model")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.precision is None:
+        a.precision = "f64" if a.workload == "luo" else "f32"
+    return a
 
 
 def peaks():
@@ -202,15 +207,18 @@ def run_reference(a):
     }), flush=True)
 
 
-def run_tables(a):
-    """The paper-reproduction workload: the 20 half-channel He / Ar runs of the Sec. VI
-    tables in one batch (16 cells, 7 x 7 x (2 x Q_n) velocities, Q_n = 7 or 30), timed
-    like the main line.  Small and latency-bound: the line reports the stage and
-    finalisation kernels' own times beside the step rate."""
+def run_small(a):
+    """The paper-reproduction workloads, timed like the main line:
+    tables  the 20 half-channel He / Ar runs of the Sec. VI tables in one batch (16 cells,
+            7 x 7 x (2 x Q_n) velocities, Q_n = 7 or 30; or the phi / chi model);
+    luo     the three low-Mach half-channel runs of Sec. IV (Table luo), FP64.
+    Small and latency-bound: the line reports the stage and finalisation kernels' own
+    times beside the step rate."""
     import torch
     from paper_1702_01335_gb300 import LBS_FP32, LBS_FP64, Instance, Solver
     torch.cuda.set_device(0)
-    inst = [Instance(**p) for _, p in W.paper_tables(reduced=a.model == "reduced")]
+    runs = W.paper_tables(reduced=a.model == "reduced") if a.workload == "tables" else W.luo_runs()
+    inst = [Instance(**p) for _, p in runs]
     from paper_1702_01335_gb300.autotune import DEFAULT_CACHE, autotune
     s = Solver(inst, precision=LBS_FP32 if a.precision == "f32" else LBS_FP64)
     if a.tiling:
@@ -250,10 +258,12 @@ def run_tables(a):
         "unit": "updates/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": a.precision, "data": "synthetic",
-        "config": {"workload": "paper tables: 20 half channels (Ar, He; delta 0.1-40; u_w sqrt 2, "
-                               "0.1 sqrt 2), Nz=16 A=0.98, N_eq=6, Sutherland, Pr=2/3; " + (
-                                   "phi/chi model, Q=7x2x(2x7) or 7x2x(2x30)" if a.model == "reduced"
-                                   else "3D set, Q=7x7x(2x7) or 7x7x(2x30)"),
+        "config": {"workload": ("paper tables: 20 half channels (Ar, He; delta 0.1-40; u_w sqrt 2, "
+                                "0.1 sqrt 2), Nz=16 A=0.98, N_eq=6, Sutherland, Pr=2/3; " + (
+                                    "phi/chi model, Q=7x2x(2x7) or 7x2x(2x30)" if a.model == "reduced"
+                                    else "3D set, Q=7x7x(2x7) or 7x7x(2x30)")) if a.workload == "tables" else
+                               ("low Mach (Table luo): 3 half channels, k = 0.03, 0.1, 1 (S = 64, 32, 32; "
+                                "Q = 2x2x(2x4), 2x2x(2x7), 2x2x(2x21)), phi/chi model, BGK, u_w = 1e-5, A = 0.98"),
                    "updates_per_step": upd_step,
                    "l2": "state (%d KiB) resident in L2: latency-bound" % (s.state_bytes() >> 10),
                    "tiling": {"V": tl["V"], "ZT": tl["ZT"], "fused_finalise": tl["fuse"]}},
@@ -264,19 +274,25 @@ def run_tables(a):
         "gpu_launches": {0: 6, 1: 3, 2: 12}[tl["fuse"]] * a.steps,
         "clocks": clk.summary(),
     }
+    if a.workload == "luo":
+        line["diagnostics_after_timed_steps"] = {
+            "k=%g" % lab["k"]: {k: v / p["u_w"] if k in ("u_slip", "u_wall") else v
+                                for k, v in s.diagnostics(b).items() if k in ("u_slip", "nu", "mflow", "Txy")}
+            for b, (lab, p) in enumerate(runs)}
     if not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_tables()
+        pick = [r for r in runs if r[0].get("delta") == 1.0 or r[0].get("k") == 0.1][0]
+        line["cpu_baseline"] = cpu_baseline_half(pick)
     print(json.dumps(line), flush=True)
     s.close()
 
 
-def cpu_baseline_tables(seconds=12.0):
-    """The oracle on one table run (Ar, delta = 1, u_w = sqrt 2).  It has no half channel:
-    it steps the full channel of 32 cells, which costs two updates per half-channel update."""
+def cpu_baseline_half(run, seconds=12.0):
+    """The oracle on one run of a half-channel workload.  It has no half channel: it steps
+    the full channel of 2 Nz cells, which costs two updates per half-channel update."""
     from oracle.oracle import Oracle
-    label, p = [r for r in W.paper_tables() if r[0]["delta"] == 1.0][0]
+    label, p = run
     o = Oracle(p["Qx"], p["Qy"], p["Qz"], p["N_eq"], 2 * p["Nz"], A=p["A"], Kn=p["Kn"], uw=p["u_w"],
-               Tw=p["T_w"], Pr=p["Pr"], visc_law=p["visc_law"], visc_param=p["visc_param"], dt=p["dt"])
+               Tw=p["T_w"], Pr=p["Pr"], visc_law=p["visc_law"], visc_param=p["visc_param"], dt=p.get("dt"))
     o.step(1)
     t0 = time.perf_counter()
     n = 0
@@ -285,17 +301,17 @@ def cpu_baseline_tables(seconds=12.0):
         n += 1
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": p["Nz"] * 2 * p["Qx"] * p["Qy"] * p["Qz"] * n / dt, "unit": "updates/s", "cores": cores,
-            "kind": "oracle", "sample": "Ar delta=1 u_w=sqrt 2 as the full channel of 32 cells, %d RK-3 "
-                                        "steps in %.1f s, counted as half-channel updates" % (n, dt)}
+    return {"value": p["Nz"] * o.Q * n / dt, "unit": "updates/s", "cores": cores, "kind": "oracle",
+            "sample": "%s as the full channel of %d cells (Q = %d), %d RK-3 steps in %.1f s, counted as "
+                      "half-channel updates" % (json.dumps(label), 2 * p["Nz"], o.Q, n, dt)}
 
 
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
-    if a.workload == "tables":
-        return run_tables(a)
+    if a.workload in ("tables", "luo"):
+        return run_small(a)
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
