@@ -275,10 +275,12 @@ def run_small(a):
         "clocks": clk.summary(),
     }
     if a.workload == "luo":
+        diag = [s.diagnostics(b) for b in range(len(runs))]
         line["diagnostics_after_timed_steps"] = {
-            "k=%g" % lab["k"]: {k: v / p["u_w"] if k in ("u_slip", "u_wall") else v
-                                for k, v in s.diagnostics(b).items() if k in ("u_slip", "nu", "mflow", "Txy")}
-            for b, (lab, p) in enumerate(runs)}
+            "k=%g" % lab["k"]: {"u_slip/u_w": d["u_slip"] / p["u_w"], "L u'(0)/2u_w": d["nu"],
+                                "mflow/mflow_hydro": d["mflow"] / d["mflow_hydro"],
+                                "Txy/Txy_bal": d["Txy"] / d["Txy_bal"]}
+            for d, (lab, p) in zip(diag, runs)}
     if not a.no_cpu_baseline:
         pick = [r for r in runs if r[0].get("delta") == 1.0 or r[0].get("k") == 0.1][0]
         line["cpu_baseline"] = cpu_baseline_half(pick)

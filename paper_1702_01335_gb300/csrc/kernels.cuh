@@ -455,9 +455,11 @@ __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& s
     // z: half h = 0 the p_z > 0 range (drift u2), h = 1 the p_z < 0 range written in
     // xi = -p_z >= 0 (drift -u2).  Both share g(0) and one erfc (erfc(x) + erfc(-x) = 2).
     const int K = I.Nzq;
-    const double r2T = sqrt(0.5 * iT);
-    const double g0 = exp(-0.5 * u2 * u2 * iT) * (r2T * (1.0 / sqrt(M_PI)));
-    const double e = erfc(fabs(u2) * r2T);
+    // 1 / sqrt(2T) straight from T, so that the transcendental chain does not wait for
+    // the division 1 / T; with x = |u2| / sqrt(2T): g(0) = exp(-x^2) / sqrt(2 pi T)
+    const double r2T = rsqrt(2.0 * Tc), x = fabs(u2) * r2T;
+    const double g0 = exp(-x * x) * (r2T * (1.0 / sqrt(M_PI)));
+    const double e = erfc_nonneg(x);
     const double us = h ? -u2 : u2;
     const double J00 = (u2 >= 0.0) != (h == 1) ? 1.0 - 0.5 * e : 0.5 * e;  // erfc(-us / sqrt(2T)) / 2
     // J_{0,k}: the half-line Gaussian moments M_k, M_{k+1} = us M_k + k T M_{k-1}
@@ -486,14 +488,18 @@ __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& s
             b[l + 1] = Jc;
         }
     }
-    double sz = 0.0;
+    double sz = 0.0, sz1 = 0.0;  // two interleaved partial sums: half the dependent adds
     if (k == 0) {
 #pragma unroll
         for (int l = 0; l <= kMaxN; ++l) {
             const T v = l <= K ? T(b[l]) : T(0);
             rec[(h ? R_BM : R_BP) + l] = v;
-            if (l <= K) sz += double(v) * I.wsum[2 + h][l];
+            if (l <= K) {
+                if (l & 1) sz1 += double(v) * I.wsum[2 + h][l];
+                else sz += double(v) * I.wsum[2 + h][l];
+            }
         }
+        sz += sz1;
     }
     // R_SCALE = n / (s_x s_y s_z) (see write_record)
 #pragma unroll

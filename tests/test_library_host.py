@@ -5,6 +5,8 @@ rejected before any device work."""
 import ctypes as C
 import os
 import re
+import subprocess
+import tempfile
 
 import numpy as np
 import pytest
@@ -117,3 +119,30 @@ def test_diagnostics_match_oracle(A, S):
             assert abs(d["mflow"] - 0.5 * np.mean(prof[0][S:] * prof[1][S:])) < 1e-13
         assert d["mflow_hydro"] == uw / 4
         assert abs(d["Txy_bal"] + uw * np.sqrt(2 * Tw / np.pi)) < 1e-15
+
+
+def test_erfc_series_against_libm():
+    """erfc_nonneg (lbs_internal.h: the Maclaurin series of erf below 1/2, the library
+    erfc above) against the C library's erfc on [0, 3], built on the host from the same
+    header the kernels include."""
+    src = r"""
+#include <cstdio>
+#include <cmath>
+#include "lbs_internal.h"
+int main() {
+    double worst = 0.0;
+    for (int i = 0; i <= 300000; ++i) {
+        const double x = 3.0 * i / 300000.0, a = lbs::erfc_nonneg(x), b = std::erfc(x);
+        worst = std::fmax(worst, std::fabs(a - b) / b);
+    }
+    std::printf("%.6e\n", worst);
+    return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        cpp, exe = os.path.join(d, "e.cpp"), os.path.join(d, "e")
+        open(cpp, "w").write(src)
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", os.path.join(ROOT, "paper_1702_01335_gb300", "csrc"),
+                               cpp, "-o", exe])
+        worst = float(subprocess.check_output([exe]).decode())
+    assert worst < 5e-16, worst
