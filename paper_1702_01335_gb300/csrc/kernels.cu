@@ -5,19 +5,6 @@
 
 namespace lbs {
 
-// The instance descriptor copied into shared memory by the whole block at once: the
-// finalisation's fields (pointers, orders, wall sums) are then one shared load
-// away instead of an L2 round trip each, at first use, inside the FP64 chains.
-static __device__ __forceinline__ const InstDev& stage_descriptor(const InstDev* g, InstDev* s)
-{
-    static_assert(sizeof(InstDev) % 8 == 0, "descriptor copied in 8-byte words");
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(g);
-    unsigned long long* dst = reinterpret_cast<unsigned long long*>(s);
-    for (int e = threadIdx.x; e < (int)(sizeof(InstDev) / 8); e += blockDim.x) dst[e] = src[e];
-    __syncthreads();
-    return *s;
-}
-
 // ---- separate finalisation launches (used when the stage kernel does not fuse them)
 template <typename T>
 __global__ void __launch_bounds__(32) finalize_cells(const InstDev* __restrict__ insts, int stage)

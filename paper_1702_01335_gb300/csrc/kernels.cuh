@@ -603,6 +603,20 @@ __global__ void records_from_macro(const InstDev* __restrict__ insts, int inst, 
     if (!write_record<T>(I, cell, macro[cell], 1.0 / macro[cell], u, macro[4 * Nz + cell], q)) atomicOr(I.status, 1);
 }
 
+// The instance descriptor copied into shared memory by the whole block at once: its
+// fields (pointers, orders, wall sums) are then one shared load away instead of an
+// L2 round trip each at first use -- in the stage kernel's prologue (pointer, then
+// table, then value) and inside the finalisation's FP64 chains.
+static __device__ __forceinline__ const InstDev& stage_descriptor(const InstDev* g, InstDev* s)
+{
+    static_assert(sizeof(InstDev) % 8 == 0, "descriptor copied in 8-byte words");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(g);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(s);
+    for (int e = threadIdx.x; e < (int)(sizeof(InstDev) / 8); e += blockDim.x) dst[e] = src[e];
+    __syncthreads();
+    return *s;
+}
+
 // ----------------------------------------------------------------------------
 // stage_kernel<T, V, STAGE, RED>: STAGE 1..3 are the RK stages; STAGE 0 only
 // analyses F0 (moments and wall fluxes) without writing F.  RED selects the
@@ -621,8 +635,9 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ double wall_red[kRedSlots];
+    __shared__ InstDev sI;
     const Tile tile = tiles[blockIdx.x];
-    const InstDev& I = insts[tile.inst];
+    const InstDev& I = stage_descriptor(insts + tile.inst, &sI);
     if (*I.active == 0) return;
 
     const int Nz = I.Nz, Q = I.Q, Qx = I.Qx, Qy = I.Qy, Qz = I.Qz, QxQy = I.QxQy;
