@@ -13,7 +13,9 @@
 //                    truncated Hermite equilibrium (Sec. III) of its cells.
 //                    Ghost rows are then built in shared memory: outgoing
 //                    populations by the quadratic extrapolation of the
-//                    Appendix, incoming ones as n_w times the wall equilibrium.
+//                    Appendix, incoming ones as n_w times the wall equilibrium;
+//                    below a half channel's centre line, cells 0..2 at the
+//                    mirrored velocity (bounce-back, Appendix).
 //                    Each thread marches up the z-range for its V velocities
 //                    with a register window: WENO-5 interface fluxes (Eqs.
 //                    weno5_flux - weno_sigma, Table weno), the divergence of
@@ -22,13 +24,18 @@
 //                    moments of F_out (FP32 within a warp in FP32 mode, FP64
 //                    across warps and chunks).  Tiles that end at a wall also
 //                    reduce the outgoing WENO flux of F_out through the wall.
-//                    Finalisation needs no further launch: the CTA that ends
-//                    last among the chunks of a z-tile (threadfence tickets)
-//                    sums their partials in FP64 per cell, forms n, u, P, T, q
-//                    (Eq. qdef) and tau, and writes the cell records of the
-//                    next stage; the one that completes an instance's last
-//                    z-tile forms the wall densities n_w (zero net mass flux,
-//                    Appendix) and, after the third stage, the residual.
+//   finalisation     per cell: the FP64 sum of the chunks' partials, n, u, P,
+//                    T, q (Eq. qdef), tau, and the cell record of the next
+//                    stage; per instance: the wall densities n_w (zero net mass
+//                    flux, Appendix) and, after the third stage, the residual.
+//                    Either a launch of its own (finalize_cells, one thread per
+//                    cell, or finalize_cells_warp, one warp per cell, in
+//                    kernels.cu), or folded into the stage kernel (fuse = 1:
+//                    the CTA that ends last among the chunks of a z-tile does
+//                    its cells, threadfence tickets).
+//
+// Template parameter RED: the reduced phi / chi model of Sec. III (j = 0 phi,
+// j = 1 chi on a two-node transverse axis), otherwise the full 3D velocity set.
 //
 // Storage: F[s][k] for interior cells s = 0..Nz-1 (no ghost rows), velocity
 // k = ((sg*Qz + m)*Qx + i)*Qy + j fastest, holding f_k / w_k.
