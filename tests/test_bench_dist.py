@@ -59,3 +59,20 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     a = argparse.Namespace(gpus=2, steps=1, warmup=0)
     assert bench.run_reference(a) is None
     assert capsys.readouterr().out == ""
+
+
+def test_workload_defaults(monkeypatch):
+    """The low-Mach workload defaults to FP64 (its 1e-5 deviations are below FP32
+    resolution); the others to FP32; an explicit --precision wins."""
+    import bench
+    for argv, want in ((["bench.py"], "f32"), (["bench.py", "--workload", "tables"], "f32"),
+                       (["bench.py", "--workload", "luo"], "f64"),
+                       (["bench.py", "--workload", "luo", "--precision", "f32"], "f32")):
+        monkeypatch.setattr("sys.argv", argv)
+        assert bench.parse().precision == want, argv
+    import workloads as W
+    luo = W.luo_runs()
+    assert [lab["k"] for lab, _ in luo] == [0.03, 0.1, 1.0]
+    assert all(p["Qy"] == 0 and p["Qx"] == 2 and p["half"] == 1 and p["Pr"] == 1.0 for _, p in luo)
+    tab = W.paper_tables(reduced=True)
+    assert len(tab) == 20 and all(p["Qy"] == 0 for _, p in tab)
