@@ -70,8 +70,8 @@ typedef enum { LBS_FP64 = 0, LBS_FP32_STORE_FP64_ACC = 1 } lbs_precision;
 
 /* Velocity-set orders.  N_eq is the order of the truncated Hermite expansion
  * of the equilibrium; each axis uses min(N_eq, Q_a - 1) (Sec. III; Q_a = Qz_half
- * on the wall-normal axis).  Limits: 1 <= Qx <= 64, Qy = 0 (the reduced phi /
- * chi model above) or 1 <= Qy <= 64, 1 <= Qz_half <= 64, 0 <= N_eq <= 8,
+ * on the wall-normal axis).  Limits: 1 <= Qx <= 100, Qy = 0 (the reduced phi /
+ * chi model above) or 1 <= Qy <= 100, 1 <= Qz_half <= 100, 0 <= N_eq <= 8,
  * Q <= 32768. */
 typedef struct { int Qx, Qy, Qz_half, N_eq; } lbs_orders;
 
@@ -242,7 +242,7 @@ lbs_status lbs_get_stream(lbs_handle h, void** out);
 
 /* Host-only: the solver's Q-point Gauss rule for omega(p) = exp(-p^2/2)/sqrt(2 pi),
  * kind 0 = full range (sum w = 1), kind 1 = half range on (0, inf) (sum w = 1/2).
- * Needs no GPU.  LBS_ERR_ARG for Q outside 1..64. */
+ * Needs no GPU.  LBS_ERR_ARG for Q outside 1..100. */
 lbs_status lbs_quadrature(int kind, int Q, double* nodes, double* weights);
 
 /* Couette-flow diagnostics over the half channel 0 <= z <= L/2 (L = 1), in the

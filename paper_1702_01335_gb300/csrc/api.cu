@@ -115,7 +115,7 @@ static lbs_status validate(const lbs_instance_desc& d)
     const lbs_orders& o = d.orders;
     if (o.Qx < 1 || o.Qx > kMaxQ1D || o.Qy < 0 || o.Qy > kMaxQ1D || o.Qz_half < 1 ||
         o.Qz_half > kMaxQ1D)
-        return fail(LBS_ERR_ARG, "velocity orders must lie in 1..64 (Qy = 0: the reduced model)");
+        return fail(LBS_ERR_ARG, "velocity orders must lie in 1..100 (Qy = 0: the reduced model)");
     if (o.N_eq < 0 || o.N_eq > kMaxN) return fail(LBS_ERR_ARG, "N_eq must lie in 0..8");
     if ((long)2 * o.Qx * std::max(o.Qy, 2) * o.Qz_half > 32768)
         return fail(LBS_ERR_ARG, "Q = 2 Qx Qy Qz_half exceeds 32768");
@@ -581,7 +581,7 @@ const char* lbs_last_error(void) { return g_err.c_str(); }
 lbs_status lbs_quadrature(int kind, int Q, double* nodes, double* weights)
 {
     if ((kind != 0 && kind != 1) || Q < 1 || Q > kMaxQ1D || !nodes || !weights)
-        return fail(LBS_ERR_ARG, "kind must be 0 or 1 and Q in 1..64");
+        return fail(LBS_ERR_ARG, "kind must be 0 or 1 and Q in 1..100");
     if (gauss_rule(kind == 0 ? QUAD_FULL : QUAD_HALF, Q, nodes, weights))
         return fail(LBS_ERR_QUADRATURE, "Gauss rule construction failed");
     return LBS_OK;

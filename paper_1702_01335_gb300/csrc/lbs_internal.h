@@ -12,7 +12,7 @@
 
 namespace lbs {
 
-constexpr int kMaxQ1D = 64;     // nodes per axis (per sign on z)
+constexpr int kMaxQ1D = 100;    // nodes per axis (per sign on z): the largest order of the paper
 constexpr int kMaxN = 8;        // equilibrium expansion order
 constexpr int kNMom = 13;       // raw moments accumulated per cell
 constexpr int kRecHead = 12;    // scalars at the head of a cell record

@@ -45,7 +45,7 @@ def test_full_range_rule_matches_oracle(Q):
     assert np.allclose(w, wo, rtol=1e-12, atol=0)
 
 
-@pytest.mark.parametrize("Q", [1, 4, 7, 16, 32, 48, 64])
+@pytest.mark.parametrize("Q", [1, 4, 7, 16, 32, 48, 64, 80, 100])
 def test_half_range_rule_matches_oracle(Q):
     x, w = L.quadrature(1, Q)
     xo, wo = oq.half_range_rule(Q)
@@ -57,7 +57,7 @@ def test_bad_arguments_are_rejected():
     lib = L.load()
     h = C.c_void_p()
     bad = [
-        L.Instance(Qx=0), L.Instance(Qz=65), L.Instance(N_eq=9), L.Instance(Nz=5),
+        L.Instance(Qx=0), L.Instance(Qz=101), L.Instance(N_eq=9), L.Instance(Nz=5),
         L.Instance(Kn=0.0), L.Instance(T_w=-1.0), L.Instance(Pr=0.0), L.Instance(A=1.0),
         L.Instance(cfl=0.0, dt=0.0), L.Instance(visc_law=1, visc_param=0.0),
         L.Instance(Qx=64, Qy=64, Qz=64), L.Instance(half=2), L.Instance(Qy=-1),
