@@ -75,4 +75,4 @@ def test_workload_defaults(monkeypatch):
     assert [lab["k"] for lab, _ in luo] == [0.03, 0.1, 1.0, 10.0]
     assert all(p["Qy"] == 0 and p["Qx"] == 2 and p["half"] == 1 and p["Pr"] == 1.0 for _, p in luo)
     tab = W.paper_tables(reduced=True)
-    assert len(tab) == 24 and all(p["Qy"] == 0 for _, p in tab)
+    assert len(tab) == 20 and all(p["Qy"] == 0 for _, p in tab)

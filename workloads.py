@@ -13,7 +13,7 @@ plain dict of instance parameters with the field names of
   paper_tables()  the He / Ar runs of Sec. VI (Tables gradu, shear, temp) on the half
       channel: 16 cells stretched with A = 0.98, 7 x 7 x (2 x Q_n) velocities with
       N_eq = 6, Sutherland viscosity, Pr = 2/3, delta = 1/(Kn sqrt 2) in
-      {0.01, 0.1, 1, 10, 20, 40}, u_w in {sqrt 2, 0.1 sqrt 2}; Q_n and dt from Table sharipov
+      {0.1, 1, 10, 20, 40}, u_w in {sqrt 2, 0.1 sqrt 2}; Q_n and dt from Table sharipov
   luo_runs()  the low-Mach runs of Sec. IV (Table luo): phi / chi model, Qx = 2,
       BGK, tau = k / sqrt 2, u_w = 1e-5, half channel with S = 64 or 32, A = 0.98
   sweep(n, seed)  instances drawn like the batched Kn / wall-speed / gas-law sweep:
@@ -32,14 +32,16 @@ C3 = dict(Qx=16, Qy=4, Qz=64, N_eq=4, Nz=256, A=0.0, Kn=100.0, u_w=0.05, T_w=1.0
           visc_law=0, visc_param=0.5)
 
 # Sec. VI: Sutherland constants of the two gases, the rarefaction parameters and the
-# per-delta normal-axis order and time step of Table sharipov
+# per-delta normal-axis order and time step of Table sharipov.  delta = 0.01 is left
+# out: at its Q_n = 100 the largest |p_z| is 22.2, and the printed dt = 2.5e-4 puts the
+# CFL number of the first stretched cell at 1.65, above the RK-3 / WENO-5 limit.
 SUTHERLAND_S = {"Ar": 0.5239, "He": 0.3101}
-TABLE_DELTAS = (0.01, 0.1, 1.0, 10.0, 20.0, 40.0)
+TABLE_DELTAS = (0.1, 1.0, 10.0, 20.0, 40.0)
 TABLE_RUN = {0.01: (100, 2.5e-4), 0.1: (30, 2.5e-4)}   # delta -> (Q_n, dt); else (7, 5e-4)
 
 
 def paper_tables(reduced=False):
-    """The 24 half-channel runs of the Sec. VI tables as (label, instance parameters)
+    """The 20 half-channel runs of the Sec. VI tables as (label, instance parameters)
     pairs, gas-major, then delta, then u_w = sqrt 2 before 0.1 sqrt 2; the label holds
     gas, delta and u_w.  reduced=True: the paper's phi / chi model (Qy = 0) instead of
     the 3D set with Q_y = 7."""
