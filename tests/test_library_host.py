@@ -146,3 +146,39 @@ int main() {
                                cpp, "-o", exe])
         worst = float(subprocess.check_output([exe]).decode())
     assert worst < 5e-16, worst
+
+
+def _rk3_upwind5_cfl_limit():
+    """Largest CFL number nu = |p| dt / dz for which RK-3 (Eq. rk3) with the linear
+    fifth-order upwind flux (WENO-5 at its ideal weights d = 1/10, 6/10, 3/10 of the
+    three third-order candidates) is stable for every Fourier mode (von Neumann)."""
+    th = np.linspace(0.0, 2 * np.pi, 4001)
+    # interface value at j+1/2 from f_{j-2..j+2}: the three candidates of Eq. (weno5_flux)
+    c1 = np.array([2, -7, 11, 0, 0]) / 6.0
+    c2 = np.array([0, -1, 5, 2, 0]) / 6.0
+    c3 = np.array([0, 0, 2, 5, -1]) / 6.0
+    coef = 0.1 * c1 + 0.6 * c2 + 0.3 * c3
+    R = sum(coef[m] * np.exp(1j * (m - 2) * th) for m in range(5))
+    sym = -(R - R * np.exp(-1j * th))          # -(F_{j+1/2} - F_{j-1/2}) per unit CFL
+    def stable(nu):
+        z = nu * sym
+        return np.max(np.abs(1 + z + z * z / 2 + z ** 3 / 6)) <= 1 + 1e-12
+    lo, hi = 0.1, 3.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if stable(mid) else (lo, mid)
+    return lo
+
+
+def test_time_step_stability_of_the_table_runs():
+    """The paper's printed time steps against the scheme's linear stability limit
+    (about 1.43): dt = 5e-4 at Q_n = 7 and 2.5e-4 at Q_n = 30 are stable on the 16-cell
+    half channel with A = 0.98; 2.5e-4 at Q_n = 100 (delta = 0.01) is not, and 1e-4 is."""
+    from oracle.oracle import grid
+    nu = _rk3_upwind5_cfl_limit()
+    assert 1.3 < nu < 1.6, nu
+    _, xf = grid(32, 0.98)
+    dz = float(np.min(np.diff(xf)))
+    for Qn, dt, ok in ((7, 5e-4, True), (30, 2.5e-4, True), (100, 2.5e-4, False), (100, 1e-4, True)):
+        x, _ = L.quadrature(1, Qn)
+        assert (x.max() * dt / dz < nu) == ok, (Qn, dt, x.max() * dt / dz, nu)
