@@ -149,7 +149,15 @@ def quadrature(kind, Q):
 
 @dataclasses.dataclass
 class Instance:
-    """One Couette problem (see lbs_instance_desc in include/lbs.h)."""
+    """One Couette problem (see lbs_instance_desc in include/lbs.h).
+
+    Qx, Qy: full-range Gauss-Hermite nodes along the flow and across it; Qy = 0 selects
+    the paper's reduced phi / chi model (the transverse momentum integrated out).
+    Qz: half-range nodes per sign of p_z.  N_eq: equilibrium expansion order.
+    Nz cells; A: tanh stretching (0: uniform).  half = 1: the upper half channel with
+    the bounce-back centre line (Nz cells of a 2 Nz grid).  Kn, u_w, T_w, Pr; the
+    viscosity law (power: omega; Sutherland: S).  dt > 0 is used as given, else
+    dt = cfl * min dz / max |p_z|."""
     Qx: int = 4
     Qy: int = 4
     Qz: int = 4
