@@ -3,6 +3,7 @@ exports every entry point include/lbs.h declares, its quadrature (an algorithm
 independent of the oracle's) agrees with the oracle's, and bad arguments are
 rejected before any device work."""
 import ctypes as C
+import math
 import os
 import re
 import subprocess
@@ -182,3 +183,24 @@ def test_time_step_stability_of_the_table_runs():
     for Qn, dt, ok in ((7, 5e-4, True), (30, 2.5e-4, True), (100, 2.5e-4, False), (100, 1e-4, True)):
         x, _ = L.quadrature(1, Qn)
         assert (x.max() * dt / dz < nu) == ok, (Qn, dt, x.max() * dt / dz, nu)
+
+
+def test_diagnostics_of_the_ballistic_state():
+    """The free-molecular state (the oracle without collisions) has closed-form
+    diagnostics: u = 0 inside, so u_slip = u_w and the mass flow vanishes, and
+    T_xy / T_xy^bal = 1 (Eq. Txy_bal) -- for a full channel and its upper half."""
+    uw, Tw = 0.3, 1.0
+    o = Oracle(4, 4, 4, 3, 16, A=0.5, uw=uw, Tw=Tw, collisions=False)
+    o.step(2500)
+    p = o.profiles()
+    prof = np.stack([p[k] for k in L.PROFILE_NAMES])
+    # the rectangle rule of Eq. (Txy) applied to a constant: 1 up to its O(d_eta^2) error
+    E = math.atanh(0.5)
+    rule = E / (0.5 * 8) * sum(1 / math.cosh((s + 0.5) * E / 8) ** 2 for s in range(8))
+    assert 0 < abs(rule - 1) < 1e-3
+    for half, pr in ((0, prof), (1, prof[:, 8:])):
+        d = L.couette_diagnostics(pr, pr.shape[1], 0.5, half, uw, Tw)
+        assert abs(d["u_slip"] - uw) < 1e-11 and abs(d["mflow"]) < 1e-12
+        assert abs(d["Txy"] / d["Txy_bal"] - rule) < 1e-11
+        assert abs(d["Pi"] - rule / math.sqrt(math.pi)) < 1e-11  # -T_xy / (u_w sqrt 2) at T_w = 1
+        assert abs(d["T0"] - (Tw + uw ** 2 / 3)) < 1e-11
