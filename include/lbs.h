@@ -280,6 +280,15 @@ lbs_status lbs_couette_diagnostics(const double* prof, int Nz, double A, int hal
  * synchronises the solver's stream. */
 lbs_status lbs_diagnostics(lbs_handle h, int inst, lbs_diag* out);
 
+/* Host-only: the nonlinear part of the velocity profile, Eq. (uy_nl):
+ * u_nl(z_s) = 2 z_s / L - u_x(z_s) / u_x(L/2) at the S cells of the half channel
+ * (L = 1, u_x(L/2) by Eq. uslip_extra), from profiles prof[14][Nz] as for
+ * lbs_couette_diagnostics.  unl_out[S] receives u_nl, z_out[S] (may be NULL)
+ * the cell centres z_s.  S = Nz (half = 1) or Nz / 2.  Needs no GPU.
+ * LBS_ERR_ARG as lbs_couette_diagnostics. */
+lbs_status lbs_couette_nonlinear_velocity(const double* prof, int Nz, double A, int half, double* z_out,
+                                          double* unl_out);
+
 /* ---- Warm-start network (not in the paper: the learned initial state of the
  * batched sweep).  A perceptron n_in -> n_hidden -> n_hidden -> n_out with GELU
  * activations, gelu(z) = z (1 + erf(z / sqrt 2)) / 2, maps the parameters of a

@@ -279,6 +279,13 @@ def u_wall(o, ux):
     return tot
 
 
+def u_nonlinear(o, ux):
+    """Eq. (uy_nl) on the upper half: 2 x / L - u_y(x) / u_y(L/2), L = 1, with u_y(L/2)
+    from Eq. (uslip_extra)."""
+    S, x = _half(o)
+    return 2.0 * x - ux[S:] / u_wall(o, ux)
+
+
 def u_slip(o, ux, uw):
     """u_slip = u_w - u_y(L/2), Eq. (uslip)."""
     return uw - u_wall(o, ux)

@@ -596,21 +596,25 @@ static double lagrange_at(double x, const double* xs, const double* ys)
     return w[0] * ys[0] + w[1] * ys[1] + w[2] * ys[2];
 }
 
-lbs_status lbs_couette_diagnostics(const double* prof, int Nz, double A, int half, double u_w, double T_w,
-                                   lbs_diag* out)
+// Checks the grid arguments of the diagnostics; S = the cells of the half channel 0 <= z <= L/2
+// (all Nz of a half channel, the upper Nz/2 of a full one).
+static lbs_status half_cells(int Nz, double A, int half, int* S)
 {
-    if (!prof || !out) return fail(LBS_ERR_ARG, "null profiles or output");
     if (!(A >= 0.0 && A < 1.0) || (half != 0 && half != 1)) return fail(LBS_ERR_ARG, "need 0 <= A < 1, half 0 or 1");
     if (!half && (Nz % 2 != 0 || Nz < 12)) return fail(LBS_ERR_ARG, "a full channel needs an even Nz >= 12");
     if (half && Nz < 6) return fail(LBS_ERR_ARG, "a half channel needs Nz >= 6");
-    const int S = half ? Nz : Nz / 2, s0 = Nz - S;  // cells s0 .. Nz-1 form the upper half
-    const double* n = prof + 0 * (size_t)Nz + s0;
-    const double* u = prof + 1 * (size_t)Nz + s0;
-    const double* T = prof + 4 * (size_t)Nz + s0;
-    const double* Pxz = prof + 12 * (size_t)Nz + s0;
-    // Eq. (etas) on the half channel: eta_s = (s - 1/2) atanh(A) / S, x_s = L tanh(eta_s) / (2A)
+    *S = half ? Nz : Nz / 2;
+    return LBS_OK;
+}
+
+// Eq. (etas) on the half channel: eta_s = (s - 1/2) atanh(A) / S, x_s = L tanh(eta_s) / (2A)
+// (uniform cells for A = 0), and the rectangle-rule weights of Eqs. (mflow), (Txy) divided
+// by L / 2 (they sum to 1 up to the rule's error).
+static void half_positions(int S, double A, std::vector<double>& x, std::vector<double>& wrect)
+{
     const double E = A > 0.0 ? std::atanh(A) : 0.0;
-    std::vector<double> x(S), wrect(S);
+    x.resize(S);
+    wrect.resize(S);
     for (int s = 0; s < S; ++s) {
         if (A > 0.0) {
             const double eta = (s + 0.5) * E / S, c = std::cosh(eta);
@@ -621,6 +625,41 @@ lbs_status lbs_couette_diagnostics(const double* prof, int Nz, double A, int hal
             wrect[s] = 1.0 / S;
         }
     }
+}
+
+lbs_status lbs_couette_nonlinear_velocity(const double* prof, int Nz, double A, int half, double* z_out,
+                                          double* unl_out)
+{
+    if (!prof || !unl_out) return fail(LBS_ERR_ARG, "null profiles or output");
+    int S = 0;
+    lbs_status st = half_cells(Nz, A, half, &S);
+    if (st != LBS_OK) return st;
+    const double* u = prof + 1 * (size_t)Nz + (Nz - S);
+    std::vector<double> x, wrect;
+    half_positions(S, A, x, wrect);
+    const double xw[3] = {x[S - 1], x[S - 2], x[S - 3]}, uw3[3] = {u[S - 1], u[S - 2], u[S - 3]};
+    const double uwall = lagrange_at(0.5, xw, uw3);  // u_x(L/2), Eq. (uslip_extra)
+    for (int s = 0; s < S; ++s) {
+        unl_out[s] = 2.0 * x[s] - u[s] / uwall;  // Eq. (uy_nl) with L = 1
+        if (z_out) z_out[s] = x[s];
+    }
+    return LBS_OK;
+}
+
+lbs_status lbs_couette_diagnostics(const double* prof, int Nz, double A, int half, double u_w, double T_w,
+                                   lbs_diag* out)
+{
+    if (!prof || !out) return fail(LBS_ERR_ARG, "null profiles or output");
+    int S = 0;
+    lbs_status st = half_cells(Nz, A, half, &S);
+    if (st != LBS_OK) return st;
+    const int s0 = Nz - S;  // cells s0 .. Nz-1 form the upper half
+    const double* n = prof + 0 * (size_t)Nz + s0;
+    const double* u = prof + 1 * (size_t)Nz + s0;
+    const double* T = prof + 4 * (size_t)Nz + s0;
+    const double* Pxz = prof + 12 * (size_t)Nz + s0;
+    std::vector<double> x, wrect;
+    half_positions(S, A, x, wrect);
     lbs_diag d;
     const double xw[3] = {x[S - 1], x[S - 2], x[S - 3]}, uw3[3] = {u[S - 1], u[S - 2], u[S - 3]};
     d.u_wall = lagrange_at(0.5, xw, uw3);

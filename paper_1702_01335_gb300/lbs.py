@@ -64,7 +64,7 @@ EXPORTS = ("lbs_create", "lbs_batch_create", "lbs_destroy", "lbs_step", "lbs_run
            "lbs_get_state", "lbs_set_state", "lbs_init_from_profiles", "lbs_quadrature",
            "lbs_get_stream", "lbs_profile_steps", "lbs_moments_static", "lbs_set_tiling",
            "lbs_get_tiling", "lbs_last_error", "lbs_couette_diagnostics", "lbs_diagnostics",
-           "lbs_set_finalize",
+           "lbs_set_finalize", "lbs_couette_nonlinear_velocity",
            # the warm-start network (bound in warmstart.py)
            "lbs_mlp_create", "lbs_mlp_destroy", "lbs_mlp_num_params", "lbs_mlp_set_params",
            "lbs_mlp_get_params", "lbs_mlp_forward", "lbs_mlp_loss_grad", "lbs_mlp_adam",
@@ -103,6 +103,7 @@ def load(build_if_missing=True):
         lib.lbs_couette_diagnostics.argtypes = [D, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
                                                 C.POINTER(_Diag)]
         lib.lbs_diagnostics.argtypes = [P, C.c_int, C.POINTER(_Diag)]
+        lib.lbs_couette_nonlinear_velocity.argtypes = [D, C.c_int, C.c_double, C.c_int, D, D]
         lib.lbs_set_finalize.argtypes = [P, C.c_int, C.POINTER(C.c_int)]
         lib.lbs_get_stream.argtypes = [P, H]
         lib.lbs_profile_steps.argtypes = [P, C.c_long, D]
@@ -137,6 +138,18 @@ def couette_diagnostics(prof, Nz, A, half, u_w, T_w=1.0):
     d = _Diag()
     _check(lib.lbs_couette_diagnostics(_dptr(prof), Nz, A, half, u_w, T_w, C.byref(d)))
     return {k: getattr(d, k) for k in DIAG_NAMES}
+
+
+def couette_nonlinear_velocity(prof, Nz, A, half):
+    """(z_s, u_nl(z_s)) over the half channel, Eq. (uy_nl), from profiles [14, Nz]."""
+    lib = load()
+    prof = np.ascontiguousarray(prof, dtype=np.float64)
+    if prof.shape != (14, Nz):
+        raise ValueError("profiles must have shape (14, Nz)")
+    S = Nz if half else Nz // 2
+    z, u = np.zeros(S), np.zeros(S)
+    _check(lib.lbs_couette_nonlinear_velocity(_dptr(prof), Nz, A, half, _dptr(z), _dptr(u)))
+    return z, u
 
 
 def quadrature(kind, Q):
@@ -312,6 +325,12 @@ class Solver:
         d = _Diag()
         _check(self.lib.lbs_diagnostics(self.h, inst, C.byref(d)))
         return {k: getattr(d, k) for k in DIAG_NAMES}
+
+    def nonlinear_velocity(self, inst=0):
+        """(z_s, u_nl) of instance inst: the departure from the straight profile, Eq. (uy_nl)."""
+        I = self.instances[inst]
+        p = self.profiles(inst)
+        return couette_nonlinear_velocity(np.stack([p[k] for k in PROFILE_NAMES]), I.Nz, I.A, I.half)
 
     def residual(self, inst=0):
         r = C.c_double()

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from oracle import quadrature as oq
-from oracle.oracle import Oracle, mass_flow, nu_center, pi_stress, t_center, txy_average, u_wall
+from oracle.oracle import Oracle, mass_flow, nu_center, pi_stress, t_center, txy_average, u_nonlinear, u_wall
 from paper_1702_01335_gb300 import lbs as L
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -120,6 +120,9 @@ def test_diagnostics_match_oracle(A, S):
             assert abs(d["mflow"] - 0.5 * np.mean(prof[0][S:] * prof[1][S:])) < 1e-13
         assert d["mflow_hydro"] == uw / 4
         assert abs(d["Txy_bal"] + uw * np.sqrt(2 * Tw / np.pi)) < 1e-15
+        z, unl = L.couette_nonlinear_velocity(p, p.shape[1], A, half)
+        assert np.abs(z - x[S:]).max() < 1e-14
+        assert np.abs(unl - u_nonlinear(o, prof[1])).max() < 1e-11
 
 
 def test_erfc_series_against_libm():

@@ -15,7 +15,7 @@ from scipy import integrate, special, stats
 
 from oracle import quadrature as quad
 from oracle.oracle import (VISC_POWER, VISC_SUTHERLAND, Oracle, mass_flow, nu_center, pi_stress,
-                           t_center, txy_average, u_slip, u_wall, weno5)
+                           t_center, txy_average, u_nonlinear, u_slip, u_wall, weno5)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -417,6 +417,18 @@ def test_postprocessing_exact_on_polynomials():
     # x^3 is missed by exactly the interpolation remainder prod (L/2 - x_s) over the last three cells
     r = np.prod(0.5 - x[-3:])
     assert abs(u_wall(o, x ** 3) - (0.125 - r)) < 1e-15 and r > 1e-9
+
+
+def test_nonlinear_velocity_profile():
+    """Eq. (uy_nl): a straight profile u = c x (the Navier-Stokes one with slip) has no
+    nonlinear part; for u = x^3 it is 2x - x^3 / (1/8 - r), r the interpolation
+    remainder of the wall extrapolation (Eq. uslip_extra)."""
+    o = Oracle(2, 2, 2, 1, 32, A=0.9)
+    x = o.xc[3:3 + o.Nz]
+    assert np.abs(u_nonlinear(o, 0.37 * x)).max() < 1e-14
+    xs = x[16:]
+    r = np.prod(0.5 - xs[-3:])
+    assert np.abs(u_nonlinear(o, x ** 3) - (2 * xs - xs ** 3 / (0.125 - r))).max() < 1e-14
 
 
 @pytest.mark.parametrize("A", [0.5, 0.98])
