@@ -79,6 +79,11 @@ def test_bad_arguments_are_rejected():
         with pytest.raises(L.LbsError):
             L.couette_diagnostics(np.zeros((14, Nz)), Nz, A, half, 0.1)
     assert lib.lbs_couette_diagnostics(None, 12, 0.5, 0, 0.1, 1.0, None) == 1
+    assert lib.lbs_couette_nonlinear_velocity(None, 12, 0.5, 0, None, None) == 1
+    for Nz, A, half in ((11, 0.5, 0), (5, 0.5, 1), (12, -0.1, 0)):
+        with pytest.raises(L.LbsError):
+            L.couette_nonlinear_velocity(np.ones((14, Nz)), Nz, A, half)
+    assert lib.lbs_set_finalize(None, 1, None) == 1
     assert L.couette_diagnostics(prof, 12, 0.5, 0, 0.1)["Txy"] == 0.0
 
 
