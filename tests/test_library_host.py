@@ -212,3 +212,56 @@ def test_diagnostics_of_the_ballistic_state():
         assert abs(d["Txy"] / d["Txy_bal"] - rule) < 1e-11
         assert abs(d["Pi"] - rule / math.sqrt(math.pi)) < 1e-11  # -T_xy / (u_w sqrt 2) at T_w = 1
         assert abs(d["T0"] - (Tw + uw ** 2 / 3)) < 1e-11
+
+
+def test_autotuner_host_logic(monkeypatch, tmp_path):
+    """autotune.py without a GPU (timings from a stand-in solver): it keeps the fastest
+    valid candidate, skips rejected ones, writes the choice under the kernel hash and the
+    batch signature, drops entries of other kernel versions, and answers a repeated call
+    from the cache without timing again."""
+    import json
+    from paper_1702_01335_gb300 import autotune as AT
+
+    made = []
+
+    class FakeSolver:
+        def __init__(self, instances, precision=1):
+            self.instances, self.precision, self.t = instances, precision, None
+            made.append(self)
+
+        def set_tiling(self, V, ZT, F):
+            if ZT > 64:
+                raise L.LbsError(1, "tiling")
+            self.t = (V, ZT, F)
+
+        def profile_steps(self, n):
+            V, ZT, F = self.t
+            ms = (1.0 + abs(V - 2) + abs(ZT - 12) / 10 + F) * n  # fastest: V = 2, ZT = 12, F = 0
+            return 0.9 * ms, 0.1 * ms, ms
+
+        def tiling(self):
+            return {"ctas": 1}
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(AT, "Solver", FakeSolver)
+    monkeypatch.setattr(AT, "_cache", {})
+    cache = tmp_path / "cache.json"
+    cache.write_text(json.dumps({"0000000000000000:p1:9x9": {"V": 1, "ZT": 4, "fuse": 0}}))
+    target = FakeSolver([L.Instance(Nz=16), L.Instance(Nz=16), L.Instance(Nz=24)], precision=1)
+    made.clear()
+    r = AT.autotune(target, candidates=((1, 8, 0), (2, 12, 0), (2, 12, 1), (4, 99, 0)), steps=3,
+                    cache_file=str(cache))
+    assert (r["V"], r["ZT"], r["fuse"]) == (2, 12, 0) and target.t == (2, 12, 0)
+    assert len(r["table"]) == 3 and len(made) == 1  # one scratch solver; the invalid one skipped
+    disk = json.loads(cache.read_text())
+    key = AT.signature(target)
+    assert list(disk) == [key] and key.startswith(AT.kernel_hash() + ":p1:")
+    assert key.endswith("2*16x128,24x128")
+    monkeypatch.setattr(AT, "_cache", {})
+    made.clear()
+    again = FakeSolver(target.instances, precision=1)
+    made.clear()
+    r2 = AT.autotune(again, cache_file=str(cache))
+    assert (r2["V"], r2["ZT"], r2["fuse"]) == (2, 12, 0) and again.t == (2, 12, 0) and not made
