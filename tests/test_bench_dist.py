@@ -76,3 +76,21 @@ def test_workload_defaults(monkeypatch):
     assert all(p["Qy"] == 0 and p["Qx"] == 2 and p["half"] == 1 and p["Pr"] == 1.0 for _, p in luo)
     tab = W.paper_tables(reduced=True)
     assert len(tab) == 20 and all(p["Qy"] == 0 for _, p in tab)
+
+
+def test_clock_summary_parses_throttle_reasons():
+    """bench.Clocks.summary: the median SM clock under load, the maximum, and every
+    throttle reason that was active in any sample (from nvidia-smi's CSV lines)."""
+    import bench
+    c = bench.Clocks(0)
+    c.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.lines = ["0, 1500, 2070, 1000.0, 0x8, Active, Not Active, Active, Not Active"]
+    assert bench.Clocks(0).summary()["reasons"] == ["no samples"]
+    s = c.summary()
+    assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and s["sm_mhz"] == 1500.0
