@@ -3,7 +3,8 @@
 Workload (the metric's configuration, config C2): Maxwell molecules, Shakhov
 Pr = 2/3, mu ~ T; Kn = 1, u_w = 0.5, T_w = 1; Nz = 128 cells stretched toward the
 walls (A = 0.98); 8 x 8 full-range x 2 x 16 half-range = 2048 velocities,
-equilibrium order 4; f stored in FP32 with FP64 moment sums.  One step is one
+equilibrium order 4; f stored in FP32 (deviations from the rest state with a
+16-bit rounding residual) with FP64 moment sums.  One step is one
 full RK-3 step (three stages: walls, WENO-5 advection, Shakhov relaxation,
 moments, residual) of a batch of B = 256 independent replicas of C2 on each GPU
 (256 MiB per state buffer, larger than the 129 MB L2, so no L2 flush is needed).
@@ -13,7 +14,7 @@ CUDA events on the solver's stream around exactly --steps steps after --warmup
 steps, max time over ranks.  `e2e` repeats the measurement through the public
 API with the state uploaded from pinned host memory and the profiles read back
 every step.  `roofline` relates the stage kernels' live event time to their
-algorithmic bytes (32 B per update and step in FP32) and the measured HBM copy
+algorithmic bytes (36 B per update and step in FP32) and the measured HBM copy
 bandwidth.  `cpu_baseline` times the FP64 CPU oracle on a bounded sample.
 
 --impl reference times that oracle (the only reference this method has) on the
@@ -34,7 +35,10 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 BATCH = 256
-BYTES_PER_UPDATE = {"f32": 32, "f64": 64}   # algorithmic HBM bytes per update per RK-3 step
+# algorithmic HBM bytes per update per RK-3 step.  FP32: stage 1 reads d, writes d1 (8);
+# stage 2 reads d, d1, writes d2 (12); stage 3 reads d, d2 and the 2-byte residual and
+# writes d and the residual (16).  FP64: 16 + 24 + 24, no residual.
+BYTES_PER_UPDATE = {"f32": 36, "f64": 64}
 
 
 def parse():
@@ -407,8 +411,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": a.precision, "data": "synthetic",
             "config": {"workload": "C2 Shakhov Maxwell molecules Kn=1 u_w=0.5 T_w=1 Pr=2/3 "
                                    "Nz=128 A=0.98 Q=8x8x(2x16)=2048 N_eq=4",
-                       "batch_per_gpu": a.batch, "state_bytes_per_buffer": s.state_bytes(),
-                       "l2": "inputs larger than L2 (3 buffers of %d MiB)" % (s.state_bytes() >> 20),
+                       "batch_per_gpu": a.batch, "state_bytes": s.state_bytes(),
+                       "l2": "inputs larger than L2 (d and two stage increments of %d MiB each)" % (
+                           upd_step * (4 if a.precision == "f32" else 8) >> 20),
                        "parallelism": "replicas, independent batches per GPU",
                        "tiling": {"V": tuned["V"], "ZT": tuned["ZT"], "fused_finalise": tuned["fuse"],
                                   "chosen_by": tuned.get("source", "autotune.py (CUDA-event timing of "

@@ -58,14 +58,25 @@ typedef enum {
     LBS_ERR_CUDA = 2,             /* a CUDA runtime call failed                */
     LBS_ERR_NONFINITE = 3,        /* NaN/Inf or n <= 0 / T <= 0 in a state      */
     LBS_ERR_NO_CONVERGENCE = 4,   /* residual target not met within max_steps  */
-    LBS_ERR_QUADRATURE = 5        /* quadrature construction failed            */
+    LBS_ERR_QUADRATURE = 5,       /* quadrature construction failed            */
+    LBS_ERR_TIMEOUT = 6           /* a kernel's bounded wait for its bulk
+                                     copies ran out (see lbs_set_wait_limit)   */
 } lbs_status;
 
 typedef enum { LBS_VISC_POWER = 0, LBS_VISC_SUTHERLAND = 1 } lbs_visc_law;
 
-/* Storage/arithmetic precision of the distribution.  FP32 stores and relaxes f
- * in FP32; moment sums across warps, the wall flux balance, the profiles and
- * the residual are FP64 in both modes. */
+/* Storage/arithmetic precision of the distribution.  The state is stored as the
+ * deviation d_k = f_k / w_k - 1 of the normalised populations from the rest
+ * Maxwellian (n = 1, u = 0, T = 1: f_k = w_k), so that the stored digits resolve the
+ * departure from rest rather than the rest state itself.  FP32 stores and relaxes
+ * d in FP32 and keeps the rounding residual of each stored value as a 16-bit
+ * fixed-point fraction of its last place: a step's increment, far below an FP32
+ * ulp near a steady state, then accumulates instead of being rounded away
+ * (without it the state stalls about eps_32 / (lambda dt) short of the steady
+ * state, lambda the decay rate of the slowest mode).  The RK stages hold their
+ * increments over the step's start state, not stage values, for the same reason.
+ * Moment sums across warps, the wall flux balance, the profiles and the residual
+ * are FP64 in both modes. */
 typedef enum { LBS_FP64 = 0, LBS_FP32_STORE_FP64_ACC = 1 } lbs_precision;
 
 /* Velocity-set orders.  N_eq is the order of the truncated Hermite expansion
@@ -158,18 +169,37 @@ lbs_status lbs_steps_taken(lbs_handle h, int inst, long* out);
  * the stored distribution; dt_out (may be NULL) receives the time step. */
 lbs_status lbs_info(lbs_handle h, int inst, long* out, double* dt_out);
 
-/* Checkpoint: copy the distribution of instance inst, [Nz][Q] in the velocity
- * order k = ((sg * Qz_half + m) * Qx + i) * Qy + j (sg = 0: p_z > 0), as
- * normalised populations f_k / w_k in the stored precision, to dst (host if
- * to_host, else device).  inst = -1: every instance, concatenated in order. */
+/* Checkpoint: copy the distribution of instance inst to dst (host if to_host,
+ * else device) exactly as stored: first d[Nz][Q], the deviations
+ * d_k = f_k / w_k - 1 in the stored precision (8-byte doubles or 4-byte floats),
+ * velocity order k = ((sg * Qz_half + m) * Qx + i) * Qy + j (sg = 0: p_z > 0);
+ * then, with FP32 storage only, r[Nz][Q], the 16-bit residuals (int16: the value
+ * is d_k + r_k * 2^-15 ulp(d_k); zero is always valid).  So an instance takes
+ * Nz Q 8 bytes (FP64) or Nz Q 6 bytes (FP32).  inst = -1: every instance's d,
+ * concatenated in instance order, then every instance's r, concatenated.
+ * Synchronises the stream. */
 lbs_status lbs_get_state(lbs_handle h, int inst, void* dst, int to_host);
 
 /* Resume / warm start: set the distribution of instance inst from src (layout
  * and precision of lbs_get_state; host if from_host, else device) and
  * recompute its moments and wall densities.  inst = -1: every instance from
- * one concatenated buffer.  LBS_ERR_NONFINITE if the state has non-finite
- * values or n <= 0 or T <= 0 in a cell. */
+ * one buffer laid out as lbs_get_state's.  LBS_ERR_NONFINITE if the state has
+ * non-finite values or n <= 0 or T <= 0 in a cell. */
 lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host);
+
+/* Tests of failure detection: the number of spins a stage CTA waits for its bulk
+ * copies (cp.async.bulk into shared memory, one mbarrier) before it gives up,
+ * flags the instance and leaves; default 2^26 (seconds).  When a wait runs out the
+ * CTA waits up to a further 2^28 spins for its copies in flight to land, so that none
+ * writes shared memory after it has left, then returns without output; the next
+ * call that checks the status returns LBS_ERR_TIMEOUT.  spins = 0 gives up at once
+ * (the copies still land).  Applies to every instance; synchronises the stream. */
+lbs_status lbs_set_wait_limit(lbs_handle h, unsigned spins);
+
+/* Clear the status words of every instance (after LBS_ERR_TIMEOUT or
+ * LBS_ERR_NONFINITE); the state is left as it is, so a caller resumes with
+ * lbs_set_state.  Synchronises the stream. */
+lbs_status lbs_clear_status(lbs_handle h);
 
 /* Warm start: seed instance inst with the discrete Shakhov target of the given
  * profiles in every cell.  prof[8][Nz] has the layout of lbs_moments (the P_ij
@@ -183,11 +213,12 @@ lbs_status lbs_init_from_profiles(lbs_handle h, int inst, const double* prof);
  * example code running under another framework's device-memory budget, or a
  * latency-critical loop where the device-wide synchronisation of cudaMalloc
  * and cudaFree is not acceptable.
- *   f_dev     device pointer, [Nz][Q] normalised populations of instance inst's
- *             velocity set in the handle's precision (layout of lbs_get_state);
- *             read only.
+ *   f_dev     device pointer, [Nz][Q] deviations d_k = f_k / w_k - 1 of instance
+ *             inst's velocity set in the handle's precision (the d part of an
+ *             lbs_get_state buffer; the FP32 residuals are not needed); read only.
  *   prof_dev  device pointer, [14][Nz] FP64 output in the layout of
- *             lbs_profiles.
+ *             lbs_profiles.  A cell whose density sums to zero gets NaN
+ *             profiles; the call reports no status for it.
  * The work is queued on the handle's stream; the call does not wait for it.
  * Its only scratch is a fixed 2 MiB array in the library's device image (every
  * GPU that loads the library holds it until the process exits), so the
@@ -195,8 +226,9 @@ lbs_status lbs_init_from_profiles(lbs_handle h, int inst, const double* prof);
  * first call on a device looks the array's address up (cudaGetSymbolAddress);
  * make that first call before any stream capture.  All calls share the array:
  * calls whose GPU work overlaps (other streams, other threads on the same
- * device) race and must be serialised by the caller.  The call allocates
- * nothing and frees nothing. */
+ * device) race and must be serialised by the caller.  The array's address is
+ * cached per device for the life of the process; like every handle, it is not
+ * valid across cudaDeviceReset.  The call allocates nothing and frees nothing. */
 lbs_status lbs_moments_static(lbs_handle h, int inst, const void* f_dev, double* prof_dev);
 
 /* Run nsteps steps launching every kernel directly with CUDA events around
@@ -325,6 +357,13 @@ lbs_status lbs_mlp_loss_grad(lbs_mlp_handle h, const float* x_dev, const float* 
 lbs_status lbs_mlp_adam(lbs_mlp_handle h, float lr, float beta1, float beta2, float eps);
 /* The network's CUDA stream. */
 lbs_status lbs_mlp_get_stream(lbs_mlp_handle h, void** out);
+
+/* Measurement helper (not in the paper): the current device's fused multiply-add
+ * rate in FLOP/s (2 per FMA), FP64 and FP32, from CUDA events around a kernel of
+ * independent FMA chains (8 per thread, 8 blocks of 256 threads per SM, best of 3
+ * launches).  The FP64 solver is bound by this FP64 rate rather than by HBM.
+ * Allocates and frees a few bytes of device memory; synchronises the device. */
+lbs_status lbs_probe_fma_rate(double* fp64_flops, double* fp32_flops);
 
 /* Message of the last error of the calling thread ("" if none). */
 const char* lbs_last_error(void);

@@ -482,8 +482,10 @@ static void res_profiles(const oracle_cfg *c, const double *F, double *W)
     }
 }
 
-/* R = max over W in {n, u_x, T} of ||W_new - W_old||_2 / max(||W_old||_2, 1e-30). */
-static double residual(int Nz, const double *Wo, const double *Wn)
+/* R = max over W in {n, u_x, T} of ||W_new - W_old||_2 / max(||W_old||_2, 1e-30);
+ * W[3][Nz] holds n, u_x, T of the interior cells (the paper states no criterion:
+ * this is the solver's).  Exported for its pin.                              */
+double oracle_residual(int Nz, const double *Wo, const double *Wn)
 {
     double R = 0.0;
     for (int a = 0; a < 3; ++a) {
@@ -524,7 +526,7 @@ void oracle_step(const oracle_cfg *c, double *F0, long nsteps, double *res)
             F0[e] = F0[e] / 3.0 + 2.0 * F2[e] / 3.0 + 2.0 * dt * L[e] / 3.0;
         if (res) {
             res_profiles(c, F0, Wn);
-            res[it] = residual(Nz, Wo, Wn);
+            res[it] = oracle_residual(Nz, Wo, Wn);
             double *t = Wo; Wo = Wn; Wn = t;
         }
     }

@@ -76,6 +76,8 @@ def _load():
             lib.oracle_weno5.restype = C.c_double
             lib.oracle_tau.argtypes = [P, C.c_double, C.c_double]
             lib.oracle_tau.restype = C.c_double
+            lib.oracle_residual.argtypes = [C.c_int, D, D]
+            lib.oracle_residual.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -229,6 +231,14 @@ class Oracle:
 
     def mass(self):
         return float(np.sum(self.profiles()["n"] * self.cell_widths()))
+
+
+def residual(W_old, W_new):
+    """The oracle's residual of one step from W[3][Nz] = (n, u_x, T) before and after."""
+    a = np.ascontiguousarray(W_old, dtype=np.float64)
+    b = np.ascontiguousarray(W_new, dtype=np.float64)
+    assert a.shape == b.shape and a.shape[0] == 3
+    return _load().oracle_residual(a.shape[1], _ptr(a), _ptr(b))
 
 
 def weno5(v):

@@ -7,8 +7,8 @@ moment reduction is amortised; it does not change the arithmetic.
 `autotune(solver)` times every candidate with CUDA events on a scratch solver
 built from the same instances (so the caller's state and step counters are not
 touched), applies the fastest tiling to `solver`, and caches the choice per
-batch signature (precision and the (Nz, Q) of every instance) in memory and,
-optionally, in a JSON file.
+batch signature (kernel sources, precision, GPU model, and the size, velocity model
+and channel of every instance) in memory and, optionally, in a JSON file.
 """
 import hashlib
 import itertools
@@ -36,11 +36,26 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
+def device_tag():
+    """The GPU a timing belongs to: its name and SM count ("cpu" without one)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pr = torch.cuda.get_device_properties(torch.cuda.current_device())
+            return "%s/%dsm" % (pr.name.replace(" ", "_"), pr.multi_processor_count)
+    except Exception:
+        pass
+    return "cpu"
+
+
 def signature(solver):
-    """Kernel hash, precision and the (Nz, Q) of the batch's instances, run-length
-    encoded ("256*128x2048")."""
-    runs = [(k, len(list(g))) for k, g in itertools.groupby("%dx%d" % (i.Nz, i.Q) for i in solver.instances)]
-    return "%s:p%d:" % (kernel_hash(), solver.precision) + ",".join(
+    """Kernel hash, precision, the GPU, and the (Nz, Q) of the batch's instances with
+    the velocity model (r: the reduced phi / chi model, which runs other kernels) and
+    the channel (h: a half channel), run-length encoded ("256*128x2048")."""
+    def tag(i):
+        return "%dx%d%s%s" % (i.Nz, i.Q, "r" if i.Qy == 0 else "", "h" if i.half else "")
+    runs = [(k, len(list(g))) for k, g in itertools.groupby(tag(i) for i in solver.instances)]
+    return "%s:p%d:%s:" % (kernel_hash(), solver.precision, device_tag()) + ",".join(
         ("%d*%s" % (n, k)) if n > 1 else k for k, n in runs)
 
 

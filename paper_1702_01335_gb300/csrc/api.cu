@@ -86,6 +86,7 @@ struct lbs_solver {
     double* prof_all = nullptr;
     size_t prof_all_n = 0;
     int* status_all = nullptr;
+    int* cur_all = nullptr;  // per instance: which of F0 / F1 holds the state
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0;
     // split stepping (fuse = 2): instances [0, nA) on stream, [nA, ninst) on stream2
@@ -244,7 +245,8 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
     Pool pool;
     struct Off {
         size_t Hx, Hy, Pz, alpha, beta, px, py, xi, wx, wy, wz, gxt, gxb, gwy, gwz, idz;
-        size_t F0, F1, F2, rec, partial, flux, nw, prof, Wold, Wnew, res, steps, active, status, zcount, icount;
+        size_t F0, F1, F2, L0, cur, rec, partial, flux, nw, prof, Wold, Wnew, res, steps, active, status, zcount,
+            icount;
     };
     std::vector<Off> off(h->ninst);
     struct Tables {
@@ -295,24 +297,28 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         else
             hermite_basis(t.py.data(), I.Qy, I.Ny, t.Hy.data());
         half_basis(t.xi.data(), I.Qz, I.Nzq, t.alpha, t.beta, t.Pz.data());
-        // wall equilibria per axis (n = 1, T = T_w, u = +-u_w along x, q = 0)
+        // wall equilibria per axis (n = 1, T = T_w, u = +-u_w along x, q = 0), stored as the
+        // deviations of the normalised factors from 1: sum_l (c_l - r_l) basis_l with the
+        // rest coefficients r (1, 0, 0, ...) on x and y, (1, 1) on the reduced y (factors
+        // 1 and T), (1/2, 0, ...) on z, as the cell records hold them
         double a[kMaxN + 1], bb[kMaxN + 1];
         t.gxt.assign(I.Qx, 0.0); t.gxb.assign(I.Qx, 0.0); t.gwy.assign(I.Qy, 0.0); t.gwz.assign(2 * I.Qz, 0.0);
         full_coeffs(d.u_w, d.T_w, I.Nx, a);
         for (int i = 0; i < I.Qx; ++i)
-            for (int l = 0; l <= I.Nx; ++l) t.gxt[i] += a[l] * t.Hx[i * (I.Nx + 1) + l];
+            for (int l = 1; l <= I.Nx; ++l) t.gxt[i] += a[l] * t.Hx[i * (I.Nx + 1) + l];
         full_coeffs(-d.u_w, d.T_w, I.Nx, a);
         for (int i = 0; i < I.Qx; ++i)
-            for (int l = 0; l <= I.Nx; ++l) t.gxb[i] += a[l] * t.Hx[i * (I.Nx + 1) + l];
+            for (int l = 1; l <= I.Nx; ++l) t.gxb[i] += a[l] * t.Hx[i * (I.Nx + 1) + l];
         if (I.reduced) {  // phi_w and chi_w = T_w phi_w
-            t.gwy[0] = 1.0;
-            t.gwy[1] = d.T_w;
+            t.gwy[0] = 0.0;
+            t.gwy[1] = d.T_w - 1.0;
         } else {
             full_coeffs(0.0, d.T_w, I.Ny, a);
             for (int j = 0; j < I.Qy; ++j)
-                for (int l = 0; l <= I.Ny; ++l) t.gwy[j] += a[l] * t.Hy[j * (I.Ny + 1) + l];
+                for (int l = 1; l <= I.Ny; ++l) t.gwy[j] += a[l] * t.Hy[j * (I.Ny + 1) + l];
         }
         half_coeffs(0.0, d.T_w, I.Nzq, t.alpha.data(), t.beta.data(), bb);
+        bb[0] -= 0.5;  // exactly 0: erfc(0) = 1
         for (int m = 0; m < I.Qz; ++m)
             for (int l = 0; l <= I.Nzq; ++l) {
                 t.gwz[m] += bb[l] * t.Pz[m * (I.Nzq + 1) + l];
@@ -360,19 +366,45 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         lagrange3(xc[2], xc[3], xc[4], xc[5], D.ext_bot[0]);
         lagrange3(xc[1], xc[2], xc[3], xc[4], D.ext_bot[1]);
         // D = sum over incoming velocities of w p_z Gw, from the stored (rounded) tables
+        // (Gw = 1 + the stored deviation on each axis)
         const std::vector<double> wx = rounded<T>(t.wx), wy = rounded<T>(t.wy), wz = rounded<T>(t.wz);
         const std::vector<double> xi = rounded<T>(t.xi), gxt = rounded<T>(t.gxt), gxb = rounded<T>(t.gxb);
         const std::vector<double> gwy = rounded<T>(t.gwy), gwz = rounded<T>(t.gwz);
+        const std::vector<double> px = rounded<T>(t.px), py = rounded<T>(t.py);
         double sxt = 0, sxb = 0, sy = 0, szp = 0, szm = 0;
-        for (int i = 0; i < I.Qx; ++i) { sxt += wx[i] * gxt[i]; sxb += wx[i] * gxb[i]; }
-        for (int j = 0; j < I.Qy; ++j) sy += wy[j] * gwy[j];
-        if (I.reduced) sy = gwy[0];  // mass is carried by phi alone
+        for (int i = 0; i < I.Qx; ++i) { sxt += wx[i] * (1.0 + gxt[i]); sxb += wx[i] * (1.0 + gxb[i]); }
+        for (int j = 0; j < I.Qy; ++j) sy += wy[j] * (1.0 + gwy[j]);
+        if (I.reduced) sy = 1.0 + gwy[0];  // mass is carried by phi alone
         for (int m = 0; m < I.Qz; ++m) {
-            szp += wz[m] * xi[m] * gwz[m];
-            szm += wz[m] * (-xi[m]) * gwz[I.Qz + m];
+            szp += wz[m] * xi[m] * (1.0 + gwz[m]);
+            szm += wz[m] * (-xi[m]) * (1.0 + gwz[I.Qz + m]);
         }
         D.Dtop = sxt * sy * szm;
         D.Dbot = sxb * sy * szp;
+        // the rest state f = w: its raw moments (the kernels sum the deviations from it)
+        // and its outgoing flux through each wall, over the stored nodes and weights
+        for (int a2 = 0; a2 < kNMom; ++a2) D.mrest[a2] = 0.0;
+        D.frest_top = D.frest_bot = 0.0;
+        for (int sg = 0; sg < 2; ++sg)
+            for (int m = 0; m < I.Qz; ++m)
+                for (int i = 0; i < I.Qx; ++i)
+                    for (int j = 0; j < I.Qy; ++j) {
+                        const double w = wx[i] * wy[j] * wz[m];
+                        const double X = px[i], Y = I.reduced ? 0.0 : py[j], Z = sg ? -xi[m] : xi[m];
+                        if (I.reduced && j == 1) {  // chi: the p_y^2 moments only
+                            D.mrest[5] += w;
+                            D.mrest[10] += w * X;
+                            D.mrest[12] += w * Z;
+                            continue;
+                        }
+                        const double p2 = X * X + Y * Y + Z * Z, m1[kNMom] = {
+                            1.0, X, Y, Z, X * X, Y * Y, Z * Z, X * Y, X * Z, Y * Z, p2 * X, p2 * Y, p2 * Z};
+                        for (int a2 = 0; a2 < kNMom; ++a2) D.mrest[a2] += w * m1[a2];
+                        if (sg) D.frest_bot += w * Z;
+                        else D.frest_top += w * Z;
+                    }
+        if (half) D.frest_bot = 0.0;  // no wall below a half channel
+        D.wait_limit = kWaitLimit;
         // weighted sums of the stored basis tables (exactly delta_l0 before rounding)
         {
             const std::vector<double> Hx = rounded<T>(t.Hx), Hy = rounded<T>(t.Hy), Pz = rounded<T>(t.Pz);
@@ -399,7 +431,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         o.gxt = pool.take(I.Qx * es); o.gxb = pool.take(I.Qx * es); o.gwy = pool.take(I.Qy * es);
         o.gwz = pool.take(2 * I.Qz * es); o.idz = pool.take(Nz * es);
         const size_t nf = (size_t)Nz * I.Q;
-        o.F1 = pool.take(nf * es); o.F2 = pool.take(nf * es);  // F0: below
+        o.F2 = pool.take(nf * es);  // F0, F1, L0: below
         o.rec = pool.take((size_t)Nz * kRecStride * es);
         const size_t maxch = 2 * ((I.Q / 2 + kThreads - 1) / kThreads);  // chunks at V = 1, the finest tiling
         o.partial = pool.take(maxch * Nz * kNMom * 8);
@@ -409,28 +441,39 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         o.res = pool.take(8); o.steps = pool.take(8); o.active = pool.take(4);  // status: below
         o.zcount = pool.take(4 * (size_t)std::max(1, Nz / 3)); o.icount = pool.take(4);
     }
-    // F0 of every instance back to back, each rounded up to 256 bytes so that every
-    // state starts aligned.  Where the rounding adds nothing (states of a multiple of
-    // 256 bytes, such as C2's 1 MiB), a whole-batch lbs_get_state / lbs_set_state is one
-    // copy.  Profiles and status words are packed.
-    size_t prof_base = 0, status_base = 0;
+    // The two state buffers F0 and F1 of every instance back to back (one region each),
+    // and likewise the FP32 rounding residuals L0, each state rounded up to 256 bytes so
+    // that every one starts aligned.  Where the rounding adds nothing (states of a
+    // multiple of 256 bytes, such as C2's 1 MiB), a whole-batch lbs_get_state /
+    // lbs_set_state is one copy per region.  Profiles, status words and the state
+    // selectors are packed.
+    size_t prof_base = 0, status_base = 0, cur_base = 0;
     {
-        size_t f0_total = 0, prof_total = 0;
+        size_t f0_total = 0, l0_total = 0, prof_total = 0;
         for (int b = 0; b < h->ninst; ++b) {
-            f0_total += ((size_t)h->ih[b].Nz * h->ih[b].Q * sizeof(T) + 255) & ~size_t(255);
+            const size_t nf = (size_t)h->ih[b].Nz * h->ih[b].Q;
+            f0_total += (nf * sizeof(T) + 255) & ~size_t(255);
+            if (h->fp32) l0_total += (nf * 2 + 255) & ~size_t(255);
             prof_total += 14 * (size_t)h->ih[b].Nz;
         }
-        const size_t f0_base = pool.take(f0_total);
+        const size_t f0_base = pool.take(f0_total), f1_base = pool.take(f0_total);
+        const size_t l0_base = h->fp32 ? pool.take(l0_total) : 0;
         prof_base = pool.take(prof_total * 8);
         status_base = pool.take(4 * (size_t)h->ninst);
+        cur_base = pool.take(4 * (size_t)h->ninst);
         h->prof_all_n = prof_total;
-        size_t fo = 0, po = 0;
+        size_t fo = 0, lo = 0, po = 0;
         for (int b = 0; b < h->ninst; ++b) {
+            const size_t nf = (size_t)h->ih[b].Nz * h->ih[b].Q;
             off[b].F0 = f0_base + fo;
-            fo += ((size_t)h->ih[b].Nz * h->ih[b].Q * sizeof(T) + 255) & ~size_t(255);
+            off[b].F1 = f1_base + fo;
+            fo += (nf * sizeof(T) + 255) & ~size_t(255);
+            off[b].L0 = l0_base + lo;
+            if (h->fp32) lo += (nf * 2 + 255) & ~size_t(255);
             off[b].prof = prof_base + 8 * po;
             po += 14 * (size_t)h->ih[b].Nz;
             off[b].status = status_base + 4 * (size_t)b;
+            off[b].cur = cur_base + 4 * (size_t)b;
         }
     }
     const size_t inst_off = pool.take(sizeof(InstDev) * h->ninst);
@@ -456,9 +499,8 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         put<T>(img, o.wx, t.wx); put<T>(img, o.wy, t.wy); put<T>(img, o.wz, t.wz);
         put<T>(img, o.gxt, t.gxt); put<T>(img, o.gxb, t.gxb); put<T>(img, o.gwy, t.gwy);
         put<T>(img, o.gwz, t.gwz); put<T>(img, o.idz, t.idz);
-        const size_t nf = (size_t)I.Nz * I.Q;
-        T* F0 = reinterpret_cast<T*>(img.data() + o.F0);
-        for (size_t e = 0; e < nf; ++e) F0[e] = T(1);  // rest Maxwellian n = 1, T = 1: f_k = w_k
+        (void)I;  // the state starts at the rest Maxwellian n = 1, T = 1 (f_k = w_k): d = 0,
+                  // the zeros of the image, with residual 0 and F0 holding the state
         *reinterpret_cast<int*>(img.data() + o.active) = 1;
         InstDev& D = h->idev[b];
         D.Hx = P + o.Hx;
@@ -470,6 +512,8 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         D.gwx_top = P + o.gxt; D.gwx_bot = P + o.gxb; D.gwy = P + o.gwy; D.gwz = P + o.gwz;
         D.inv_dz = P + o.idz;
         D.F0 = P + o.F0; D.F1 = P + o.F1; D.F2 = P + o.F2; D.rec = P + o.rec;
+        D.L0 = h->fp32 ? reinterpret_cast<unsigned short*>(P + o.L0) : nullptr;
+        D.cur = reinterpret_cast<int*>(P + o.cur);
         D.partial = reinterpret_cast<double*>(P + o.partial);
         D.flux_part = reinterpret_cast<double*>(P + o.flux);
         D.nw = reinterpret_cast<double*>(P + o.nw);
@@ -492,6 +536,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
     h->d_macro = reinterpret_cast<double*>(P + macro_off);
     h->prof_all = reinterpret_cast<double*>(P + prof_base);
     h->status_all = reinterpret_cast<int*>(P + status_base);
+    h->cur_all = reinterpret_cast<int*>(P + cur_base);
     h->ntiles = (int)tiles.size();
     CK(cudaMemcpyAsync(P, img.data(), pool.bytes, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -568,6 +613,11 @@ static lbs_status check_status(lbs_solver* h)
     std::vector<int> st(h->ninst);
     CK(cudaMemcpyAsync(st.data(), h->status_all, 4 * (size_t)h->ninst, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    for (int b = 0; b < h->ninst; ++b)
+        if (st[b] & STATUS_TIMEOUT)
+            return fail(LBS_ERR_TIMEOUT, "instance " + std::to_string(b) +
+                                             ": a stage CTA's bounded wait for its bulk copies ran out; that stage's "
+                                             "output is incomplete");
     for (int b = 0; b < h->ninst; ++b)
         if (st[b]) return fail(LBS_ERR_NONFINITE, "instance " + std::to_string(b) + " reached a non-finite or non-positive state");
     return LBS_OK;
@@ -1036,26 +1086,49 @@ lbs_status lbs_info(lbs_handle h, int inst, long* out, double* dt_out)
     return LBS_OK;
 }
 
+// The state of instances b0 .. b1-1 as the C ABI exposes it (see lbs_get_state): the
+// deviations d of every instance, concatenated, then (FP32) their rounding residuals,
+// concatenated.  Consecutive instances whose device buffers are adjacent go in one copy.
+// sel[b] picks F1 instead of F0 for instance b (get: where the state is; set: always F0).
+static lbs_status copy_state(lbs_solver* h, int b0, int b1, unsigned char* ext, bool to_ext, bool ext_host,
+                             const std::vector<int>& sel)
+{
+    const cudaMemcpyKind kind = to_ext ? (ext_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice)
+                                       : (ext_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice);
+    size_t off = 0;
+    for (int part = 0; part < (h->fp32 ? 2 : 1); ++part) {
+        const size_t es = part ? 2 : h->esize;
+        for (int b = b0; b < b1;) {
+            auto dev = [&](int e) -> unsigned char* {
+                if (part) return reinterpret_cast<unsigned char*>(h->idev[e].L0);
+                return static_cast<unsigned char*>(sel[e] ? h->idev[e].F1 : h->idev[e].F0);
+            };
+            unsigned char* d = dev(b);
+            size_t bytes = 0;
+            int e = b;
+            do {
+                bytes += (size_t)h->ih[e].Nz * h->ih[e].Q * es;
+                ++e;
+            } while (e < b1 && dev(e) == d + bytes);
+            if (to_ext) CK(cudaMemcpyAsync(ext + off, d, bytes, kind, h->stream));
+            else CK(cudaMemcpyAsync(d, ext + off, bytes, kind, h->stream));
+            off += bytes;
+            b = e;
+        }
+    }
+    return LBS_OK;
+}
+
 lbs_status lbs_get_state(lbs_handle h, int inst, void* dst, int to_host)
 {
     if (!h || inst < -1 || inst >= h->ninst) return fail(LBS_ERR_ARG, "invalid handle or instance index");
     if (!dst) return fail(LBS_ERR_ARG, "null destination");
     const int b0 = inst < 0 ? 0 : inst, b1 = inst < 0 ? h->ninst : inst + 1;
-    size_t off = 0;
-    for (int b = b0; b < b1;) {
-        // a run of instances whose states are adjacent on the device: one copy
-        unsigned char* d = static_cast<unsigned char*>(h->idev[b].F0);
-        size_t bytes = 0;
-        int e = b;
-        do {
-            bytes += (size_t)h->ih[e].Nz * h->ih[e].Q * h->esize;
-            ++e;
-        } while (e < b1 && static_cast<unsigned char*>(h->idev[e].F0) == d + bytes);
-        CK(cudaMemcpyAsync(static_cast<unsigned char*>(dst) + off, d, bytes,
-                           to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
-        off += bytes;
-        b = e;
-    }
+    std::vector<int> cur(h->ninst);
+    CK(cudaMemcpyAsync(cur.data(), h->cur_all, 4 * (size_t)h->ninst, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    lbs_status s = copy_state(h, b0, b1, static_cast<unsigned char*>(dst), true, to_host != 0, cur);
+    if (s != LBS_OK) return s;
     CK(cudaStreamSynchronize(h->stream));
     return LBS_OK;
 }
@@ -1065,24 +1138,33 @@ lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host)
     if (!h || inst < -1 || inst >= h->ninst) return fail(LBS_ERR_ARG, "invalid handle or instance index");
     if (!src) return fail(LBS_ERR_ARG, "null source");
     const int b0 = inst < 0 ? 0 : inst, b1 = inst < 0 ? h->ninst : inst + 1;
-    size_t off = 0;
-    for (int b = b0; b < b1;) {
-        // a run of instances whose states are adjacent on the device: one copy
-        unsigned char* d = static_cast<unsigned char*>(h->idev[b].F0);
-        size_t bytes = 0;
-        int e = b;
-        do {
-            bytes += (size_t)h->ih[e].Nz * h->ih[e].Q * h->esize;
-            ++e;
-        } while (e < b1 && static_cast<unsigned char*>(h->idev[e].F0) == d + bytes);
-        CK(cudaMemcpyAsync(d, static_cast<const unsigned char*>(src) + off, bytes,
-                           from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
-        off += bytes;
-        b = e;
-    }
-    lbs_status s = analyse(h);
+    // the state goes to F0, and F0 becomes the state buffer of those instances
+    std::vector<int> sel(h->ninst, 0);
+    lbs_status s = copy_state(h, b0, b1, static_cast<unsigned char*>(const_cast<void*>(src)), false,
+                              from_host != 0, sel);
+    if (s != LBS_OK) return s;
+    CK(cudaMemsetAsync(h->cur_all + b0, 0, 4 * (size_t)(b1 - b0), h->stream));
+    s = analyse(h);
     if (s != LBS_OK) return s;
     return check_status(h);
+}
+
+lbs_status lbs_set_wait_limit(lbs_handle h, unsigned spins)
+{
+    if (!h) return fail(LBS_ERR_ARG, "invalid handle");
+    CK(cudaStreamSynchronize(h->stream));
+    for (int b = 0; b < h->ninst; ++b) h->idev[b].wait_limit = spins;
+    CK(cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->ninst, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBS_OK;
+}
+
+lbs_status lbs_clear_status(lbs_handle h)
+{
+    if (!h) return fail(LBS_ERR_ARG, "invalid handle");
+    CK(cudaMemsetAsync(h->status_all, 0, 4 * (size_t)h->ninst, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBS_OK;
 }
 
 lbs_status lbs_init_from_profiles(lbs_handle h, int inst, const double* prof)

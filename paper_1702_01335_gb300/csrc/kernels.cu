@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(32) finalize_cells(const InstDev* __restrict__
     const int nblk = (I.Nz + 31) >> 5;
     if (blockIdx.x >= nblk || *I.active == 0) return;
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell < I.Nz) finalize_cell<T>(I, cell);
+    if (cell < I.Nz) finalize_cell<T>(I, cell, stage);
     // the instance's last block to finish (threadfence ticket) forms n_w and, after
     // stage 3, the residual; the counter is reset by its last user
     __threadfence();
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(128) finalize_cells_warp(const InstDev* __rest
     const int nblk = (I.Nz + 3) >> 2;
     if (blockIdx.x >= nblk || *I.active == 0) return;
     const int cell = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (cell < I.Nz) finalize_cell_warp<T>(I, cell, threadIdx.x & 31);
+    if (cell < I.Nz) finalize_cell_warp<T>(I, cell, threadIdx.x & 31, stage);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(I.icount, 1) == nblk - 1;
@@ -51,14 +51,16 @@ __global__ void __launch_bounds__(128) finalize_cells_warp(const InstDev* __rest
     finalize_instance(I, stage, red);
 }
 
-// ---- seed a cell from its record: f_k / w_k = n Gx Gy Gz (1 + S) ----------
+// ---- seed a cell from its record: d_k = f_k / w_k - 1 = R_SCALE Gx Gy Gz (1 + S) - 1,
+// formed from the factors' deviations as in the stage kernel; the rounding residual
+// (FP32 storage) starts at zero.  Written into whichever buffer holds the state.
 template <typename T>
 __global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ insts, int inst)
 {
     const InstDev& I = insts[inst];
     const int cell = blockIdx.x;
     const T* rc = static_cast<const T*>(I.rec) + (size_t)cell * kRecStride;
-    T* F = static_cast<T*>(I.F0) + (size_t)cell * I.Q;
+    T* F = static_cast<T*>(*I.cur ? I.F1 : I.F0) + (size_t)cell * I.Q;
     for (int k = threadIdx.x; k < I.Q; k += blockDim.x) {
         const int j = k % I.Qy, i = (k / I.Qy) % I.Qx, zm = k / I.QxQy;
         const int sg = zm >= I.Qz, m = zm - sg * I.Qz;
@@ -66,13 +68,16 @@ __global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ in
         for (int l = 0; l <= I.Nx; ++l) gx += rc[R_AX + l] * ld<T>(I.Hx, i * (I.Nx + 1) + l);
         for (int l = 0; l <= I.Ny; ++l) gy += rc[R_AY + l] * ld<T>(I.Hy, j * (I.Ny + 1) + l);
         for (int l = 0; l <= I.Nzq; ++l) gz += rc[(sg ? R_BM : R_BP) + l] * ld<T>(I.Pz, m * (I.Nzq + 1) + l);
+        gx = rc[R_SCALE1] + (T(1) + rc[R_SCALE1]) * gx;
         const T x = ld<T>(I.xi, m);
         const T ex = ld<T>(I.px, i) - rc[R_UX], ey = ld<T>(I.py, j) - rc[R_UY], ez = (sg ? -x : x) - rc[R_UZ];
         const T S = I.reduced ? rc[R_CS] * ((ex * ex + ez * ez) * rc[R_I5T] - (j ? T(0.4) : T(0.8))) *
                                     (ex * rc[R_QX] + ez * rc[R_QZ])
                               : rc[R_CS] * ((ex * ex + ey * ey + ez * ez) * rc[R_I5T] - T(1)) *
                     (ex * rc[R_QX] + ey * rc[R_QY] + ez * rc[R_QZ]);
-        F[k] = rc[R_SCALE] * gx * gy * gz * (T(1) + S);
+        const T a = gx + gy + gx * gy, b = a + gz + a * gz;
+        F[k] = b + S + b * S;
+        if (I.L0) I.L0[(size_t)cell * I.Q + k] = 0;
     }
 }
 
@@ -80,7 +85,7 @@ __global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ in
 size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int nhx, int nhy, int npz)
 {
     const int KC = kThreads * V;
-    return stage_smem(zn, KC, G, fp32 ? 4 : 8, fp32 ? 4 : 8, stage >= 2, nhx, nhy, npz).total;
+    return stage_smem(zn, KC, G, fp32 ? 4 : 8, 8, stage >= 2, nhx, nhy, npz).total;
 }
 
 template <typename T>

@@ -51,7 +51,6 @@ namespace lbs {
 template <typename T> struct Acc { typedef double type; };
 template <> struct Acc<float> { typedef float type; };
 
-constexpr uint32_t kSpinLimit = 1u << 26;  // bounded mbarrier waits (~seconds)
 
 // ---- PTX helpers: mbarrier and bulk global -> shared copies ------------------
 static __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -90,24 +89,29 @@ static __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t par
     return ok != 0;
 }
 
-// WENO-5 reconstruction of five upwind-ordered values (no advection factor).
-// The weights are scale free, so they are formed from r_q = sigma_q / max
-// sigma; an r_q below kTiny counts as vanishing and the weights of Table
-// (weno) apply (proportional to the ideal weights over the vanishing set).
+// WENO-5 reconstruction of five upwind-ordered values (no advection factor), as the
+// correction to the upwind cell's value v2: weno5 = v2 + weno5_corr.  The candidate
+// reconstructions are c_q = v2 + e_q / 6 with e_q made of the differences d_j = v_j - v2
+// (Eq. weno5_flux), and the smoothness indicators are written in the same differences
+// (Eq. weno_sigma), so the correction carries the precision of the differences, not of
+// v2, and the divergence of Eq. (flux) can be formed as a difference of cell values plus
+// a difference of corrections.  The weights (Eq. weno5_omega) are scale free, so they
+// are formed from r_q = sigma_q / max sigma; an r_q below kTiny counts as vanishing and
+// the weights of Table (weno) apply (proportional to the ideal weights over the
+// vanishing set).
 template <typename T>
-__device__ __forceinline__ T weno5(T v0, T v1, T v2, T v3, T v4)
+__device__ __forceinline__ T weno5_corr(T v0, T v1, T v2, T v3, T v4)
 {
     const T kTiny = sizeof(T) == 8 ? T(1e-150) : T(1e-18);
-    const T c1 = v0 * T(1.0 / 3.0) - v1 * T(7.0 / 6.0) + v2 * T(11.0 / 6.0);
-    const T c2 = -v1 * T(1.0 / 6.0) + v2 * T(5.0 / 6.0) + v3 * T(1.0 / 3.0);
-    const T c3 = v2 * T(1.0 / 3.0) + v3 * T(5.0 / 6.0) - v4 * T(1.0 / 6.0);
-    T a = v0 - T(2) * v1 + v2, b = v0 - T(4) * v1 + T(3) * v2;
+    const T d0 = v0 - v2, d1 = v1 - v2, d3 = v3 - v2, d4 = v4 - v2;
+    const T e1 = T(2) * d0 - T(7) * d1, e2 = T(2) * d3 - d1, e3 = T(5) * d3 - d4;
+    T a = d0 - T(2) * d1, b = d0 - T(4) * d1;
     const T s1 = T(13.0 / 12.0) * a * a + T(0.25) * b * b;
-    a = v1 - T(2) * v2 + v3;
-    b = v1 - v3;
+    a = d1 + d3;
+    b = d1 - d3;
     const T s2 = T(13.0 / 12.0) * a * a + T(0.25) * b * b;
-    a = v2 - T(2) * v3 + v4;
-    b = T(3) * v2 - T(4) * v3 + v4;
+    a = d4 - T(2) * d3;
+    b = d4 - T(4) * d3;
     const T s3 = T(13.0 / 12.0) * a * a + T(0.25) * b * b;
     const T smax = fmax(s1, fmax(s2, s3));
     T w1, w2, w3;
@@ -123,7 +127,7 @@ __device__ __forceinline__ T weno5(T v0, T v1, T v2, T v3, T v4)
             w1 = T(0.1) / (r1 * r1); w2 = T(0.6) / (r2 * r2); w3 = T(0.3) / (r3 * r3);
         }
     }
-    return (w1 * c1 + w2 * c2 + w3 * c3) / (w1 + w2 + w3);
+    return (w1 * e1 + w2 * e2 + w3 * e3) / (T(6) * (w1 + w2 + w3));
 }
 
 static __device__ __forceinline__ float rcp_approx(float x)
@@ -137,13 +141,9 @@ static __device__ __forceinline__ float rcp_approx(float x)
 // hardware reciprocals).  As sigma_q -> 0 the floor gives exactly the limits
 // of Table (weno); it changes nothing while sigma_q^2 > 1e-30, i.e. for
 // differences above the FP32 resolution of O(1) normalised populations.  The
-// candidate reconstructions are written as v2 plus corrections made of
-// differences (c_q = v2 + e_q / 6), so a constant stencil gives exactly its
-// value (the incoming ghosts at a wall: the flux is then exactly the wall
-// Maxwellian's, as Table weno implies) and the rounded weights only multiply the
-// small corrections.
+// rounded weights only multiply the small corrections e_q.
 template <>
-__device__ __forceinline__ float weno5<float>(float v0, float v1, float v2, float v3, float v4)
+__device__ __forceinline__ float weno5_corr<float>(float v0, float v1, float v2, float v3, float v4)
 {
     const float d0 = v0 - v2, d1 = v1 - v2, d3 = v3 - v2, d4 = v4 - v2;
     const float e1 = fmaf(2.f, d0, -7.f * d1);   // 6 (c1 - v2)
@@ -161,7 +161,13 @@ __device__ __forceinline__ float weno5<float>(float v0, float v1, float v2, floa
     const float w2 = 0.6f * rcp_approx(fmaf(s2, s2, 1e-37f));
     const float w3 = 0.3f * rcp_approx(fmaf(s3, s3, 1e-37f));
     const float inv = (1.f / 6.f) * rcp_approx(w1 + w2 + w3);
-    return fmaf(fmaf(w1, e1, fmaf(w2, e2, w3 * e3)), inv, v2);
+    return fmaf(w1, e1, fmaf(w2, e2, w3 * e3)) * inv;
+}
+
+template <typename T>
+__device__ __forceinline__ T weno5(T v0, T v1, T v2, T v3, T v4)
+{
+    return v2 + weno5_corr<T>(v0, v1, v2, v3, v4);
 }
 
 template <typename T>
@@ -238,20 +244,21 @@ __device__ __forceinline__ A reduce_scatter16(A (&v)[16], int lane)
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// shared-memory layout of a stage CTA (offsets in bytes): staged F_in rows,
-// F_l rows, the cell records and the Hermite basis tables (all by bulk copy),
-// the evaluated per-axis factors, 1/dz, and the per-warp moment sums.
+// shared-memory layout of a stage CTA (offsets in bytes): the staged rows of the
+// step's start state d (cells z0-3 .. z0+zn+2), the same rows of the stage input's
+// increment (stages 2 and 3), the cell records and the Hermite basis tables (all by
+// bulk copy), the evaluated per-axis factors, 1/dz, and the per-warp moment sums.
 struct StageSmem {
-    size_t fin, f0, rec, hx, hy, pz, g, idz, red, total;
+    size_t fin, dr, rec, hx, hy, pz, g, idz, red, total;
 };
 __host__ __device__ inline size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
-__host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize, int asize, bool withF0,
+__host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize, int asize, bool withD,
                                                 int nhx, int nhy, int npz)
 {
     StageSmem L;
     size_t o = 0;
     L.fin = o; o += (size_t)(zn + 6) * KC * esize;
-    L.f0 = o; o += withF0 ? (size_t)zn * KC * esize : 0;
+    L.dr = o; o += withD ? (size_t)(zn + 6) * KC * esize : 0;  // directly after fin (row offset (zn+6) KC)
     L.rec = o; o += (size_t)zn * kRecStride * esize;
     L.hx = o; o += pad16((size_t)nhx * esize);
     L.hy = o; o += pad16((size_t)nhy * esize);
@@ -261,6 +268,30 @@ __host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize
     L.red = o; o += (size_t)zn * (kThreads / 32) * 16 * asize;
     L.total = o;
     return L;
+}
+
+// ---- the FP32 state's rounding residual --------------------------------------
+// The state d is stored as hi (FP32) plus lo, |lo| <= ulp(hi) / 2, kept as a 16-bit
+// integer q = round(lo / ulp(hi) * 2^15).  The RK increment of a step near the steady
+// state is far below ulp(hi); added to hi alone it would be rounded away and the state
+// would stall at a distance of about eps_32 / (lambda dt) from the steady state
+// (lambda the decay rate of its slowest mode).  With lo the increment accumulates in
+// lo until it carries into hi; what is lost is below 2^-16 ulp(hi) per step.
+// ulp(hi) = 2^(E - 150) for the biased exponent E of a normal hi, so
+// lo / ulp(hi) * 2^15 = lo * 2^(165 - E), a power of two built in the exponent field
+// (valid for 38 <= E; a hi below 2^-89 keeps no residual).
+static __device__ __forceinline__ unsigned short lo_encode(float lo, float hi)
+{
+    const unsigned E = (__float_as_uint(hi) >> 23) & 0xffu;
+    const float s = __uint_as_float((292u - E) << 23);  // 2^(165 - E)
+    const int q = E >= 38u ? __float2int_rn(lo * s) : 0;
+    return static_cast<unsigned short>(static_cast<short>(q));
+}
+static __device__ __forceinline__ float lo_decode(unsigned short q, float hi)
+{
+    const unsigned E = (__float_as_uint(hi) >> 23) & 0xffu;
+    const float s = __uint_as_float((E - 38u) << 23);  // 2^(E - 165)
+    return E >= 39u ? float(static_cast<short>(q)) * s : 0.0f;
 }
 
 // ----------------------------------------------------------------------------
@@ -297,14 +328,19 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     // ulps of the same sign every step, which would let FP32 runs drift in mass.
     // The sums are sum_l c_l W_l with the stored coefficients c_l and the
     // weighted sums W_l of the stored basis tables (computed at set-up).
+    // The slots hold c_l - r_l, the coefficients minus those of the rest state r (n = 1,
+    // u = 0, T = 1): r = (1, 0, 0, ...) on x and y, (1, 1) on the reduced model's y
+    // (factors 1 and T), (1/2, 0, 0, ...) on each half range of z; sum_l r_l basis_l = 1 at
+    // every node.  The R_SCALE sums use the implied coefficients r_l + slot_l.
     double c[kMaxN + 1], cm[kMaxN + 1], s[3];
     full_coeffs(u0, Tc, I.Nx, c);
     s[0] = 0.0;
 #pragma unroll
     for (int l = 0; l <= kMaxN; ++l) {
-        const T v = l <= I.Nx ? T(c[l]) : T(0);
+        const double r = l == 0 ? 1.0 : 0.0;
+        const T v = l <= I.Nx ? T(c[l] - r) : T(0);
         rec[R_AX + l] = v;
-        if (l <= I.Nx) s[0] += double(v) * I.wsum[0][l];
+        if (l <= I.Nx) s[0] += (r + double(v)) * I.wsum[0][l];
     }
     if (I.reduced) {  // y factors of phi and chi: 1 and T (basis: the identity on j)
         c[0] = 1.0;
@@ -315,49 +351,23 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     s[1] = 0.0;
 #pragma unroll
     for (int l = 0; l <= kMaxN; ++l) {
-        const T v = l <= I.Ny ? T(c[l]) : T(0);
+        const double r = l == 0 || (l == 1 && I.reduced) ? 1.0 : 0.0;
+        const T v = l <= I.Ny ? T(c[l] - r) : T(0);
         rec[R_AY + l] = v;
-        if (l <= I.Ny) s[1] += double(v) * I.wsum[1][l];
+        if (l <= I.Ny) s[1] += (r + double(v)) * I.wsum[1][l];
     }
     half_coeffs_pm(u2, Tc, iT, I.Nzq, I.alpha, I.beta, c, cm);
     s[2] = 0.0;
 #pragma unroll
     for (int l = 0; l <= kMaxN; ++l) {
-        const T vp = l <= I.Nzq ? T(c[l]) : T(0), vm = l <= I.Nzq ? T(cm[l]) : T(0);
+        const double r = l == 0 ? 0.5 : 0.0;
+        const T vp = l <= I.Nzq ? T(c[l] - r) : T(0), vm = l <= I.Nzq ? T(cm[l] - r) : T(0);
         rec[R_BP + l] = vp;
         rec[R_BM + l] = vm;
-        if (l <= I.Nzq) s[2] += double(vp) * I.wsum[2][l] + double(vm) * I.wsum[3][l];
+        if (l <= I.Nzq) s[2] += (r + double(vp)) * I.wsum[2][l] + (r + double(vm)) * I.wsum[3][l];
     }
-    rec[R_SCALE] = T(nn / (s[0] * s[1] * s[2]));
+    rec[R_SCALE1] = T(nn / (s[0] * s[1] * s[2]) - 1.0);
     return !bad;
-}
-
-// Macroscopic state of a cell from its 13 raw moments (FP64): n, u, the central
-// second moments P_ab = sum p_a p_b f - n u_a u_b, T = tr P / (3n) and the heat flux
-// q_a = 1/2 sum |xi|^2 xi_a f with xi = p - u (Eq. qdef), expanded in raw moments.
-struct CellState {
-    double n, in, u[3], T, q[3], P[6];  // P: xx, yy, zz, xy, xz, yz
-};
-static __device__ __forceinline__ void cell_state(const double* mom, CellState& c)
-{
-    const double n = mom[0], in = 1.0 / n;
-    c.n = n;
-    c.in = in;
-    c.u[0] = mom[1] * in; c.u[1] = mom[2] * in; c.u[2] = mom[3] * in;
-    const double* u = c.u;
-    c.P[0] = mom[4] - n * u[0] * u[0]; c.P[1] = mom[5] - n * u[1] * u[1];
-    c.P[2] = mom[6] - n * u[2] * u[2]; c.P[3] = mom[7] - n * u[0] * u[1];
-    c.P[4] = mom[8] - n * u[0] * u[2]; c.P[5] = mom[9] - n * u[1] * u[2];
-    c.T = (c.P[0] + c.P[1] + c.P[2]) * (1.0 / 3.0) * in;
-    const double M2[3][3] = {{mom[4], mom[7], mom[8]}, {mom[7], mom[5], mom[9]}, {mom[8], mom[9], mom[6]}};
-    const double tr = mom[4] + mom[5] + mom[6];
-    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const double um = u[0] * mom[1] + u[1] * mom[2] + u[2] * mom[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double uM2 = u[0] * M2[0][a] + u[1] * M2[1][a] + u[2] * M2[2][a];
-        c.q[a] = 0.5 * (mom[10 + a] - u[a] * tr - 2.0 * uM2 + 2.0 * u[a] * um + uu * mom[1 + a] - uu * u[a] * n);
-    }
 }
 
 // profiles [14][Nz] and W = (n, u_x, T) of a cell; false if any value is not finite
@@ -378,14 +388,39 @@ static __device__ __forceinline__ bool store_cell(const InstDev& I, int cell, co
     return !bad;
 }
 
+// The velocity the stage kernel took its moments about: the cell record's u after
+// stage 3 (the stage record is still in place when the finalisation reads it), else 0.
+template <typename T>
+__device__ __forceinline__ void moment_origin(const InstDev& I, int cell, int stage, double* ur)
+{
+    const T* rc = static_cast<const T*>(I.rec) + (size_t)cell * kRecStride;
+    ur[0] = stage == 3 ? double(rc[R_UX]) : 0.0;
+    ur[1] = stage == 3 ? double(rc[R_UY]) : 0.0;
+    ur[2] = stage == 3 ? double(rc[R_UZ]) : 0.0;
+}
+
+// The macroscopic state from the partials' moments about ur (sums over the deviations
+// d) and the rest state's moments, re-expressed about ur: n, u = ur + the mean of
+// p - ur, P, T and q.
+static __device__ __forceinline__ void state_about(const InstDev& I, double* mom, const double* ur, CellState& st)
+{
+    double rest[kNMom];
+    shift_moments(I.mrest, ur, rest);
+#pragma unroll
+    for (int a = 0; a < kNMom; ++a) mom[a] += rest[a];
+    cell_state(mom, st);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) st.u[a] += ur[a];
+}
+
 // One cell (one thread): FP64 sum of the per-chunk moment partials (written by
 // other CTAs of this launch, hence read past L1), the macroscopic state, the
 // profiles, W for the residual, and the cell record of the next stage.
 template <typename T>
-__device__ void finalize_cell(const InstDev& I, int cell)
+__device__ void finalize_cell(const InstDev& I, int cell, int stage)
 {
     const int Nz = I.Nz, nch = I.nchunks;
-    double mom[kNMom];
+    double mom[kNMom];  // the partials: moments of the deviations about ur
     for (int a = 0; a < kNMom; ++a) mom[a] = 0.0;
     // chunks in order, four at a time with every load issued before the adds (the
     // partials come from L2: one round trip per four chunks instead of per chunk)
@@ -402,11 +437,13 @@ __device__ void finalize_cell(const InstDev& I, int cell)
             for (int a = 0; a < kNMom; ++a)
                 if (c + j < nch) mom[a] += p[j][a];
     }
+    double ur[3];
+    moment_origin<T>(I, cell, stage, ur);
     CellState st;
-    cell_state(mom, st);
+    state_about(I, mom, ur, st);
     bool bad = !store_cell(I, cell, st);
     bad |= !write_record<T>(I, cell, st.n, st.in, st.u, st.T, st.q);
-    if (bad) atomicOr(I.status, 1);
+    if (bad) atomicOr(I.status, STATUS_NONFINITE);
 }
 
 // ---- one cell per warp: the same record with its FP64 work spread over the lanes.
@@ -455,9 +492,10 @@ __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& s
         if (l == k) ck = c[l];
     double sxy = 0.0;  // this lane's term of sum_l c_l W_l (the R_SCALE sums, as in write_record)
     if (k <= kMaxN) {
-        const T v = k <= Nh ? T(ck) : T(0);
+        const double r = k == 0 || (k == 1 && h && I.reduced) ? 1.0 : 0.0;  // rest coefficients
+        const T v = k <= Nh ? T(ck - r) : T(0);
         rec[(h ? R_AY : R_AX) + k] = v;
-        if (k <= Nh) sxy = double(v) * I.wsum[h][k];
+        if (k <= Nh) sxy = (r + double(v)) * I.wsum[h][k];
     }
     // z: half h = 0 the p_z > 0 range (drift u2), h = 1 the p_z < 0 range written in
     // xi = -p_z >= 0 (drift -u2).  Both share g(0) and one erfc (erfc(x) + erfc(-x) = 2).
@@ -499,11 +537,12 @@ __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& s
     if (k == 0) {
 #pragma unroll
         for (int l = 0; l <= kMaxN; ++l) {
-            const T v = l <= K ? T(b[l]) : T(0);
+            const double r = l == 0 ? 0.5 : 0.0;
+            const T v = l <= K ? T(b[l] - r) : T(0);
             rec[(h ? R_BM : R_BP) + l] = v;
             if (l <= K) {
-                if (l & 1) sz1 += double(v) * I.wsum[2 + h][l];
-                else sz += double(v) * I.wsum[2 + h][l];
+                if (l & 1) sz1 += (r + double(v)) * I.wsum[2 + h][l];
+                else sz += (r + double(v)) * I.wsum[2 + h][l];
             }
         }
         sz += sz1;
@@ -513,12 +552,12 @@ __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& s
     for (int o = 8; o > 0; o >>= 1) sxy += __shfl_xor_sync(0xffffffffu, sxy, o, 16);
     const double sx = __shfl_sync(0xffffffffu, sxy, 0), sy = __shfl_sync(0xffffffffu, sxy, 16);
     const double s2 = __shfl_sync(0xffffffffu, sz, 0) + __shfl_sync(0xffffffffu, sz, 16);
-    if (lane == 0) rec[R_SCALE] = T(nn / (sx * sy * s2));
+    if (lane == 0) rec[R_SCALE1] = T(nn / (sx * sy * s2) - 1.0);
     return !bad;
 }
 
 template <typename T>
-__device__ void finalize_cell_warp(const InstDev& I, int cell, int lane)
+__device__ void finalize_cell_warp(const InstDev& I, int cell, int lane, int stage)
 {
     const int Nz = I.Nz, nch = I.nchunks, am = lane & 15, h = lane >> 4;
     // moment am: lanes am and 16 + am sum the even and the odd chunks (loads four
@@ -538,12 +577,14 @@ __device__ void finalize_cell_warp(const InstDev& I, int cell, int lane)
     double mom[kNMom];
 #pragma unroll
     for (int a = 0; a < kNMom; ++a) mom[a] = __shfl_sync(0xffffffffu, part, a);
+    double ur[3];
+    moment_origin<T>(I, cell, stage, ur);
     CellState st;
-    cell_state(mom, st);
+    state_about(I, mom, ur, st);
     bool bad = false;
     if (lane == 0) bad = !store_cell(I, cell, st);
     bad |= !write_record_warp<T>(I, cell, st, lane);
-    if (bad && lane == 0) atomicOr(I.status, 1);
+    if (bad && lane == 0) atomicOr(I.status, STATUS_NONFINITE);
 }
 
 // One instance (whole CTA): wall densities n_w from the outgoing wall fluxes
@@ -576,10 +617,10 @@ static __device__ void finalize_instance(const InstDev& I, int stage, double* re
         v[0] = w[0];
         v[1] = w[1];
     }
-    if (t == 0) {
-        I.nw[0] = -v[0] / I.Dbot;
-        I.nw[1] = -v[1] / I.Dtop;
-        if (!isfinite(I.nw[0]) || !isfinite(I.nw[1])) atomicOr(I.status, 1);
+    if (t == 0) {  // the partials sum w p_z over the deviations: add the rest state's flux
+        I.nw[0] = -(I.frest_bot + v[0]) / I.Dbot;
+        I.nw[1] = -(I.frest_top + v[1]) / I.Dtop;
+        if (!isfinite(I.nw[0]) || !isfinite(I.nw[1])) atomicOr(I.status, STATUS_NONFINITE);
     }
     if (stage == 3) {
         double R = 0.0;
@@ -590,7 +631,8 @@ static __device__ void finalize_instance(const InstDev& I, int stage, double* re
         if (t == 0) {
             *I.res = R;
             *I.steps += 1;
-            if (!(R == R)) atomicOr(I.status, 1);
+            *I.cur ^= 1;  // the new state was written over the stage-1 increment
+            if (!(R == R)) atomicOr(I.status, STATUS_NONFINITE);
             if (I.tol > 0.0 && R < I.tol) *I.active = 0;
         }
     } else if (stage == 0) {
@@ -607,7 +649,8 @@ __global__ void records_from_macro(const InstDev* __restrict__ insts, int inst, 
     if (cell >= Nz) return;
     const double u[3] = {macro[Nz + cell], macro[2 * Nz + cell], macro[3 * Nz + cell]};
     const double q[3] = {macro[5 * Nz + cell], macro[6 * Nz + cell], macro[7 * Nz + cell]};
-    if (!write_record<T>(I, cell, macro[cell], 1.0 / macro[cell], u, macro[4 * Nz + cell], q)) atomicOr(I.status, 1);
+    if (!write_record<T>(I, cell, macro[cell], 1.0 / macro[cell], u, macro[4 * Nz + cell], q))
+        atomicOr(I.status, STATUS_NONFINITE);
 }
 
 // The instance descriptor copied into shared memory by the whole block at once: its
@@ -639,6 +682,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<V>::value)
 stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, int fuse)
 {
     typedef typename Acc<T>::type A;
+    constexpr bool kLo = sizeof(T) == 4;  // FP32 storage keeps the rounding residual of d
+    constexpr bool kD = STAGE >= 2;       // the stage input is d + an increment
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ double wall_red[kRedSlots];
@@ -646,6 +691,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     const Tile tile = tiles[blockIdx.x];
     const InstDev& I = stage_descriptor(insts + tile.inst, &sI);
     if (*I.active == 0) return;
+    const int cur = *I.cur;  // which of F0 / F1 holds the step's start state
 
     const int Nz = I.Nz, Q = I.Q, Qx = I.Qx, Qy = I.Qy, Qz = I.Qz, QxQy = I.QxQy;
     const int z0 = tile.z0, zn = tile.zn;            // cells z0 .. z0+zn-1 (0-based)
@@ -657,23 +703,28 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     const int zm_lo = k0 / QxQy, zm_hi = (kend - 1) / QxQy, nzm = zm_hi - zm_lo + 1;
     const int G = Qx + Qy + nzm;                     // per-cell factors held in smem
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr bool kF0 = STAGE >= 2;
 
     const int nhx = Qx * (I.Nx + 1), nhy = Qy * (I.Ny + 1), npz = Qz * (I.Nzq + 1);
-    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(A), kF0, nhx, nhy, npz);
-    T* Fs = reinterpret_cast<T*>(smem_raw + L.fin);   // rows: cells z0-3 .. z0+zn+2
-    T* F0s = reinterpret_cast<T*>(smem_raw + L.f0);   // rows: cells z0 .. z0+zn-1
+    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(double), kD, nhx, nhy, npz);
+    T* Fs = reinterpret_cast<T*>(smem_raw + L.fin);   // d rows: cells z0-3 .. z0+zn+2
+    T* Ds = reinterpret_cast<T*>(smem_raw + L.dr);    // increment rows, same cells (stages 2, 3)
     T* recs = reinterpret_cast<T*>(smem_raw + L.rec); // records of cells z0 .. z0+zn-1
     T* hxs = reinterpret_cast<T*>(smem_raw + L.hx);
     T* hys = reinterpret_cast<T*>(smem_raw + L.hy);
     T* pzs = reinterpret_cast<T*>(smem_raw + L.pz);
     T* gsm = reinterpret_cast<T*>(smem_raw + L.g);
     T* idzs = reinterpret_cast<T*>(smem_raw + L.idz);
-    A* red = reinterpret_cast<A*>(smem_raw + L.red);
+    double* red = reinterpret_cast<double*>(smem_raw + L.red);  // per-warp moment sums, summed in FP64
+    const long doff = (long)(zn + 6) * KC;            // Ds = Fs + doff
 
-    const T* Fin = static_cast<const T*>(STAGE <= 1 ? I.F0 : STAGE == 2 ? I.F1 : I.F2);
-    T* Fout = static_cast<T*>(STAGE == 1 ? I.F1 : STAGE == 2 ? I.F2 : I.F0);
-    const T* F0g = static_cast<const T*>(I.F0);
+    // Buffers (Eq. rk3 in increment form, F_l the step's start state d):
+    //   stage 1: d1 = dt L[F_l]                  -> the other of F0 / F1
+    //   stage 2: d2 = (d1 + dt L[F_l + d1]) / 4  -> F2
+    //   stage 3: F_l + 2/3 (d2 + dt L[F_l + d2]) -> the other of F0 / F1 (over d1)
+    const T* Hg = static_cast<const T*>(cur ? I.F1 : I.F0);
+    T* Og = static_cast<T*>(cur ? I.F0 : I.F1);
+    const T* Dg = STAGE == 2 ? Og : static_cast<const T*>(I.F2);
+    T* Fout = STAGE == 2 ? static_cast<T*>(I.F2) : Og;
     const int s_lo = max(0, z0 - 3), s_hi = min(Nz - 1, z0 + zn + 2);
 
     // ---- 1. stage the input rows, the cell records and the basis tables
@@ -688,15 +739,14 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         __syncthreads();
         if (tid == 0) {
             const uint32_t bytes = kn * sizeof(T);
-            uint32_t total = bytes * ((s_hi - s_lo + 1) + (kF0 ? zn : 0));
+            uint32_t total = bytes * (s_hi - s_lo + 1) * (kD ? 2 : 1);
             if (STAGE > 0)
                 total += rec_bytes + pad16(nhx * sizeof(T)) + pad16(nhy * sizeof(T)) + pad16(npz * sizeof(T));
             mbar_expect_tx(&bar, total);
-            for (int s = s_lo; s <= s_hi; ++s)
-                bulk_g2s(Fs + (size_t)(s - z0 + 3) * KC, Fin + (size_t)s * Q + k0, bytes, &bar);
-            if (kF0)
-                for (int c = 0; c < zn; ++c)
-                    bulk_g2s(F0s + (size_t)c * KC, F0g + (size_t)(z0 + c) * Q + k0, bytes, &bar);
+            for (int s = s_lo; s <= s_hi; ++s) {
+                bulk_g2s(Fs + (size_t)(s - z0 + 3) * KC, Hg + (size_t)s * Q + k0, bytes, &bar);
+                if (kD) bulk_g2s(Ds + (size_t)(s - z0 + 3) * KC, Dg + (size_t)s * Q + k0, bytes, &bar);
+            }
             if (STAGE > 0) {
                 bulk_g2s(recs, Rg, rec_bytes, &bar);
                 bulk_g2s(hxs, I.Hx, pad16(nhx * sizeof(T)), &bar);  // tables are padded to 16 bytes
@@ -706,10 +756,10 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         }
     } else {
         for (int s = s_lo; s <= s_hi; ++s)
-            for (int kl = tid; kl < kn; kl += kThreads) Fs[(size_t)(s - z0 + 3) * KC + kl] = Fin[(size_t)s * Q + k0 + kl];
-        if (kF0)
-            for (int c = 0; c < zn; ++c)
-                for (int kl = tid; kl < kn; kl += kThreads) F0s[(size_t)c * KC + kl] = F0g[(size_t)(z0 + c) * Q + k0 + kl];
+            for (int kl = tid; kl < kn; kl += kThreads) {
+                Fs[(size_t)(s - z0 + 3) * KC + kl] = Hg[(size_t)s * Q + k0 + kl];
+                if (kD) Ds[(size_t)(s - z0 + 3) * KC + kl] = Dg[(size_t)s * Q + k0 + kl];
+            }
         if (STAGE > 0) {
             for (int e = tid; e < zn * kRecStride; e += kThreads) recs[e] = Rg[e];
             for (int e = tid; e < nhx; e += kThreads) hxs[e] = ld<T>(I.Hx, e);
@@ -761,25 +811,29 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         }
     }
 
-    // ---- 3. wait for the copies (bounded); a CTA whose copies never land flags
-    //         the instance and leaves once they are no longer in flight
+    // ---- 3. wait for the copies (bounded).  A CTA whose wait runs out flags the
+    //         instance (STATUS_TIMEOUT), then waits a further bounded time for its copies
+    //         in flight to land before it leaves, so that none writes shared memory after
+    //         the CTA is gone; if that wait runs out too the CTA leaves regardless.
     int late = 0;
     if (I.bulk) {
-        uint32_t spins = 0;
-        while (!mbar_try_wait(&bar, 0)) {
-            if (++spins > kSpinLimit) { late = 1; break; }
+        for (uint32_t spins = 0;; ++spins) {
+            if (spins >= I.wait_limit) { late = 1; break; }
+            if (mbar_try_wait(&bar, 0)) break;
         }
     }
     if (__syncthreads_or(late)) {
-        if (tid == 0) atomicOr(I.status, 2);
+        if (tid == 0) atomicOr(I.status, STATUS_TIMEOUT);
         uint32_t spins = 0;
-        while (!mbar_try_wait(&bar, 0) && ++spins < kSpinLimit) {
+        while (!mbar_try_wait(&bar, 0) && ++spins < kDrainLimit) {
         }
         return;
     }
 
-    // ---- 4a. per-cell factors of the truncated Hermite equilibrium (Sec. III)
-    //          from the staged records: n*Gx[i], Gy[j], Gz[zm] for this chunk's zm
+    // ---- 4a. per-cell factors of the truncated Hermite equilibrium (Sec. III) from
+    //          the staged records, as deviations from 1: dx[i] = R_SCALE Gx[i] - 1,
+    //          dy[j] = Gy[j] - 1, dz[zm] = Gz[zm] - 1 for this chunk's zm (the records
+    //          hold the coefficients minus those of the rest state)
     if (STAGE > 0) {
         for (int e = tid; e < zn * G; e += kThreads) {
             const int c = e / G, r = e - c * G;
@@ -788,7 +842,8 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             if (r < Qx) {
                 const T* h = hxs + r * (I.Nx + 1);
                 for (int l = 0; l <= I.Nx; ++l) g += rc[R_AX + l] * h[l];
-                g *= rc[R_SCALE];
+                const T s1 = rc[R_SCALE1];
+                g = s1 + (T(1) + s1) * g;
             } else if (r < Qx + Qy) {
                 const T* h = hys + (r - Qx) * (I.Ny + 1);
                 for (int l = 0; l <= I.Ny; ++l) g += rc[R_AY + l] * h[l];
@@ -802,8 +857,12 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         }
     }
 
-    // ---- 4b. ghost rows (each thread fills only its own columns)
+    // ---- 4b. ghost rows (each thread fills only its own columns).  A ghost row holds
+    //          the whole stage-input value d (+ increment) in Fs and zero in Ds.
     const int rbase = 3 - z0;  // smem row of cell s is s + rbase
+    auto rowval = [&](int row, int col) -> T {
+        return kD ? Fs[(size_t)row * KC + col] + Ds[(size_t)row * KC + col] : Fs[(size_t)row * KC + col];
+    };
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         if (!ok[v]) continue;  // columns past the chunk end hold no data
@@ -815,15 +874,18 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             const int zm = zz[v] + (sgc ? -Qz : Qz);
             const int kmir = (zm * Qx + (Qx - 1 - ii[v])) * Qy + jj[v];
             for (int s = 0; s < 3; ++s)
-                if (-1 - s + rbase >= 0) col[(size_t)(-1 - s + rbase) * KC] = Fin[(size_t)s * Q + kmir];
+                if (-1 - s + rbase >= 0)
+                    col[(size_t)(-1 - s + rbase) * KC] =
+                        kD ? Hg[(size_t)s * Q + kmir] + Dg[(size_t)s * Q + kmir] : Hg[(size_t)s * Q + kmir];
         } else if (z0 < 3) {
-            if (!sgc) {  // incoming at the bottom wall: n_w times the wall equilibrium
-                const T g = T(I.nw[0]) * ld<T>(I.gwx_bot, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
+            if (!sgc) {  // incoming at the bottom wall: n_w times the wall equilibrium, minus 1
+                const T ax = ld<T>(I.gwx_bot, ii[v]), ay = ld<T>(I.gwy, jj[v]), az = ld<T>(I.gwz, zz[v]);
+                const T a = ax + ay + ax * ay, b = a + az + a * az;
+                const T g = T(I.nw[0] - 1.0) + T(I.nw[0]) * b;
                 for (int s = -3; s <= -1; ++s)
                     if (s + rbase >= 0) col[(size_t)(s + rbase) * KC] = g;
             } else {      // outgoing: quadratic extrapolation (Appendix)
-                const T f1 = col[(size_t)(0 + rbase) * KC], f2 = col[(size_t)(1 + rbase) * KC],
-                        f3 = col[(size_t)(2 + rbase) * KC];
+                const T f1 = rowval(0 + rbase, kl[v]), f2 = rowval(1 + rbase, kl[v]), f3 = rowval(2 + rbase, kl[v]);
                 const T g0 = T(I.ext_bot[0][0]) * f1 + T(I.ext_bot[0][1]) * f2 + T(I.ext_bot[0][2]) * f3;
                 const T g1 = T(I.ext_bot[1][0]) * g0 + T(I.ext_bot[1][1]) * f1 + T(I.ext_bot[1][2]) * f2;
                 if (-1 + rbase >= 0) col[(size_t)(-1 + rbase) * KC] = g0;
@@ -831,21 +893,29 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 if (-3 + rbase >= 0) col[(size_t)(-3 + rbase) * KC] = g1;  // never read for p_z < 0
             }
         }
+        if (kD && z0 < 3)
+            for (int s = -3; s <= -1; ++s)
+                if (s + rbase >= 0) col[doff + (size_t)(s + rbase) * KC] = T(0);
         if (z0 + zn + 3 > Nz) {
             const int smax = z0 + zn + 2;
             if (sgc) {
-                const T g = T(I.nw[1]) * ld<T>(I.gwx_top, ii[v]) * ld<T>(I.gwy, jj[v]) * ld<T>(I.gwz, zz[v]);
+                const T ax = ld<T>(I.gwx_top, ii[v]), ay = ld<T>(I.gwy, jj[v]), az = ld<T>(I.gwz, zz[v]);
+                const T a = ax + ay + ax * ay, b = a + az + a * az;
+                const T g = T(I.nw[1] - 1.0) + T(I.nw[1]) * b;
                 for (int s = Nz; s <= Nz + 2; ++s)
                     if (s <= smax) col[(size_t)(s + rbase) * KC] = g;
             } else {
-                const T f1 = col[(size_t)(Nz - 1 + rbase) * KC], f2 = col[(size_t)(Nz - 2 + rbase) * KC],
-                        f3 = col[(size_t)(Nz - 3 + rbase) * KC];
+                const T f1 = rowval(Nz - 1 + rbase, kl[v]), f2 = rowval(Nz - 2 + rbase, kl[v]),
+                        f3 = rowval(Nz - 3 + rbase, kl[v]);
                 const T g0 = T(I.ext_top[0][0]) * f1 + T(I.ext_top[0][1]) * f2 + T(I.ext_top[0][2]) * f3;
                 const T g1 = T(I.ext_top[1][0]) * g0 + T(I.ext_top[1][1]) * f1 + T(I.ext_top[1][2]) * f2;
                 if (Nz <= smax) col[(size_t)(Nz + rbase) * KC] = g0;
                 if (Nz + 1 <= smax) col[(size_t)(Nz + 1 + rbase) * KC] = g1;
                 if (Nz + 2 <= smax) col[(size_t)(Nz + 2 + rbase) * KC] = g1;  // never read for p_z > 0
             }
+            if (kD)
+                for (int s = Nz; s <= Nz + 2; ++s)
+                    if (s <= smax) col[doff + (size_t)(s + rbase) * KC] = T(0);
         }
     }
 
@@ -859,22 +929,29 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     // divergence of Eq. (flux) is (ahead - behind) / dz for the signed p_z either way.
     const long rstep = sgc ? -(long)KC : (long)KC;
     const T* rp = Fs + (sgc ? (size_t)(zn + 5) * KC : 0);  // window row d at step c: rp + (c + d) rstep
-    T w[V][6], flm[V];
+    // cm: the WENO correction of the interface behind (its flux is |p_z| (w2 + cm))
+    T w[V][6], cm[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
 #pragma unroll
-        for (int d = 0; d < 6; ++d) w[v][d] = rp[d * rstep + kl[v]];
-        flm[v] = apz[v] * weno5<T>(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4]);
+        for (int d = 0; d < 6; ++d) {
+            const T* q = rp + d * rstep + kl[v];
+            w[v][d] = kD ? q[0] + q[doff] : q[0];
+        }
+        cm[v] = weno5_corr<T>(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4]);
     }
     const T dt = T(I.dt);
     const long ostep = sgc ? -(long)Q : (long)Q;
-    T* outp = Fout + (size_t)(sgc ? z0 + zn - 1 : z0) * Q + k0;
+    const size_t orow0 = (size_t)(sgc ? z0 + zn - 1 : z0) * Q + k0;  // global offset of the first cell
+    T* outp = Fout + orow0;
+    unsigned short* lop = kLo && STAGE == 3 ? I.L0 + orow0 : nullptr;
 #pragma unroll 1  // unrolling the z-march only adds instruction-cache misses
     for (int c = 0; c < zn; ++c) {
         const int cc = sgc ? zn - 1 - c : c;  // the cell within the tile
         const T* sc = recs + (size_t)cc * kRecStride;
         const T* gc = gsm + cc * G;
         const T* rn = rp + (c + 6) * rstep;
+        const T* own = Fs + (size_t)(cc + 3) * KC;  // the cell's row of d
         T ux = 0, uy = 0, uz = 0, i5T = 0, qx = 0, qy = 0, qz = 0, itau = 0, cS = 0, idz = 0;
         if (STAGE > 0) {
             ux = sc[R_UX]; uy = sc[R_UY]; uz = sc[R_UZ];
@@ -886,67 +963,118 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         for (int a = 0; a < 16; ++a) acc[a] = A(0);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const T wn = rn[kl[v]];
-            T out = w[v][3];
+            unsigned short lq = 0;
+            if (kLo && STAGE == 3 && ok[v]) lq = lop[kl[v]];
+            const T wn = kD ? rn[kl[v]] + rn[doff + kl[v]] : rn[kl[v]];
+            T out = w[v][3];  // the value whose moments are taken
+            T ex = 0, ey = 0, ez = 0, xi2 = 0;  // xi = p - u of the cell's record
             if (STAGE > 0) {
-                const T flp = apz[v] * weno5<T>(w[v][1], w[v][2], w[v][3], w[v][4], w[v][5]);
+                const T cp = weno5_corr<T>(w[v][1], w[v][2], w[v][3], w[v][4], w[v][5]);
                 const T f = w[v][3];
                 // Shakhov target n Gx Gy Gz (1 + S), S = cS (xi^2/(5T) - 1) xi.q; in the
                 // phi / chi model (Eq. sred_def) S = cS ((xi_x^2 + xi_z^2)/(5T) - 4/5 or 2/5) xi.q
                 // with u_y = q_y = 0, and Gy = 1 (phi) or T (chi) from the record
                 T S;
+                ex = px[v] - ux;
+                ez = pz[v] - uz;
                 if (RED) {
-                    const T ex = px[v] - ux, ez = pz[v] - uz;
-                    S = cS * ((ex * ex + ez * ez) * i5T + py[v]) * (ex * qx + ez * qz);
+                    xi2 = ex * ex + ez * ez;
+                    S = cS * (xi2 * i5T + py[v]) * (ex * qx + ez * qz);
                 } else {
-                    const T ex = px[v] - ux, ey = py[v] - uy, ez = pz[v] - uz;
-                    const T xi2 = ex * ex + ey * ey + ez * ez;
+                    ey = py[v] - uy;
+                    xi2 = ex * ex + ey * ey + ez * ez;
                     const T xq = ex * qx + ey * qy + ez * qz;
                     S = cS * (xi2 * i5T - T(1)) * xq;
                 }
-                const T geq = gc[ii[v]] * gc[Qx + jj[v]] * gc[Qx + Qy + zz[v] - zm_lo];
-                // the advection and relaxation increments nearly cancel near a steady
-                // state: combine them first, then add to f once
-                const T Lv = -(flp - flm[v]) * idz - (f - geq * (T(1) + S)) * itau;
-                const T f1 = f + dt * Lv;
-                // Shu-Osher combine written as F_l + b (f1 - F_l): identical to
-                // (1 - b) F_l + b f1, but a rounded b only scales the increment
-                // (with b = 2/3 the two rounded weights would not add up to 1 and
-                // would scale the whole state every step)
+                // the target's deviation from 1: (1 + dx)(1 + dy)(1 + dz)(1 + S) - 1
+                const T dx = gc[ii[v]], dy = gc[Qx + jj[v]], dz = gc[Qx + Qy + zz[v] - zm_lo];
+                const T a = dx + dy + dx * dy, b = a + dz + a * dz, tgt = b + S + b * S;
+                // Eq. (flux): (|p_z| (w3 + cp) - |p_z| (w2 + cm)) / dz, formed from the
+                // difference of the two upwind cells and of the two corrections, so that
+                // its rounding is relative to the divergence rather than to d.  The
+                // advection and relaxation increments nearly cancel near a steady state:
+                // combine them first.
+                const T Lv = -apz[v] * ((w[v][3] - w[v][2]) + (cp - cm[v])) * idz - (f - tgt) * itau;
+                T st;  // the value stored
                 if (STAGE == 1) {
-                    out = f1;
+                    st = dt * Lv;
+                    out = f + st;
+                } else if (STAGE == 2) {
+                    st = T(0.25) * (own[doff + kl[v]] + dt * Lv);
+                    out = own[kl[v]] + st;
                 } else {
-                    const T fl = F0s[(size_t)cc * KC + kl[v]];
-                    out = fl + (STAGE == 2 ? T(0.25) : T(2.0 / 3.0)) * (f1 - fl);
+                    // Shu-Osher combine in increment form: F_l + 2/3 (d2 + dt L), added to the
+                    // state with its rounding residual carried (FP32)
+                    const T inc = T(2.0 / 3.0) * (own[doff + kl[v]] + dt * Lv);
+                    const T h = own[kl[v]];
+                    if constexpr (kLo) {
+                        const T t = lo_decode(lq, h) + inc;
+                        const T h2 = h + t;
+                        const T lo2 = t - (h2 - h);
+                        if (ok[v]) lop[kl[v]] = lo_encode(lo2, h2);
+                        st = h2;
+                    } else {
+                        st = h + inc;
+                    }
+                    out = st;
                 }
-                if (ok[v]) outp[kl[v]] = out;
-                flm[v] = flp;
+                if (ok[v]) outp[kl[v]] = st;
+                cm[v] = cp;
             }
 #pragma unroll
             for (int d = 0; d < 5; ++d) w[v][d] = w[v][d + 1];
             w[v][5] = wn;
             const A o = ok[v] ? A(out) : A(0);  // columns past the chunk hold no data
+            if (STAGE == 3) {
+                // the profiles' moments: of psi(p - u_r) about the velocity u_r of the cell's
+                // record, so that the third moments are close to the heat flux itself
+                // instead of its sum with terms of size u |p|^2 that cancel it (160-fold in
+                // config C1); the finalisation adds the rest state's moments about u_r
+                // w of the velocity: wpsi[v][0] for phi and the full set, wpsi[v][5] for chi
+                // (whose other weighted moments are zero)
+                const A ow = o * (RED ? wpsi[v][0] + wpsi[v][5] : wpsi[v][0]);
+                if (RED) {
+                    const A owc = jj[v] ? ow : A(0), owp = ow - owc;  // chi, phi
+                    const A opx = owp * A(ex), opz = owp * A(ez), r3 = owp * A(xi2) + owc;
+                    acc[0] += owp; acc[1] += opx; acc[3] += opz;
+                    acc[4] += opx * A(ex); acc[5] += owc; acc[6] += opz * A(ez); acc[8] += opx * A(ez);
+                    acc[10] += r3 * A(ex); acc[12] += r3 * A(ez);
+                } else {
+                    const A owx = ow * A(ex), owy = ow * A(ey), owz = ow * A(ez), ow2 = ow * A(xi2);
+                    acc[0] += ow; acc[1] += owx; acc[2] += owy; acc[3] += owz;
+                    acc[4] += owx * A(ex); acc[5] += owy * A(ey); acc[6] += owz * A(ez);
+                    acc[7] += owx * A(ey); acc[8] += owx * A(ez); acc[9] += owy * A(ez);
+                    acc[10] += ow2 * A(ex); acc[11] += ow2 * A(ey); acc[12] += ow2 * A(ez);
+                }
+            } else {
 #pragma unroll
-            for (int a = 0; a < kNMom; ++a) acc[a] += o * wpsi[v][a];
+                for (int a = 0; a < kNMom; ++a) acc[a] += o * wpsi[v][a];
+            }
         }
         const A tot = reduce_scatter16<A>(acc, lane);
         const int m = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
         if ((lane & 1) == 0) red[((size_t)cc * (kThreads / 32) + warp) * 16 + m] = tot;
         outp += ostep;
+        if (kLo && STAGE == 3) lop += ostep;
     }
     __syncthreads();
     for (int e = tid; e < zn * kNMom; e += kThreads) {
         const int c = e / kNMom, a = e - c * kNMom;
-        A s = A(0);
+        double s = 0.0;
 #pragma unroll
         for (int q = 0; q < kThreads / 32; ++q) s += red[((size_t)c * (kThreads / 32) + q) * 16 + a];
-        I.partial[((size_t)tile.chunk * kNMom + a) * Nz + z0 + c] = double(s);
+        I.partial[((size_t)tile.chunk * kNMom + a) * Nz + z0 + c] = s;
     }
 
-    // ---- 6. outgoing WENO flux of F_out through the wall interfaces (for n_w).
-    // Each thread re-reads the outputs it wrote itself (STAGE 0: its input rows).
+    // ---- 6. outgoing WENO flux of the stage output through the wall interfaces (for
+    // n_w), as a sum over the deviations (the rest state's flux is added by the
+    // finalisation).  Each thread re-reads the outputs it wrote itself: the new d after
+    // stage 3, d + the increment after stages 1 and 2 (STAGE 0: its input rows).
     auto outval = [&](int v, int cell) -> T {
-        return STAGE == 0 ? Fs[(size_t)(cell + rbase) * KC + kl[v]] : Fout[(size_t)cell * Q + k0 + kl[v]];
+        const T* row = Fs + (size_t)(cell + rbase) * KC;
+        if (STAGE == 0) return row[kl[v]];
+        const T o = Fout[(size_t)cell * Q + k0 + kl[v]];
+        return STAGE == 3 ? o : row[kl[v]] + o;
     };
     if (z0 == 0) {  // bottom: p_z < 0 leaves through s = -1/2
         double fl = 0.0;
@@ -988,9 +1116,9 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     if (!last) return;
     __threadfence();
     if (I.fin_warp) {
-        for (int c = tid >> 5; c < zn; c += kThreads / 32) finalize_cell_warp<T>(I, z0 + c, tid & 31);
+        for (int c = tid >> 5; c < zn; c += kThreads / 32) finalize_cell_warp<T>(I, z0 + c, tid & 31, STAGE);
     } else if (tid < zn) {
-        finalize_cell<T>(I, z0 + tid);
+        finalize_cell<T>(I, z0 + tid, STAGE);
     }
     if (tid == 0) I.zcount[tile.zt] = 0;
     __threadfence();

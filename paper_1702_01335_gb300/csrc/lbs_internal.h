@@ -22,11 +22,13 @@ constexpr int kMaxZT = 64;      // cells of a z-tile
 enum { QUAD_FULL = 0, QUAD_HALF = 1 };
 
 // Cell record (storage type T): n, ux, uy, uz, T, qx, qy, qz, 1/tau,
-// (1 - Pr)/(n T^2), 1/(5T), n / (discrete weighted sums of the per-axis factors);
-// then the expansion coefficients of the
-// truncated equilibrium: a_l (x), a_l (y), b_l (z, p_z > 0), b_l (z, p_z < 0),
-// kMaxN + 1 slots each.
-enum { R_N = 0, R_UX, R_UY, R_UZ, R_T, R_QX, R_QY, R_QZ, R_ITAU, R_CS, R_I5T, R_SCALE };
+// (1 - Pr)/(n T^2), 1/(5T), R_SCALE - 1 where R_SCALE = n / (discrete weighted sums of
+// the per-axis factors); then the expansion coefficients of the truncated equilibrium
+// minus those of the rest state (the populations are stored as deviations from it):
+// a_l (x), a_l (y) with a_0 - 1 = 0 in slot 0, b_l (z, p_z > 0), b_l (z, p_z < 0) with
+// b_0 - 1/2 in slot 0; kMaxN + 1 slots each.  A factor's deviation from 1 is then
+// sum_l slot_l basis_l, free of the cancellation of 1 + small - 1.
+enum { R_N = 0, R_UX, R_UY, R_UZ, R_T, R_QX, R_QY, R_QZ, R_ITAU, R_CS, R_I5T, R_SCALE1 };
 constexpr int R_AX = kRecHead, R_AY = R_AX + kMaxN + 1, R_BP = R_AY + kMaxN + 1, R_BM = R_BP + kMaxN + 1;
 constexpr int kRecStride = R_BM + kMaxN + 1;
 
@@ -45,6 +47,11 @@ struct InstDev {
     double Dtop, Dbot;            // sum over incoming velocities of w p_z Gw (n_w = 1)
     double wsum[4][kMaxN + 1];    // sum_i w_i basis_l(p_i) of the stored (rounded) tables:
                                   // x, y, z (p_z > 0), z (p_z < 0); 1, 0, 0, ... exactly
+    double mrest[kNMom];          // raw moments of the rest state f = w (the stored weights and
+                                  // nodes): the partials hold sums over the deviations only
+    double frest_bot, frest_top;  // outgoing wall flux of the rest state (sum w p_z over the
+                                  // velocities leaving through each wall)
+    unsigned wait_limit;          // spins of the bounded wait for the bulk copies
     double ext_top[2][3];         // ghost Nz+1 <- (Nz, Nz-1, Nz-2); Nz+2 <- (Nz+1, Nz, Nz-1)
     double ext_bot[2][3];         // ghost 0 <- (1, 2, 3); ghost -1 <- (0, 1, 2)
     // tables
@@ -52,10 +59,19 @@ struct InstDev {
     const double *alpha, *beta;   // half-range recurrence, [kMaxN + 2]
     // storage-typed tables (float or double)
     const void *px, *py, *xi, *wx, *wy, *wz;
-    const void *gwx_top, *gwx_bot, *gwy, *gwz;  // wall equilibria per axis (Q_x, Q_x, Q_y, 2Q_z)
+    const void *gwx_top, *gwx_bot, *gwy, *gwz;  // wall equilibria per axis (Q_x, Q_x, Q_y, 2Q_z),
+                                                 // deviations from 1 of the normalised factors
     const void *inv_dz;                          // [Nz]
-    // state and work
-    void *F0, *F1, *F2;           // [Nz][Q] normalised populations f / w
+    // state and work.  The state is d = f / w - 1 (deviation of the normalised populations
+    // from the rest Maxwellian), [Nz][Q].  F0 and F1 take turns: *cur = 0 means F0 holds d
+    // and F1 the stage-1 increment d1 = F1 - F_l; *cur = 1 the reverse.  F2 holds the
+    // stage-2 increment d2 = F2 - F_l.  Stage 3 writes the new d over the stage-1
+    // increment (no longer needed) and flips *cur, so no stage writes what another CTA
+    // of the same launch still reads.  FP32 storage keeps the rounding residual of d in
+    // L0 (16-bit fixed point in units of 2^-15 ulp(d), see lo_encode).
+    void *F0, *F1, *F2;
+    unsigned short *L0;           // [Nz][Q], FP32 storage only
+    int *cur;                     // [1]
     void *rec;                    // [Nz][kRecStride]
     double *partial;              // [nchunks][kNMom][Nz]
     double *flux_part;            // [nchunks][2]: bottom, top outgoing flux
@@ -68,8 +84,13 @@ struct InstDev {
     int *zcount;                  // [nzt] chunks of a z-tile finished this stage (ticket counters)
     int *icount;                  // [1] z-tiles of the instance finalised this stage
     int nzt;                      // z-tiles of the current tiling
-    int *status;                  // [1]: bit 0 non-finite / non-positive n, T
+    int *status;                  // [1]: bit 0 non-finite / non-positive n, T; bit 1 a bounded
+                                  // wait for the bulk copies ran out
 };
+
+enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
+constexpr unsigned kWaitLimit = 1u << 26;   // default spins of the bounded wait (~seconds)
+constexpr unsigned kDrainLimit = 1u << 28;  // spins granted to copies still in flight after a timeout
 
 struct Tile { int inst, z0, zn, chunk, zt; };
 
@@ -192,6 +213,57 @@ LBS_HD void half_coeffs_pm(double u, double T, double iT, int N, const double* a
             bp[l + 1] = Pc[0];
             bm[l + 1] = Mc[0];
         }
+    }
+}
+
+// Macroscopic state of a cell from its 13 raw moments (FP64): n, u, the central
+// second moments P_ab = sum p_a p_b f - n u_a u_b, T = tr P / (3n) and the heat flux
+// q_a = 1/2 sum |xi|^2 xi_a f with xi = p - u (Eq. qdef), expanded in raw moments.
+struct CellState {
+    double n, in, u[3], T, q[3], P[6];  // P: xx, yy, zz, xy, xz, yz
+};
+LBS_HD void cell_state(const double* mom, CellState& c)
+{
+    const double n = mom[0], in = 1.0 / n;
+    c.n = n;
+    c.in = in;
+    c.u[0] = mom[1] * in; c.u[1] = mom[2] * in; c.u[2] = mom[3] * in;
+    const double* u = c.u;
+    c.P[0] = mom[4] - n * u[0] * u[0]; c.P[1] = mom[5] - n * u[1] * u[1];
+    c.P[2] = mom[6] - n * u[2] * u[2]; c.P[3] = mom[7] - n * u[0] * u[1];
+    c.P[4] = mom[8] - n * u[0] * u[2]; c.P[5] = mom[9] - n * u[1] * u[2];
+    c.T = (c.P[0] + c.P[1] + c.P[2]) * (1.0 / 3.0) * in;
+    const double M2[3][3] = {{mom[4], mom[7], mom[8]}, {mom[7], mom[5], mom[9]}, {mom[8], mom[9], mom[6]}};
+    const double tr = mom[4] + mom[5] + mom[6];
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double um = u[0] * mom[1] + u[1] * mom[2] + u[2] * mom[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double uM2 = u[0] * M2[0][a] + u[1] * M2[1][a] + u[2] * M2[2][a];
+        c.q[a] = 0.5 * (mom[10 + a] - u[a] * tr - 2.0 * uM2 + 2.0 * u[a] * um + uu * mom[1 + a] - uu * u[a] * n);
+    }
+}
+
+// The 13 raw moments m (order of cell_state: 1, p_a, p_a p_b (xx yy zz xy xz yz),
+// |p|^2 p_a) of a distribution re-expressed about the velocity u: the moments of
+// psi(p - u).  |p - u|^2 (p_a - u_a) = |p|^2 p_a - u_a |p|^2 - 2 (p.u) p_a + 2 u_a (p.u)
+// + |u|^2 p_a - |u|^2 u_a.
+LBS_HD void shift_moments(const double* m, const double* u, double* out)
+{
+    const double m0 = m[0], m1[3] = {m[1], m[2], m[3]};
+    const double M2[3][3] = {{m[4], m[7], m[8]}, {m[7], m[5], m[9]}, {m[8], m[9], m[6]}};
+    out[0] = m0;
+    for (int a = 0; a < 3; ++a) out[1 + a] = m1[a] - u[a] * m0;
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int e = 0; e < 6; ++e) {
+        const int a = ia[e], b = ib[e];
+        out[4 + e] = M2[a][b] - u[a] * m1[b] - u[b] * m1[a] + u[a] * u[b] * m0;
+    }
+    const double tr = m[4] + m[5] + m[6], uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double um = u[0] * m1[0] + u[1] * m1[1] + u[2] * m1[2];
+    for (int a = 0; a < 3; ++a) {
+        const double uM2 = u[0] * M2[0][a] + u[1] * M2[1][a] + u[2] * M2[2][a];
+        out[10 + a] = m[10 + a] - u[a] * tr - 2.0 * uM2 + 2.0 * u[a] * um + uu * m1[a] - uu * u[a] * m0;
     }
 }
 

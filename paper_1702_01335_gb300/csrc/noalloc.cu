@@ -30,7 +30,8 @@ constexpr size_t kStaticScratch = size_t(1) << 18;  // doubles
 // on one device) race on it.
 static __device__ __align__(256) double g_static_partial[kStaticScratch];
 
-// per (velocity chunk, cell): raw moments sum_k w_k f_k psi(p_k), FP64 sums
+// per (velocity chunk, cell): raw moments sum_k w_k f_k psi(p_k), FP64 sums, of the
+// populations f_k = w_k (1 + d_k) given as their deviations d_k (the solver's state form)
 template <typename T>
 __global__ void __launch_bounds__(128) static_partials(const InstDev* __restrict__ insts, int inst,
                                                       const T* __restrict__ f, double* __restrict__ partial)
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(128) static_partials(const InstDev* __restrict
         const double xi = static_cast<const T*>(I.xi)[m], Z = sg ? -xi : xi;
         const double w = double(static_cast<const T*>(I.wx)[i]) * double(static_cast<const T*>(I.wy)[j]) *
                          double(static_cast<const T*>(I.wz)[m]);
-        const double g = w * double(f[(size_t)cell * Q + k]);
+        const double g = w * (1.0 + double(f[(size_t)cell * Q + k]));  // f_k = w_k (1 + d_k)
         if (I.reduced && j == 1) {  // chi = int p_y^2 f dp_y: the p_y^2 moments only
             acc[5] += g;
             acc[10] += g * X;
@@ -88,22 +89,10 @@ __global__ void static_profiles(const InstDev* __restrict__ insts, int inst, int
         for (int c = 0; c < nchunks; ++c) s += partial[((size_t)c * Nz + cell) * kNMom + a];
         mom[a] = s;
     }
-    const double n = mom[0];
-    const double u[3] = {mom[1] / n, mom[2] / n, mom[3] / n};
-    const double Pxx = mom[4] - n * u[0] * u[0], Pyy = mom[5] - n * u[1] * u[1];
-    const double Pzz = mom[6] - n * u[2] * u[2], Pxy = mom[7] - n * u[0] * u[1];
-    const double Pxz = mom[8] - n * u[0] * u[2], Pyz = mom[9] - n * u[1] * u[2];
-    const double T_ = (Pxx + Pyy + Pzz) / (3.0 * n);
-    const double M2[3][3] = {{mom[4], mom[7], mom[8]}, {mom[7], mom[5], mom[9]}, {mom[8], mom[9], mom[6]}};
-    const double tr = mom[4] + mom[5] + mom[6];
-    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const double um = u[0] * mom[1] + u[1] * mom[2] + u[2] * mom[3];
-    double q[3];
-    for (int a = 0; a < 3; ++a) {
-        const double uM2 = u[0] * M2[0][a] + u[1] * M2[1][a] + u[2] * M2[2][a];
-        q[a] = 0.5 * (mom[10 + a] - u[a] * tr - 2.0 * uM2 + 2.0 * u[a] * um + uu * mom[1 + a] - uu * u[a] * n);
-    }
-    const double vals[14] = {n, u[0], u[1], u[2], T_, q[0], q[1], q[2], Pxx, Pyy, Pzz, Pxy, Pxz, Pyz};
+    CellState c;  // the solver's own raw -> central moment map (NaN profiles if n = 0)
+    cell_state(mom, c);
+    const double vals[14] = {c.n, c.u[0], c.u[1], c.u[2], c.T, c.q[0], c.q[1], c.q[2],
+                             c.P[0], c.P[1], c.P[2], c.P[3], c.P[4], c.P[5]};
     for (int a = 0; a < 14; ++a) prof[(size_t)a * Nz + cell] = vals[a];
 }
 

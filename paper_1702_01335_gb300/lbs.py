@@ -22,7 +22,10 @@ MOMENT_NAMES = ("n", "ux", "T", "qx", "qz", "Pxx", "Pxz", "Pzz")
 PROFILE_NAMES = ("n", "ux", "uy", "uz", "T", "qx", "qy", "qz",
                  "Pxx", "Pyy", "Pzz", "Pxy", "Pxz", "Pyz")
 STATUS = {0: "LBS_OK", 1: "LBS_ERR_ARG", 2: "LBS_ERR_CUDA", 3: "LBS_ERR_NONFINITE",
-          4: "LBS_ERR_NO_CONVERGENCE", 5: "LBS_ERR_QUADRATURE"}
+          4: "LBS_ERR_NO_CONVERGENCE", 5: "LBS_ERR_QUADRATURE", 6: "LBS_ERR_TIMEOUT"}
+LBS_ERR_NONFINITE = 3
+LBS_ERR_NO_CONVERGENCE = 4
+LBS_ERR_TIMEOUT = 6
 
 _lock = threading.Lock()
 _lib = None
@@ -64,7 +67,8 @@ EXPORTS = ("lbs_create", "lbs_batch_create", "lbs_destroy", "lbs_step", "lbs_run
            "lbs_get_state", "lbs_set_state", "lbs_init_from_profiles", "lbs_quadrature",
            "lbs_get_stream", "lbs_profile_steps", "lbs_moments_static", "lbs_set_tiling",
            "lbs_get_tiling", "lbs_last_error", "lbs_couette_diagnostics", "lbs_diagnostics",
-           "lbs_set_finalize", "lbs_couette_nonlinear_velocity",
+           "lbs_set_finalize", "lbs_couette_nonlinear_velocity", "lbs_set_wait_limit", "lbs_clear_status",
+           "lbs_probe_fma_rate",
            # the warm-start network (bound in warmstart.py)
            "lbs_mlp_create", "lbs_mlp_destroy", "lbs_mlp_num_params", "lbs_mlp_set_params",
            "lbs_mlp_get_params", "lbs_mlp_forward", "lbs_mlp_loss_grad", "lbs_mlp_adam",
@@ -109,6 +113,9 @@ def load(build_if_missing=True):
         lib.lbs_profile_steps.argtypes = [P, C.c_long, D]
         lib.lbs_moments_static.argtypes = [P, C.c_int, P, P]
         lib.lbs_set_tiling.argtypes = [P, C.c_int, C.c_int, C.c_int]
+        lib.lbs_set_wait_limit.argtypes = [P, C.c_uint]
+        lib.lbs_clear_status.argtypes = [P]
+        lib.lbs_probe_fma_rate.argtypes = [D, D]
         I = C.POINTER(C.c_int)
         lib.lbs_get_tiling.argtypes = [P, I, I, I, I, L]
         lib.lbs_last_error.restype = C.c_char_p
@@ -152,12 +159,42 @@ def couette_nonlinear_velocity(prof, Nz, A, half):
     return z, u
 
 
+def probe_fma_rate():
+    """(FP64, FP32) fused multiply-add rates of the current device in FLOP/s."""
+    lib = load()
+    a, b = C.c_double(), C.c_double()
+    _check(lib.lbs_probe_fma_rate(C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
 def quadrature(kind, Q):
     """The solver's Gauss rule (host only): kind 0 full range, 1 half range."""
     lib = load()
     x, w = np.zeros(Q), np.zeros(Q)
     _check(lib.lbs_quadrature(kind, Q, _dptr(x), _dptr(w)))
     return x, w
+
+
+@dataclasses.dataclass
+class State:
+    """A stored state as lbs_get_state returns it: d[Nz, Q], the deviations f / w - 1 in
+    the storage dtype, and (FP32 storage) r[Nz, Q] int16, the rounding residuals in units
+    of 2^-15 ulp(d); None with FP64 storage."""
+    d: np.ndarray
+    r: object = None
+
+    def normalised(self):
+        """f / w = 1 + d + r 2^-15 ulp(d) as float64 (exact: every term is exact in FP64)."""
+        return 1.0 + self.deviation()
+
+    def deviation(self):
+        """d + r 2^-15 ulp(d) as float64."""
+        d = self.d.astype(np.float64)
+        if self.r is None:
+            return d
+        E = ((self.d.view(np.uint32) >> 23) & 0xFF).astype(np.int64)
+        lo = np.where(E >= 39, self.r.astype(np.float64) * np.exp2(np.clip(E, 39, 255) - 165.0), 0.0)
+        return d + lo
 
 
 @dataclasses.dataclass
@@ -269,8 +306,17 @@ class Solver:
         return tuple(out)
 
     def state_bytes(self):
-        esize = 4 if self.precision == LBS_FP32 else 8
+        """Bytes of every instance's state in the layout of lbs_get_state (d, then the
+        FP32 residuals)."""
+        esize = 6 if self.precision == LBS_FP32 else 8
         return sum(i.Nz * i.Q for i in self.instances) * esize
+
+    def set_wait_limit(self, spins):
+        """Spins of the stage kernel's bounded wait for its bulk copies (failure tests)."""
+        _check(self.lib.lbs_set_wait_limit(self.h, int(spins)))
+
+    def clear_status(self):
+        _check(self.lib.lbs_clear_status(self.h))
 
     def moments_static(self, inst, f_dev_ptr, prof_dev_ptr):
         """Profiles [14][Nz] (FP64, device) of the device state at f_dev_ptr, computed
@@ -343,18 +389,37 @@ class Solver:
         return r.value
 
     def get_state(self, inst=0):
-        """Normalised populations f_k / w_k, [Nz, Q], as a host array."""
+        """The stored state of instance inst (a State: deviations d and, with FP32
+        storage, the residuals r), copied to host arrays."""
         I = self.instances[inst]
-        a = np.zeros((I.Nz, I.Q), dtype=self.dtype)
-        _check(self.lib.lbs_get_state(self.h, inst, a.ctypes.data_as(C.c_void_p), 1))
-        return a
+        n = I.Nz * I.Q
+        esize = np.dtype(self.dtype).itemsize
+        buf = np.zeros(n * esize + (2 * n if self.precision == LBS_FP32 else 0), dtype=np.uint8)
+        _check(self.lib.lbs_get_state(self.h, inst, buf.ctypes.data_as(C.c_void_p), 1))
+        d = buf[:n * esize].view(self.dtype).reshape(I.Nz, I.Q).copy()
+        r = buf[n * esize:].view(np.int16).reshape(I.Nz, I.Q).copy() if self.precision == LBS_FP32 else None
+        return State(d, r)
+
+    def populations(self, inst=0):
+        """Normalised populations f_k / w_k, [Nz, Q], float64."""
+        return self.get_state(inst).normalised()
 
     def get_state_device(self, inst, out_ptr):
+        """Copy instance inst's state (lbs_get_state layout) to device memory at out_ptr."""
         _check(self.lib.lbs_get_state(self.h, inst, C.c_void_p(out_ptr), 0))
 
-    def set_state(self, inst, a):
-        a = np.ascontiguousarray(a, dtype=self.dtype)
-        _check(self.lib.lbs_set_state(self.h, inst, a.ctypes.data_as(C.c_void_p), 1))
+    def set_state(self, inst, state):
+        """Set instance inst from a State (or a bare deviation array d: residuals zero)."""
+        I = self.instances[inst]
+        if not isinstance(state, State):
+            state = State(np.asarray(state), None)
+        d = np.ascontiguousarray(state.d, dtype=self.dtype).reshape(I.Nz, I.Q)
+        parts = [d.view(np.uint8).ravel()]
+        if self.precision == LBS_FP32:
+            r = np.zeros((I.Nz, I.Q), np.int16) if state.r is None else np.ascontiguousarray(state.r, np.int16)
+            parts.append(r.view(np.uint8).ravel())
+        buf = np.ascontiguousarray(np.concatenate(parts))
+        _check(self.lib.lbs_set_state(self.h, inst, buf.ctypes.data_as(C.c_void_p), 1))
 
     def set_state_device(self, inst, ptr):
         _check(self.lib.lbs_set_state(self.h, inst, C.c_void_p(ptr), 0))

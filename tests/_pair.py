@@ -19,7 +19,12 @@ def solver_of(ps, dt, precision):
 
 def gpu_f(solver, o, inst=0):
     """GPU state as populations with the weights applied, [Nz, Q] (oracle layout)."""
-    return solver.get_state(inst).astype(np.float64) * o.weights()[None, :]
+    return solver.populations(inst) * o.weights()[None, :]
+
+
+def same_state(a, b):
+    """Two stored states (deviations and FP32 residuals) equal bit for bit."""
+    return np.array_equal(a.d, b.d) and (a.r is None) == (b.r is None) and (a.r is None or np.array_equal(a.r, b.r))
 
 
 def rel_err(a, b, scale=None):

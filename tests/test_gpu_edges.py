@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from tests._pair import gpu_f, oracle_of, profile_errors, rel_err, solver_of
+from tests._pair import gpu_f, oracle_of, profile_errors, rel_err, same_state, solver_of
 
 pytestmark = pytest.mark.gpu
 
@@ -66,17 +66,19 @@ def test_largest_expansion_order():
 
 def test_zero_steps_and_resting_walls():
     """lbs_step(0) changes nothing; with u_w = 0 and T_w = 1 the rest state stays at
-    rest (n = 1, u = 0, T = 1) to rounding, and the residual stays at rounding level."""
+    rest (n = 1, u = 0, T = 1) to rounding: the stored deviations stay at the level of
+    the FP64 rounding of the equilibrium coefficients.  (The residual is a relative
+    change; with u_x zero up to rounding in every cell its u_x part compares rounding
+    with rounding, so it is not a measure here.)"""
     P = _lbs()
     p = dict(W.C1, u_w=0.0, A=0.9)
     s = solver_of(p, 0.003, P.LBS_FP64)
     before = s.get_state(0)
     s.step(0)
-    assert np.array_equal(s.get_state(0), before)
+    assert same_state(s.get_state(0), before)
     s.step(200)
     prof = s.profiles()
     assert np.abs(prof["n"] - 1).max() < 1e-13
     assert np.abs(prof["ux"]).max() < 1e-13
     assert np.abs(prof["T"] - 1).max() < 1e-13
-    assert s.residual() < 1e-12
-    assert np.abs(s.get_state(0) - 1.0).max() < 1e-12
+    assert np.abs(s.get_state(0).d).max() < 1e-12

@@ -30,7 +30,7 @@ def test_lowmach_half_channel_matches_oracle():
     s = Solver([Instance(dt=o.dt, **p)], precision=P.LBS_FP64)
     o.step(300)
     s.step(300)
-    f_gpu = s.get_state().astype(np.float64) * o.weights()[None, :]
+    f_gpu = s.populations() * o.weights()[None, :]
     f_ora = o.f[3 + S:3 + 2 * S]
     assert rel_err(f_gpu, f_ora) < 1e-13
     po = {k: v[S:] for k, v in o.profiles().items()}

@@ -1,65 +1,112 @@
-"""FP32 storage with FP64 moment sums: the error of every macroscopic profile against
-the FP64 oracle, stated as a number and bounded by 1e-5 relative to the profile's
-scale: its own maximum, except velocities (the Couette scale max(max |u_x|, u_w)) and
-heat fluxes (n T^(3/2)).  Both the bounded numbers and the errors relative to each
-profile's own maximum are printed for the record."""
+"""FP32 storage with FP64 moment sums: the error of every macroscopic profile against the
+FP64 oracle, stated as a number and bounded by 1e-5 relative to that profile's own
+largest magnitude (no profile among n, u_x, T, q_x, q_z, P_xx, P_xz, P_zz vanishes in
+these flows, so no absolute floor is used), on trajectories marched to the steady state.
+
+The two solves start from the same rest state and take the same number of steps, so
+they follow the same trajectory; two solves each stopped at R < tol would only be
+R / (1 - lambda) apart along the slowest mode (lambda its contraction per step), far
+more than the storage precision.  The steady states are the oracle's own (C1 here, C2
+from tests/golden/steady_C2.json, written by tests/golden/make_steady.py).
+
+Without the stored rounding residual of the state, FP32 storage loses every RK
+increment below half an ulp of f and stalls about eps_32 / (lambda dt) short of the
+steady state: 1e-5 on C1 (dt = 5.4e-3), 1e-3 on C2 (dt = 4.7e-5, stretched cells)."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 import workloads as W
-from tests._pair import oracle_of, profile_errors, solver_of
+from tests._pair import oracle_of, solver_of
 
 pytestmark = pytest.mark.gpu
 
 BOUND = 1e-5
 PROFILES8 = ("n", "ux", "T", "qx", "qz", "Pxx", "Pxz", "Pzz")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-def _report(name, errs, s=None, o=None, own=None):
-    worst = max(errs[k] for k in PROFILES8)
-    if own is not None:
-        print("\n[fp32 vs fp64 oracle, own-maximum scale] %s: %s" % (
-            name, ", ".join("%s %.1e" % (k, own[k]) for k in PROFILES8)))
-    extra = ""
-    if s is not None:
-        dz = np.diff(o.xf)
-        extra = "; mass drift fp32 %.1e, oracle %.1e" % (np.sum(s.profiles()["n"] * dz) - 1.0,
-                                                          np.sum(o.profiles()["n"] * dz) - 1.0)
-    print("\n[fp32 vs fp64 oracle] %s: %s; worst %.2e%s" % (
+def own_scale_errors(gp, op):
+    """max |fp32 - oracle| / max |oracle| for each of the eight profiles."""
+    return {k: float(np.abs(np.asarray(gp[k]) - np.asarray(op[k])).max() / np.abs(np.asarray(op[k])).max())
+            for k in PROFILES8}
+
+
+def _report(name, errs, drift=None):
+    worst = max(errs.values())
+    extra = "" if drift is None else "; mass drift %.1e" % drift
+    print("\n[fp32 vs fp64 oracle, own scale] %s: %s; worst %.2e%s" % (
         name, ", ".join("%s %.1e" % (k, errs[k]) for k in PROFILES8), worst, extra))
     return worst
 
 
 def test_fp32_error_c1_steady_state():
-    """C1 marched to the oracle's steady state (R < 1e-8)."""
+    """C1 marched to the oracle's R < 1e-10 (well past the FP32 resolution of a step's
+    change)."""
     import paper_1702_01335_gb300 as P
     o = oracle_of(W.C1, None)
-    steps, R = o.run_to_steady(1e-8, chunk=100)
+    steps, R = o.run_to_steady(1e-10, chunk=100)
     s = solver_of(W.C1, o.dt, P.LBS_FP32)
     s.step(steps)
     gp, op = s.profiles(), o.profiles()
-    worst = _report("C1 steady (%d steps)" % steps, profile_errors(gp, op, W.C1["u_w"]), s, o,
-                    profile_errors(gp, op))
+    dz = np.diff(o.xf)
+    worst = _report("C1 steady (%d steps, R %.1e)" % (steps, R), own_scale_errors(gp, op),
+                    float(np.sum(gp["n"] * dz)) - 1.0)
     assert worst < BOUND
 
 
-def test_fp32_error_c2_2000_steps():
+def _golden(name):
+    with open(os.path.join(GOLDEN, "steady_%s.json" % name)) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.skipif(not os.path.exists(os.path.join(GOLDEN, "steady_C2.json")),
+                    reason="tests/golden/steady_C2.json not written yet")
+@pytest.mark.parametrize("tol", [1e-7, 1e-8])
+def test_fp32_error_c2_steady_state(tol):
+    """C2 (stretched cells, dt = 4.7e-5) at the oracle's first steps with R < 1e-7 and
+    R < 1e-8, from the golden record of the oracle's march."""
     import paper_1702_01335_gb300 as P
-    o = oracle_of(W.C2, None)
-    o.step(2000)
-    s = solver_of(W.C2, o.dt, P.LBS_FP32)
-    s.step(2000)
-    gp, op = s.profiles(), o.profiles()
-    worst = _report("C2 after 2000 steps", profile_errors(gp, op, W.C2["u_w"]), s, o, profile_errors(gp, op))
+    g = _golden("C2")
+    mark = [m for m in g["marks"] if m["tol"] == tol][0]
+    s = solver_of(W.C2, g["dt"], P.LBS_FP32)
+    s.step(mark["steps"])
+    worst = _report("C2 at R < %.0e (%d steps)" % (tol, mark["steps"]),
+                    own_scale_errors(s.profiles(), mark["profiles"]))
     assert worst < BOUND
 
 
-def test_fp32_error_c3_60_steps():
+def test_fp32_error_c3():
+    """C3 (8192 velocities, Kn = 100) after 300 steps."""
     import paper_1702_01335_gb300 as P
     o = oracle_of(W.C3, None)
-    o.step(60)
+    o.step(300)
     s = solver_of(W.C3, o.dt, P.LBS_FP32)
-    s.step(60)
-    gp, op = s.profiles(), o.profiles()
-    worst = _report("C3 after 60 steps", profile_errors(gp, op, W.C3["u_w"]), s, o, profile_errors(gp, op))
+    s.step(300)
+    worst = _report("C3 after 300 steps", own_scale_errors(s.profiles(), o.profiles()))
     assert worst < BOUND
+
+
+def test_fp32_paper_tables_equal_fp64():
+    """The 20 table runs of Sec. VI (reading of the run parameters as in the table
+    test), 120000 steps in FP32 storage and in FP64: nu, Pi and T_0 agree to 1e-5
+    relative, including delta = 0.1, where FP32 without the residual stalled 8e-4 short
+    on Pi (Ar: 0.53536 against 0.53579)."""
+    import paper_1702_01335_gb300 as P
+    from paper_1702_01335_gb300 import Instance, Solver
+    runs = W.paper_tables()
+    res = {}
+    for prec in (P.LBS_FP32, P.LBS_FP64):
+        s = Solver([Instance(**p) for _, p in runs], precision=prec)
+        s.step(120000)
+        res[prec] = [s.diagnostics(b) for b in range(len(runs))]
+        s.close()
+    worst = {k: 0.0 for k in ("nu", "Pi", "T0")}
+    for b, (label, _) in enumerate(runs):
+        for k in worst:
+            a, r = res[P.LBS_FP32][b][k], res[P.LBS_FP64][b][k]
+            worst[k] = max(worst[k], abs(a - r) / abs(r))
+    print("\n[paper tables, fp32 vs fp64, 120000 steps] worst relative: %s" % worst)
+    assert max(worst.values()) < BOUND, worst

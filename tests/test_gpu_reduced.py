@@ -85,7 +85,7 @@ def test_reduced_half_channel_is_upper_half_of_full_channel():
     s = Solver([Instance(dt=o.dt, half=1, **dict(RED, Nz=S))], precision=P.LBS_FP64)
     o.step(40)
     s.step(40)
-    f_gpu = s.get_state().astype(np.float64) * o.weights()[None, :]
+    f_gpu = s.populations() * o.weights()[None, :]
     assert rel_err(f_gpu, o.f[3 + S:3 + 2 * S]) < FP64_TOL
     p_ora = {k: v[S:] for k, v in o.profiles().items()}
     errs = profile_errors(s.profiles(), p_ora)

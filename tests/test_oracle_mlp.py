@@ -62,3 +62,28 @@ def test_adam_first_step_is_signed_lr():
     mlp.adam_step(p, g, st, lr=0.01)
     # m_hat = g, v_hat = g^2: the step is lr g / (|g| + eps)
     assert np.allclose(p["W"], old - 0.01 * np.sign(g["W"]), rtol=0, atol=1e-8)
+
+
+def test_gpu_error_bounds_catch_a_wrong_column():
+    """The element-wise check of the GPU network (tests/test_gpu_mlp.py) has the power to
+    see a plausible kernel mistake: a gradient whose column k of W1 is replaced by
+    column k+1 (planted in the oracle's own gradient, on the CPU), or a bias gradient
+    with one row doubled, fails it."""
+    from tests.test_gpu_mlp import _within, error_bounds
+    om = mlp
+    rng = np.random.default_rng(7)
+    sizes, B = (6, 32, 32, 40), 37
+    p = om.init_params(rng, sizes)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = 0.1 * rng.standard_normal(p[k].shape)
+    x, t = rng.standard_normal((B, 6)), rng.standard_normal((B, 40))
+    E = error_bounds(p, x, t)
+    _, g = om.loss_and_grads(p, x, t)
+    assert all(_within(g[k], g[k], E[k]) for k in g)
+    wrong = g["W1"].copy()
+    wrong[:, 2] = g["W1"][:, 3]
+    assert not _within(wrong, g["W1"], E["W1"])
+    wrong = g["b2"].copy()
+    wrong[5] *= 2.0
+    assert not _within(wrong, g["b2"], E["b2"])

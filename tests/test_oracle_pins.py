@@ -470,3 +470,41 @@ def test_paper_printed_values():
     assert abs(nu - case["nu"]) <= 1.0e-3
     assert abs(Pi / case["Pi"] - 1) < 1e-3
     assert abs(T0 / case["T0"] - 1) < 1e-3
+
+
+def test_residual_hand_computed():
+    """The steady-state residual (the paper states no criterion; the solver's definition
+    R = max over W in {n, u_x, T} of ||W_new - W_old||_2 / max(||W_old||_2, 1e-30)) on
+    3-cell cases computed by hand.  A squared norm, an L1 norm, a missing max over the
+    three profiles, or the new state in the denominator each give another number."""
+    from oracle.oracle import residual
+    one = [1.0, 1.0, 1.0]
+    # only u_x changes: R = 0.003 / sqrt(0.1^2 + 0.1^2) = 0.0212132034...
+    Wo = [one, [0.1, 0.0, -0.1], one]
+    Wn = [one, [0.1, 0.003, -0.1], [1.0, 1.0004, 1.0]]
+    assert abs(residual(Wo, Wn) - 0.003 / math.sqrt(0.02)) < 1e-15
+    assert abs(0.003 / math.sqrt(0.02) - 0.021213203435596) < 1e-14
+    # T dominates: n changes 0.01 in one cell (0.01 / sqrt 3), T 0.05 (0.05 / sqrt 3)
+    Wo = [one, [0.2, 0.0, -0.2], one]
+    Wn = [[1.01, 1.0, 1.0], [0.2, 0.0, -0.2], [1.0, 1.0, 1.05]]
+    assert abs(residual(Wo, Wn) - 0.05 / math.sqrt(3.0)) < 1e-15
+    # u_x from rest: the norm of the old profile is floored at 1e-30
+    Wo = [one, [0.0, 0.0, 0.0], one]
+    Wn = [one, [1e-3, 0.0, 0.0], one]
+    assert abs(residual(Wo, Wn) / 1e27 - 1.0) < 1e-12
+    # nothing changes
+    assert residual(Wo, Wo) == 0.0
+
+
+def test_residual_of_a_step_is_that_of_n_ux_T():
+    """The residual oracle_step reports for a step is the one of the profiles n, u_x
+    (velocity, not momentum) and T before and after that step."""
+    from oracle.oracle import residual
+    o = Oracle(3, 2, 3, 2, 8, Kn=0.2, uw=0.3, Pr=2.0 / 3.0)
+    o.step(5)
+    a = o.profiles()
+    r = o.step(1, residuals=True)[0]
+    b = o.profiles()
+    assert abs(r / residual([a["n"], a["ux"], a["T"]], [b["n"], b["ux"], b["T"]]) - 1.0) < 1e-12
+    mom = [b["n"], b["n"] * b["ux"], b["T"]]
+    assert abs(r / residual([a["n"], a["n"] * a["ux"], a["T"]], mom) - 1.0) > 1e-6

@@ -25,20 +25,28 @@ def test_static_moments_match_profiles(params, precision, tol):
     s = Solver(Instance(**params), precision=precision)
     st = s.torch_stream()
     Nz, Q = params["Nz"], Instance(**params).Q
-    dtype = torch.float32 if precision == 1 else torch.float64
-    f_dev = torch.empty((Nz, Q), dtype=dtype, device="cuda")
+    # the whole stored state (deviations, then the FP32 residuals); the call reads the
+    # deviations at its start
+    f_dev = torch.empty(s.state_bytes(), dtype=torch.uint8, device="cuda")
     out = torch.empty((14, Nz), dtype=torch.float64, device="cuda")
+    free = []
     for call in range(2):
         s.step(7 + 5 * call)
         s.get_state_device(0, f_dev.data_ptr())
         out.fill_(float("nan"))
         torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
         s.moments_static(0, f_dev.data_ptr(), out.data_ptr())
         with torch.cuda.stream(st):
             got = out.cpu().numpy()
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
         ref = s.profiles(0)
         errs = profile_errors(dict(zip(PROFILE_NAMES, got)), ref)
         assert max(errs.values()) < tol, (call, errs)
+    # no device memory taken by the calls themselves (the first call may load the module's
+    # scratch array, which is part of the library image; the second call must not grow it)
+    assert free[2] == free[3], free
     s.close()
 
 
