@@ -57,10 +57,13 @@ def parse():
                     help="V,ZT,fuse: use this stage-kernel tiling instead of the autotuner")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON cache of tile choices (default: the package's tuning_cache.json)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "tables", "luo"],
-                    help="c2: the throughput workload (default); tables: the 20 half-channel "
-                         "runs of the paper's Sec. VI tables; luo: the low-Mach runs of Sec. IV "
-                         "(Table luo); the last two on one GPU")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3x32", "sweep", "tables", "luo"],
+                    help="c2: the throughput workload (default; --precision f64 for the FP64 line); "
+                         "c3x32: 32 replicas of config C3 (Kn = 100, 8192 velocities); sweep: the "
+                         "64-instance seed-1702 sweep of config C4, timed per step and marched to "
+                         "R < 1e-8 per instance; tables: the 20 half-channel runs of the paper's "
+                         "Sec. VI tables; luo: the low-Mach runs of Sec. IV (Table luo); the last "
+                         "three on one GPU")
     ap.add_argument("--model", default="full", choices=["full", "reduced"],
                     help="tables workload: the 3D velocity set (Q_y = 7) or the paper's phi / chi model")
     a = ap.parse_args()
@@ -75,6 +78,17 @@ def peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+# FP64 floating-point operations of one cell x velocity update in one RK stage of the
+# FP64 solver (an FMA counts two), counted from the stage kernel's source: the WENO-5
+# correction of the interface ahead (differences 4, candidate corrections 6, smoothness
+# indicators 18, weights 10 with 4 divisions, the weighted sum 8: 46), the divergence
+# (5), the Shakhov factor (14), the target's deviation (6), the departure and the
+# combine (8), and the 13 moment sums (26): 105 per update and stage, 315 per RK-3 step.
+# Rounded to 300 (the stage-3 moments about the cell velocity add 10, stage 1's combine
+# is 4 shorter): an under-count makes the reported fraction a lower bound.
+FP64_FLOPS_PER_UPDATE_STEP = 300.0
 
 
 class Clocks:
@@ -131,16 +145,18 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _oracle_c2():
+def _oracle_c2(p=None):
     from oracle.oracle import Oracle
-    p = W.C2
+    p = p or W.C2
     return Oracle(p["Qx"], p["Qy"], p["Qz"], p["N_eq"], p["Nz"], A=p["A"], Kn=p["Kn"], uw=p["u_w"],
                   Tw=p["T_w"], Pr=p["Pr"], visc_law=p["visc_law"], visc_param=p["visc_param"])
 
 
-def cpu_baseline(seconds=12.0):
-    """The FP64 oracle as it stands on the host cores: one C2 instance, whole RK-3 steps."""
-    o = _oracle_c2()
+def cpu_baseline(p=None, seconds=12.0):
+    """The FP64 oracle as it stands on the host cores: one instance (C2 by default),
+    whole RK-3 steps."""
+    p = p or W.C2
+    o = _oracle_c2(p)
     o.step(1)
     t0 = time.perf_counter()
     n = 0
@@ -148,11 +164,11 @@ def cpu_baseline(seconds=12.0):
         o.step(1)
         n += 1
     dt = time.perf_counter() - t0
-    upd = W.C2["Nz"] * 2 * W.C2["Qx"] * W.C2["Qy"] * W.C2["Qz"] * n
+    upd = p["Nz"] * 2 * p["Qx"] * p["Qy"] * p["Qz"] * n
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": upd / dt, "unit": "updates/s", "cores": cores, "kind": "oracle",
-            "sample": "one C2 instance (128 cells x 2048 velocities), %d full RK-3 steps, FP64, "
-                      "%.1f s" % (n, dt)}
+            "sample": "one instance (%d cells x %d velocities), %d full RK-3 steps, FP64, "
+                      "%.1f s" % (p["Nz"], 2 * p["Qx"] * p["Qy"] * p["Qz"], n, dt)}
 
 
 def time_to_steady():
@@ -312,12 +328,117 @@ def cpu_baseline_half(run, seconds=12.0):
                       "half-channel updates" % (json.dumps(label), 2 * p["Nz"], o.Q, n, dt)}
 
 
+def run_sweep(a):
+    """Config C4: the 64-instance sweep (numpy PCG64 seed 1702; Kn log-uniform in
+    [0.01, 100], u_w in [0.05, 1], half mu ~ T^omega, half Sutherland; Nz 32-512, up to
+    16 x 4 x (2 x 48) velocities), every instance at its own CFL time step, in one batch.
+    Timed like the main line; then marched to R < 1e-8 per instance (device-side
+    retirement) within a step budget, reporting each instance's steps."""
+    import torch
+    from paper_1702_01335_gb300 import LBS_FP32, LBS_FP64, Instance, Solver
+    from paper_1702_01335_gb300.autotune import DEFAULT_CACHE, autotune
+    torch.cuda.set_device(0)
+    ps = W.sweep(64, W.SWEEP_SEED)
+    inst = [Instance(**p) for p in ps]
+    prec = LBS_FP32 if a.precision == "f32" else LBS_FP64
+    s = Solver(inst, precision=prec)
+    if a.tiling:
+        s.set_tiling(*(int(x) for x in a.tiling.split(",")))
+        tuned = {"source": "--tiling"}
+    else:
+        tuned = autotune(s, candidates=tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (8, 12, 16)
+                                             for F in (0, 2)), steps=3,
+                         cache_file=a.tuning_cache or DEFAULT_CACHE)
+    st = s.torch_stream()
+    upd_step = sum(i.Nz * i.Q for i in inst)
+    s.step(a.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record(st)
+        s.step(a.steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nprof = max(3, min(200, a.steps // 10))
+    tl = s.tiling()
+    if tl["fuse"] == 2:
+        s.set_tiling(tl["V"], tl["ZT"], 0)
+        s.profile_steps(1)
+    k_stage, k_fin, k_step = s.profile_steps(nprof)
+    if tl["fuse"] == 2:
+        s.set_tiling(tl["V"], tl["ZT"], 2)
+    bpu = BYTES_PER_UPDATE[a.precision]
+    achieved = upd_step * bpu * nprof / (k_stage * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    # end to end through the C ABI with host buffers
+    pinned = torch.empty(s.state_bytes(), dtype=torch.uint8, pin_memory=True)
+    s.get_state_all_ptr(pinned.data_ptr(), to_host=True)
+    nrows = sum(8 * i.Nz for i in inst)
+    out_host = torch.empty(nrows, dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(3, min(100, a.steps // 30))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state_all_ptr(pinned.data_ptr(), from_host=True)
+        s.step(1)
+        s.moments_all_ptr(out_host.data_ptr())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    s.close()
+    # to the steady state from rest, one batch, device-side retirement
+    budget = 60000
+    s = Solver(inst, precision=prec)
+    if "V" in tl:
+        s.set_tiling(tl["V"], tl["ZT"], tl["fuse"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = s.run_to_steady(1e-8, max_steps=budget, check_every=500, raise_on_fail=False)
+    wall = time.perf_counter() - t0
+    res = [s.residual(b) for b in range(len(inst))]
+    conv = [r < 1e-8 for r in res]
+    s.close()
+    line = {
+        "metric": "cell x velocity updates/s (RK-3 steps)", "value": upd_step * a.steps / (ms * 1e-3),
+        "unit": "updates/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": a.precision, "data": "synthetic",
+        "config": {"workload": "C4 sweep: 64 instances, seed 1702, Kn 10^U(-2,2), u_w U(0.05,1), Pr 2/3, "
+                               "T^omega / Sutherland (0.27, 0.52), Nz 32-512, Qx 4-16, Qy 4, Qz 4-48, "
+                               "N_eq 4, uniform cells, own CFL step each",
+                   "updates_per_step": upd_step,
+                   "l2": "inputs larger than L2 (d and two increments of %d MiB each)" % (
+                       upd_step * (4 if a.precision == "f32" else 8) >> 20),
+                   "tiling": {"V": tl["V"], "ZT": tl["ZT"], "fused_finalise": tl["fuse"],
+                              "chosen_by": tuned.get("source", "autotune.py")}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "kernel": "stage_kernel", "algorithmic_bytes_per_update_step": bpu,
+                     "stage_kernel_ms_per_step": k_stage / nprof, "finalize_ms_per_step": k_fin / nprof},
+        "e2e": {"value": upd_step * e2e_steps / e2e_s, "unit": "updates/s",
+                "h2d_bytes_per_step": sum(i.Nz * i.Q for i in inst) * (6 if a.precision == "f32" else 8),
+                "d2h_bytes_per_step": nrows * 8},
+        "to_steady": {"tol": 1e-8, "step_budget": budget, "wall_s": wall, "converged": int(sum(conv)),
+                      "steps": [int(x) for x in steps],
+                      "not_converged": [{"inst": b, "Kn": ps[b]["Kn"], "Nz": ps[b]["Nz"], "R": res[b]}
+                                        for b in range(len(inst)) if not conv[b]]},
+        "gpu_launches": {0: 6, 1: 3, 2: 12}[tl["fuse"]] * a.steps,
+        "clocks": clk.summary(),
+    }
+    if not a.no_cpu_baseline:
+        mid = sorted(range(len(ps)), key=lambda b: ps[b]["Nz"] * ps[b]["Qx"] * ps[b]["Qz"])[len(ps) // 2]
+        line["cpu_baseline"] = cpu_baseline(ps[mid])
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
     if a.workload in ("tables", "luo"):
         return run_small(a)
+    if a.workload == "sweep":
+        return run_sweep(a)
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -332,14 +453,17 @@ def main():
     from paper_1702_01335_gb300 import LBS_FP32, LBS_FP64, Instance, Solver
     from paper_1702_01335_gb300.autotune import DEFAULT_CACHE, autotune
     prec = LBS_FP32 if a.precision == "f32" else LBS_FP64
-    inst = [Instance(**W.C2)] * a.batch
+    if a.workload == "c3x32":
+        inst = [Instance(**W.C3)] * (a.batch if a.batch != BATCH else 32)
+    else:
+        inst = [Instance(**W.C2)] * a.batch
     s = Solver(inst, precision=prec)
     if a.tiling:
         V, ZT, F = (int(x) for x in a.tiling.split(","))
         s.set_tiling(V, ZT, F)
         tuned = {"V": V, "ZT": ZT, "fuse": F, "source": "--tiling"}
     else:
-        tuned = autotune(s, candidates=tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (8, 12, 16, 24)
+        tuned = autotune(s, candidates=tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (8, 10, 12, 16, 24)
                                              for F in (0, 1, 2)), steps=3,
                          cache_file=a.tuning_cache or DEFAULT_CACHE)
     st = s.torch_stream()
@@ -376,8 +500,16 @@ def main():
     if tuned["fuse"] == 2:
         s.set_tiling(tuned["V"], tuned["ZT"], 2)
     bpu = BYTES_PER_UPDATE[a.precision]
-    achieved = upd_step * bpu * nprof / (k_stage * 1e-3) / 1e9
-    peak, peak_kind = peaks()
+    if a.precision == "f64":
+        # the FP64 solver is bound by the FP64 pipe: its rate against the measured FMA rate
+        from paper_1702_01335_gb300.lbs import probe_fma_rate
+        f64_rate, f32_rate = probe_fma_rate()
+        achieved = upd_step * FP64_FLOPS_PER_UPDATE_STEP * nprof / (k_stage * 1e-3) / 1e12
+        peak, peak_kind = f64_rate / 1e12, "measured by lbs_probe_fma_rate (FP64 FMA chains, CUDA events)"
+    else:
+        achieved = upd_step * bpu * nprof / (k_stage * 1e-3) / 1e9
+        peak, peak_kind = peaks()
+        peak_kind += " (MEASURED_PEAKS.json hbm_gbs)"
 
     # ---- end to end through the C ABI with host buffers
     pinned = torch.empty(s.state_bytes(), dtype=torch.uint8, pin_memory=True)
@@ -404,13 +536,32 @@ def main():
             traffic = d["bytes_per_step_per_update"] * upd_step / 3.0
 
     if rank == 0:
+        wl = ("C3 high Kn: Kn=100 u_w=0.05 T_w=1 Pr=2/3 mu~T^0.5 Nz=256 uniform Q=16x4x(2x64)=8192 N_eq=4"
+              if a.workload == "c3x32" else
+              "C2 Shakhov Maxwell molecules Kn=1 u_w=0.5 T_w=1 Pr=2/3 Nz=128 A=0.98 Q=8x8x(2x16)=2048 N_eq=4")
+        if a.precision == "f64":
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                    "fp32_fma_rate_tflops": f32_rate / 1e12,
+                    "flops_per_update_step": FP64_FLOPS_PER_UPDATE_STEP,
+                    "hbm_gbs_at_64_bytes_per_update": upd_step * bpu * nprof / (k_stage * 1e-3) / 1e9}
+        else:
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind}
+        roof.update({"kernel": "stage_kernel (3 launches per step%s)" % {
+                         0: "", 1: ", finalisation folded in",
+                         2: "; timed with the batch unsplit, the tuned run steps its halves on "
+                            "two streams"}[tuned["fuse"]],
+                     "algorithmic_bytes_per_update_step": bpu,
+                     "stage_kernel_ms_per_step": k_stage / nprof,
+                     "finalize_ms_per_step": k_fin / nprof,
+                     "profiled_step_ms": k_step / nprof})
         line = {
             "metric": "cell x velocity updates/s (RK-3 steps)",
             "value": value, "unit": "updates/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": a.precision, "data": "synthetic",
-            "config": {"workload": "C2 Shakhov Maxwell molecules Kn=1 u_w=0.5 T_w=1 Pr=2/3 "
-                                   "Nz=128 A=0.98 Q=8x8x(2x16)=2048 N_eq=4",
+            "config": {"workload": wl,
                        "batch_per_gpu": a.batch, "state_bytes": s.state_bytes(),
                        "l2": "inputs larger than L2 (d and two stage increments of %d MiB each)" % (
                            upd_step * (4 if a.precision == "f32" else 8) >> 20),
@@ -418,17 +569,7 @@ def main():
                        "tiling": {"V": tuned["V"], "ZT": tuned["ZT"], "fused_finalise": tuned["fuse"],
                                   "chosen_by": tuned.get("source", "autotune.py (CUDA-event timing of "
                                                                    "candidates, cached per kernel hash)")}},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                         "kernel": "stage_kernel (3 launches per step%s)" % {
-                             0: "", 1: ", finalisation folded in",
-                             2: "; timed with the batch unsplit, the tuned run steps its halves on "
-                                "two streams"}[tuned["fuse"]],
-                         "algorithmic_bytes_per_update_step": bpu,
-                         "stage_kernel_ms_per_step": k_stage / nprof,
-                         "finalize_ms_per_step": k_fin / nprof,
-                         "profiled_step_ms": k_step / nprof},
+            "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "updates/s",
                     "h2d_bytes_per_step": s.state_bytes(), "d2h_bytes_per_step": nprof_rows * 8,
                     "what": "lbs_set_state(all, pinned host) + lbs_step(1) + lbs_moments(all, host) "
@@ -437,8 +578,8 @@ def main():
             "clocks": clk.summary(),
         }
         if not a.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline()
-        if not a.no_steady and world == 1:
+            line["cpu_baseline"] = cpu_baseline(W.C3 if a.workload == "c3x32" else W.C2)
+        if not a.no_steady and world == 1 and a.workload == "c2":
             line["time_to_steady"] = time_to_steady()
         print(json.dumps(line), flush=True)
     s.close()

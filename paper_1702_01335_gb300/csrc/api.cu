@@ -22,7 +22,7 @@ cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int nins
                             cudaStream_t st);
 cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,
                         cudaStream_t st);
-size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int nhx, int nhy, int npz);
+size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride);
 }  // namespace lbs
 
 using namespace lbs;
@@ -183,16 +183,16 @@ static void build_tiles(lbs_solver* h, std::vector<Tile>& tiles)
         }
         I.nzm_max = nzm_max;
         const int G = I.Qx + I.Qy + nzm_max;
-        const int nhx = I.Qx * (I.Nx + 1), nhy = I.Qy * (I.Ny + 1), npz = I.Qz * (I.Nzq + 1);
+        const int rs = rec_stride_of(I.Qx, I.Qy, I.Qz);
         // z-tiles of about ZT cells, at least 3 cells each, within the shared-memory budget
         int zt = std::max(3, std::min(h->ZT, kMaxZT));
-        while (zt > 3 && stage_smem_bytes(h->fp32, h->V, zt, G, 3, nhx, nhy, npz) > kSmemBudget) --zt;
+        while (zt > 3 && stage_smem_bytes(h->fp32, h->V, zt, G, 3, rs) > kSmemBudget) --zt;
         int nzt = std::min((I.Nz + zt - 1) / zt, I.Nz / 3);
         nzt = std::max(nzt, 1);
         const int base = I.Nz / nzt, rem = I.Nz % nzt;
         const int zmax = base + (rem ? 1 : 0);
         I.nzt = nzt;
-        smem = std::max(smem, stage_smem_bytes(h->fp32, h->V, zmax, G, 3, nhx, nhy, npz));
+        smem = std::max(smem, stage_smem_bytes(h->fp32, h->V, zmax, G, 3, rs));
         for (int c = 0; c < I.nchunks; ++c) {
             int z0 = 0;
             for (int t = 0; t < nzt; ++t) {
@@ -405,26 +405,10 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
                     }
         if (half) D.frest_bot = 0.0;  // no wall below a half channel
         D.wait_limit = kWaitLimit;
-        // weighted sums of the stored basis tables (exactly delta_l0 before rounding)
-        {
-            const std::vector<double> Hx = rounded<T>(t.Hx), Hy = rounded<T>(t.Hy), Pz = rounded<T>(t.Pz);
-            for (int l = 0; l <= kMaxN; ++l) D.wsum[0][l] = D.wsum[1][l] = D.wsum[2][l] = D.wsum[3][l] = 0.0;
-            for (int l = 0; l <= I.Nx; ++l)
-                for (int i = 0; i < I.Qx; ++i) D.wsum[0][l] += wx[i] * Hx[i * (I.Nx + 1) + l];
-            for (int l = 0; l <= I.Ny; ++l)
-                for (int j = 0; j < I.Qy; ++j) D.wsum[1][l] += wy[j] * Hy[j * (I.Ny + 1) + l];
-            if (I.reduced) {  // the mass sum of R_SCALE counts phi (factor a_0) only
-                D.wsum[1][0] = 1.0;
-                D.wsum[1][1] = 0.0;
-            }
-            for (int l = 0; l <= I.Nzq; ++l)
-                for (int m = 0; m < I.Qz; ++m) D.wsum[2][l] += wz[m] * Pz[m * (I.Nzq + 1) + l];
-            for (int l = 0; l <= I.Nzq; ++l) D.wsum[3][l] = D.wsum[2][l];
-        }
         // memory layout
         Off& o = off[b];
         const size_t es = sizeof(T);
-        o.Hx = pool.take(t.Hx.size() * es); o.Hy = pool.take(t.Hy.size() * es); o.Pz = pool.take(t.Pz.size() * es);
+        o.Hx = pool.take(t.Hx.size() * 8); o.Hy = pool.take(t.Hy.size() * 8); o.Pz = pool.take(t.Pz.size() * 8);
         o.alpha = pool.take(t.alpha.size() * 8); o.beta = pool.take(t.beta.size() * 8);
         o.px = pool.take(I.Qx * es); o.py = pool.take(I.Qy * es); o.xi = pool.take(I.Qz * es);
         o.wx = pool.take(I.Qx * es); o.wy = pool.take(I.Qy * es); o.wz = pool.take(I.Qz * es);
@@ -432,7 +416,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         o.gwz = pool.take(2 * I.Qz * es); o.idz = pool.take(Nz * es);
         const size_t nf = (size_t)Nz * I.Q;
         o.F2 = pool.take(nf * es);  // F0, F1, L0: below
-        o.rec = pool.take((size_t)Nz * kRecStride * es);
+        o.rec = pool.take((size_t)Nz * rec_stride_of(I.Qx, I.Qy, I.Qz) * es);
         const size_t maxch = 2 * ((I.Q / 2 + kThreads - 1) / kThreads);  // chunks at V = 1, the finest tiling
         o.partial = pool.take(maxch * Nz * kNMom * 8);
         o.flux = pool.take(maxch * 2 * 8);
@@ -493,7 +477,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         const Off& o = off[b];
         const Tables& t = tb[b];
         const InstHost& I = h->ih[b];
-        put<T>(img, o.Hx, t.Hx); put<T>(img, o.Hy, t.Hy); put<T>(img, o.Pz, t.Pz);
+        put<double>(img, o.Hx, t.Hx); put<double>(img, o.Hy, t.Hy); put<double>(img, o.Pz, t.Pz);
         put<double>(img, o.alpha, t.alpha); put<double>(img, o.beta, t.beta);
         put<T>(img, o.px, t.px); put<T>(img, o.py, t.py); put<T>(img, o.xi, t.xi);
         put<T>(img, o.wx, t.wx); put<T>(img, o.wy, t.wy); put<T>(img, o.wz, t.wz);
@@ -503,9 +487,9 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
                   // the zeros of the image, with residual 0 and F0 holding the state
         *reinterpret_cast<int*>(img.data() + o.active) = 1;
         InstDev& D = h->idev[b];
-        D.Hx = P + o.Hx;
-        D.Hy = P + o.Hy;
-        D.Pz = P + o.Pz;
+        D.Hx = reinterpret_cast<const double*>(P + o.Hx);
+        D.Hy = reinterpret_cast<const double*>(P + o.Hy);
+        D.Pz = reinterpret_cast<const double*>(P + o.Pz);
         D.alpha = reinterpret_cast<const double*>(P + o.alpha);
         D.beta = reinterpret_cast<const double*>(P + o.beta);
         D.px = P + o.px; D.py = P + o.py; D.xi = P + o.xi; D.wx = P + o.wx; D.wy = P + o.wy; D.wz = P + o.wz;
@@ -527,6 +511,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         D.zcount = reinterpret_cast<int*>(P + o.zcount);
         D.icount = reinterpret_cast<int*>(P + o.icount);
         D.nzt = I.nzt;
+        D.rec_stride = rec_stride_of(I.Qx, I.Qy, I.Qz);
     }
     choose_finalize(h);
     std::memcpy(img.data() + inst_off, h->idev.data(), sizeof(InstDev) * h->ninst);

@@ -59,16 +59,13 @@ __global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ in
 {
     const InstDev& I = insts[inst];
     const int cell = blockIdx.x;
-    const T* rc = static_cast<const T*>(I.rec) + (size_t)cell * kRecStride;
+    const T* rc = static_cast<const T*>(I.rec) + (size_t)cell * I.rec_stride;
     T* F = static_cast<T*>(*I.cur ? I.F1 : I.F0) + (size_t)cell * I.Q;
     for (int k = threadIdx.x; k < I.Q; k += blockDim.x) {
         const int j = k % I.Qy, i = (k / I.Qy) % I.Qx, zm = k / I.QxQy;
         const int sg = zm >= I.Qz, m = zm - sg * I.Qz;
-        T gx = 0, gy = 0, gz = 0;
-        for (int l = 0; l <= I.Nx; ++l) gx += rc[R_AX + l] * ld<T>(I.Hx, i * (I.Nx + 1) + l);
-        for (int l = 0; l <= I.Ny; ++l) gy += rc[R_AY + l] * ld<T>(I.Hy, j * (I.Ny + 1) + l);
-        for (int l = 0; l <= I.Nzq; ++l) gz += rc[(sg ? R_BM : R_BP) + l] * ld<T>(I.Pz, m * (I.Nzq + 1) + l);
-        gx = rc[R_SCALE1] + (T(1) + rc[R_SCALE1]) * gx;
+        const T gx = rc[R_SCALE1] + (T(1) + rc[R_SCALE1]) * rc[R_DX + i];
+        const T gy = rc[R_DX + I.Qx + j], gz = rc[R_DX + I.Qx + I.Qy + zm];
         const T x = ld<T>(I.xi, m);
         const T ex = ld<T>(I.px, i) - rc[R_UX], ey = ld<T>(I.py, j) - rc[R_UY], ez = (sg ? -x : x) - rc[R_UZ];
         const T S = I.reduced ? rc[R_CS] * ((ex * ex + ez * ez) * rc[R_I5T] - (j ? T(0.4) : T(0.8))) *
@@ -82,10 +79,10 @@ __global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ in
 }
 
 // ---- host launchers ---------------------------------------------------------
-size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int nhx, int nhy, int npz)
+size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride)
 {
     const int KC = kThreads * V;
-    return stage_smem(zn, KC, G, fp32 ? 4 : 8, 8, stage >= 2, nhx, nhy, npz).total;
+    return stage_smem(zn, KC, G, fp32 ? 4 : 8, 8, stage >= 2, rstride).total;
 }
 
 template <typename T>

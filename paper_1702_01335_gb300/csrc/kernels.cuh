@@ -246,23 +246,20 @@ __device__ __forceinline__ A reduce_scatter16(A (&v)[16], int lane)
 
 // shared-memory layout of a stage CTA (offsets in bytes): the staged rows of the
 // step's start state d (cells z0-3 .. z0+zn+2), the same rows of the stage input's
-// increment (stages 2 and 3), the cell records and the Hermite basis tables (all by
-// bulk copy), the evaluated per-axis factors, 1/dz, and the per-warp moment sums.
+// increment (stages 2 and 3), the cell records (all by bulk copy), the per-axis
+// factors of this chunk's nodes, 1/dz, and the per-warp moment sums.
 struct StageSmem {
-    size_t fin, dr, rec, hx, hy, pz, g, idz, red, total;
+    size_t fin, dr, rec, g, idz, red, total;
 };
 __host__ __device__ inline size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
 __host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize, int asize, bool withD,
-                                                int nhx, int nhy, int npz)
+                                                int rstride)
 {
     StageSmem L;
     size_t o = 0;
     L.fin = o; o += (size_t)(zn + 6) * KC * esize;
     L.dr = o; o += withD ? (size_t)(zn + 6) * KC * esize : 0;  // directly after fin (row offset (zn+6) KC)
-    L.rec = o; o += (size_t)zn * kRecStride * esize;
-    L.hx = o; o += pad16((size_t)nhx * esize);
-    L.hy = o; o += pad16((size_t)nhy * esize);
-    L.pz = o; o += pad16((size_t)npz * esize);
+    L.rec = o; o += (size_t)zn * rstride * esize;
     L.g = o; o += pad16((size_t)zn * G * esize);
     L.idz = o; o += pad16((size_t)zn * esize);
     L.red = o; o += (size_t)zn * (kThreads / 32) * 16 * asize;
@@ -295,15 +292,19 @@ static __device__ __forceinline__ float lo_decode(unsigned short q, float hi)
 }
 
 // ----------------------------------------------------------------------------
-// Cell record from a macroscopic state: scalars and the coefficients a_l, b_l
-// of the truncated Hermite equilibrium (Sec. III, Eqs. fyz, Fmn_def), FP64.
-// Returns false for a non-finite or non-positive state (a neutral state is
-// written instead).
+// Cell record of a macroscopic state: the scalars and the per-node factors of the
+// truncated Hermite equilibrium (Sec. III, Eqs. fyz, Fmn_def), computed in FP64 (the
+// half-range coefficients cancel strongly for N >= 4) and rounded once.  A factor's
+// deviation from 1 is sum_l (c_l - r_l) basis_l(node) with the rest state's
+// coefficients r: (1, 0, 0, ...) on x and y, (1, 1) on the reduced model's y (factors 1
+// and T), (1/2, 0, ...) on each half range of z, for which sum_l r_l basis_l = 1 at every
+// node.  R_SCALE makes the discrete equilibrium carry exactly n: in exact arithmetic
+// sum_i w_i Gx = 1, sum_j w_j Gy = 1 and the sum over both half ranges of w Gz = 1
+// (orthogonality of the bases); with the factors rounded to the storage type the sums
+// miss by a few ulps of the same sign every step, which would let FP32 runs drift in
+// mass, so the sums are taken over the stored values.  Returns false for a non-finite
+// or non-positive state (a neutral state is written instead).
 // ----------------------------------------------------------------------------
-// Cell record of a macroscopic state: the scalars and the coefficients a_l, b_l
-// of the truncated Hermite equilibrium (Sec. III, Eqs. fyz, Fmn_def), computed in
-// FP64 (the half-range ones cancel strongly for N >= 4).  Returns false for a
-// non-finite or non-positive state (a neutral state is written instead).
 template <typename T>
 __device__ bool write_record(const InstDev& I, int cell, double n, double in, const double* u, double T_,
                              const double* q)
@@ -314,57 +315,68 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     for (int a = 0; a < 3; ++a) bad |= !isfinite(u[a]) || !isfinite(q[a]);
     const double nn = bad ? 1.0 : n, inn = bad ? 1.0 : in, Tc = bad ? 1.0 : T_;
     const double u0 = bad ? 0.0 : u[0], u1 = bad ? 0.0 : u[1], u2 = bad ? 0.0 : u[2];
-    T* rec = static_cast<T*>(I.rec) + (size_t)cell * kRecStride;
+    T* rec = static_cast<T*>(I.rec) + (size_t)cell * I.rec_stride;
     const double iT = 1.0 / Tc;
     rec[R_N] = T(nn); rec[R_UX] = T(u0); rec[R_UY] = T(u1); rec[R_UZ] = T(u2); rec[R_T] = T(Tc);
     rec[R_QX] = T(bad ? 0.0 : q[0]); rec[R_QY] = T(bad ? 0.0 : q[1]); rec[R_QZ] = T(bad ? 0.0 : q[2]);
     rec[R_ITAU] = T(inv_relax_time(I.visc_law, I.iKn, I.visc_param, I.isuth, nn, Tc, iT));
     rec[R_CS] = T((1.0 - I.Pr) * inn * iT * iT);
     rec[R_I5T] = T(0.2 * iT);
-    // R_SCALE multiplies the x factors so that the discrete equilibrium carries
-    // exactly n: in exact arithmetic sum_i wx Gx = 1, sum_j wy Gy = 1 and the sum
-    // over both half ranges of wz Gz = 1 (orthogonality of the bases); with
-    // coefficients and bases rounded to the storage type the sums miss by a few
-    // ulps of the same sign every step, which would let FP32 runs drift in mass.
-    // The sums are sum_l c_l W_l with the stored coefficients c_l and the
-    // weighted sums W_l of the stored basis tables (computed at set-up).
-    // The slots hold c_l - r_l, the coefficients minus those of the rest state r (n = 1,
-    // u = 0, T = 1): r = (1, 0, 0, ...) on x and y, (1, 1) on the reduced model's y
-    // (factors 1 and T), (1/2, 0, 0, ...) on each half range of z; sum_l r_l basis_l = 1 at
-    // every node.  The R_SCALE sums use the implied coefficients r_l + slot_l.
+    const int Qx = I.Qx, Qy = I.Qy, Qz = I.Qz;
+    T* dx = rec + R_DX;
+    T* dy = dx + Qx;
+    T* dz = dy + Qy;
     double c[kMaxN + 1], cm[kMaxN + 1], s[3];
+    // x: a_l, l >= 1, against He_l / l!
     full_coeffs(u0, Tc, I.Nx, c);
     s[0] = 0.0;
+    for (int i = 0; i < Qx; ++i) {
+        const double* h = I.Hx + i * (I.Nx + 1);
+        double g = 0.0;
 #pragma unroll
-    for (int l = 0; l <= kMaxN; ++l) {
-        const double r = l == 0 ? 1.0 : 0.0;
-        const T v = l <= I.Nx ? T(c[l] - r) : T(0);
-        rec[R_AX + l] = v;
-        if (l <= I.Nx) s[0] += (r + double(v)) * I.wsum[0][l];
+        for (int l = 1; l <= kMaxN; ++l)
+            if (l <= I.Nx) g += c[l] * h[l];
+        const T v = T(g);
+        dx[i] = v;
+        s[0] += double(ld<T>(I.wx, i)) * (1.0 + double(v));
     }
-    if (I.reduced) {  // y factors of phi and chi: 1 and T (basis: the identity on j)
-        c[0] = 1.0;
-        c[1] = Tc;
+    // y: the reduced model's factors 1 and T (phi and chi; its mass is phi's alone)
+    s[1] = 0.0;
+    if (I.reduced) {
+        dy[0] = T(0);
+        dy[1] = T(Tc - 1.0);
+        s[1] = 1.0;
     } else {
         full_coeffs(u1, Tc, I.Ny, c);
-    }
-    s[1] = 0.0;
+        for (int j = 0; j < Qy; ++j) {
+            const double* h = I.Hy + j * (I.Ny + 1);
+            double g = 0.0;
 #pragma unroll
-    for (int l = 0; l <= kMaxN; ++l) {
-        const double r = l == 0 || (l == 1 && I.reduced) ? 1.0 : 0.0;
-        const T v = l <= I.Ny ? T(c[l] - r) : T(0);
-        rec[R_AY + l] = v;
-        if (l <= I.Ny) s[1] += (r + double(v)) * I.wsum[1][l];
+            for (int l = 1; l <= kMaxN; ++l)
+                if (l <= I.Ny) g += c[l] * h[l];
+            const T v = T(g);
+            dy[j] = v;
+            s[1] += double(ld<T>(I.wy, j)) * (1.0 + double(v));
+        }
     }
+    // z: b_l on each half range against pi_l / h_l, b_0 - 1/2 in place of b_0
     half_coeffs_pm(u2, Tc, iT, I.Nzq, I.alpha, I.beta, c, cm);
+    c[0] -= 0.5;
+    cm[0] -= 0.5;
     s[2] = 0.0;
+    for (int m = 0; m < Qz; ++m) {
+        const double* h = I.Pz + m * (I.Nzq + 1);
+        double gp = 0.0, gm = 0.0;
 #pragma unroll
-    for (int l = 0; l <= kMaxN; ++l) {
-        const double r = l == 0 ? 0.5 : 0.0;
-        const T vp = l <= I.Nzq ? T(c[l] - r) : T(0), vm = l <= I.Nzq ? T(cm[l] - r) : T(0);
-        rec[R_BP + l] = vp;
-        rec[R_BM + l] = vm;
-        if (l <= I.Nzq) s[2] += (r + double(vp)) * I.wsum[2][l] + (r + double(vm)) * I.wsum[3][l];
+        for (int l = 0; l <= kMaxN; ++l)
+            if (l <= I.Nzq) {
+                gp += c[l] * h[l];
+                gm += cm[l] * h[l];
+            }
+        const T vp = T(gp), vm = T(gm);
+        dz[m] = vp;
+        dz[Qz + m] = vm;
+        s[2] += double(ld<T>(I.wz, m)) * ((1.0 + double(vp)) + (1.0 + double(vm)));
     }
     rec[R_SCALE1] = T(nn / (s[0] * s[1] * s[2]) - 1.0);
     return !bad;
@@ -393,7 +405,7 @@ static __device__ __forceinline__ bool store_cell(const InstDev& I, int cell, co
 template <typename T>
 __device__ __forceinline__ void moment_origin(const InstDev& I, int cell, int stage, double* ur)
 {
-    const T* rc = static_cast<const T*>(I.rec) + (size_t)cell * kRecStride;
+    const T* rc = static_cast<const T*>(I.rec) + (size_t)cell * I.rec_stride;
     ur[0] = stage == 3 ? double(rc[R_UX]) : 0.0;
     ur[1] = stage == 3 ? double(rc[R_UY]) : 0.0;
     ur[2] = stage == 3 ? double(rc[R_UZ]) : 0.0;
@@ -450,10 +462,10 @@ __device__ void finalize_cell(const InstDev& I, int cell, int stage)
 // FP64 instructions issue at a small fraction of the FP32 rate, so with one thread
 // per cell a small batch waits on each cell's long FP64 chain; here lane a sums
 // moment a, the two halves of the warp run the x / y coefficient recurrences and
-// the p_z > 0 / p_z < 0 half-range tables side by side, and within a half lane k
+// the p_z > 0 / p_z < 0 half-range tables side by side, within a half lane k
 // carries column k of the table J_{l,k} (one shuffle per row instead of the whole
-// triangle in one thread).  Large batches keep one thread per cell, where every
-// lane has a cell of its own.
+// triangle in one thread), and the nodes' factors are spread over the lanes.  Large
+// batches keep one thread per cell, where every lane has a cell of its own.
 template <typename T>
 __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& st, int lane)
 {
@@ -468,7 +480,7 @@ __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& s
     for (int a = 0; a < 3; ++a) bad |= !isfinite(st.u[a]) || !isfinite(st.q[a]);
     const double nn = bad ? 1.0 : st.n, inn = bad ? 1.0 : st.in, Tc = bad ? 1.0 : st.T;
     const double u0 = bad ? 0.0 : st.u[0], u1 = bad ? 0.0 : st.u[1], u2 = bad ? 0.0 : st.u[2];
-    T* rec = static_cast<T*>(I.rec) + (size_t)cell * kRecStride;
+    T* rec = static_cast<T*>(I.rec) + (size_t)cell * I.rec_stride;
     const double iT = 1.0 / Tc;
     if (lane == 0) {
         rec[R_N] = T(nn); rec[R_UX] = T(u0); rec[R_UY] = T(u1); rec[R_UZ] = T(u2); rec[R_T] = T(Tc);
@@ -477,26 +489,15 @@ __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& s
         rec[R_CS] = T((1.0 - I.Pr) * inn * iT * iT);
         rec[R_I5T] = T(0.2 * iT);
     }
+    const int Qx = I.Qx, Qy = I.Qy, Qz = I.Qz;
+    T* dx = rec + R_DX;
+    T* dy = dx + Qx;
+    T* dz = dy + Qy;
     const int h = lane >> 4, k = lane & 15;  // half of the warp, lane within it
-    // x (h = 0) and y (h = 1) coefficients a_l (Eq. fyz); lane k keeps a_k
+    // x (h = 0) and y (h = 1) coefficients a_l (Eq. fyz), in every lane of the half
     double c[kMaxN + 1];
     const int Nh = h ? I.Ny : I.Nx;
     full_coeffs(h ? u1 : u0, Tc, Nh, c);
-    if (h && I.reduced) {  // y factors of phi and chi: 1 and T (basis: the identity on j)
-        c[0] = 1.0;
-        c[1] = Tc;
-    }
-    double ck = 0.0;
-#pragma unroll
-    for (int l = 0; l <= kMaxN; ++l)
-        if (l == k) ck = c[l];
-    double sxy = 0.0;  // this lane's term of sum_l c_l W_l (the R_SCALE sums, as in write_record)
-    if (k <= kMaxN) {
-        const double r = k == 0 || (k == 1 && h && I.reduced) ? 1.0 : 0.0;  // rest coefficients
-        const T v = k <= Nh ? T(ck - r) : T(0);
-        rec[(h ? R_AY : R_AX) + k] = v;
-        if (k <= Nh) sxy = (r + double(v)) * I.wsum[h][k];
-    }
     // z: half h = 0 the p_z > 0 range (drift u2), h = 1 the p_z < 0 range written in
     // xi = -p_z >= 0 (drift -u2).  Both share g(0) and one erfc (erfc(x) + erfc(-x) = 2).
     const int K = I.Nzq;
@@ -533,26 +534,67 @@ __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& s
             b[l + 1] = Jc;
         }
     }
-    double sz = 0.0, sz1 = 0.0;  // two interleaved partial sums: half the dependent adds
-    if (k == 0) {
+    // column 0 (lanes 0 and 16) holds the two coefficient sets: give them to every lane,
+    // b_0 - 1/2 in place of b_0 (the rest state's coefficient)
+    double bp[kMaxN + 1], bm[kMaxN + 1];
 #pragma unroll
-        for (int l = 0; l <= kMaxN; ++l) {
-            const double r = l == 0 ? 0.5 : 0.0;
-            const T v = l <= K ? T(b[l] - r) : T(0);
-            rec[(h ? R_BM : R_BP) + l] = v;
-            if (l <= K) {
-                if (l & 1) sz1 += (r + double(v)) * I.wsum[2 + h][l];
-                else sz += (r + double(v)) * I.wsum[2 + h][l];
-            }
+    for (int l = 0; l <= kMaxN; ++l) {
+        bp[l] = __shfl_sync(0xffffffffu, b[l], 0) - (l == 0 ? 0.5 : 0.0);
+        bm[l] = __shfl_sync(0xffffffffu, b[l], 16) - (l == 0 ? 0.5 : 0.0);
+    }
+    // the nodes' factors: x over the lanes of half 0, y over half 1, z over the warp;
+    // each lane's terms of the R_SCALE sums
+    double sxy = 0.0, sz = 0.0;
+    if (h == 0) {
+        for (int i = k; i < Qx; i += 16) {
+            const double* hb = I.Hx + i * (I.Nx + 1);
+            double g = 0.0;
+#pragma unroll
+            for (int l = 1; l <= kMaxN; ++l)
+                if (l <= I.Nx) g += c[l] * hb[l];
+            const T v = T(g);
+            dx[i] = v;
+            sxy += double(ld<T>(I.wx, i)) * (1.0 + double(v));
         }
-        sz += sz1;
+    } else if (I.reduced) {  // y factors of phi and chi: 1 and T; the mass is phi's alone
+        if (k == 0) {
+            dy[0] = T(0);
+            dy[1] = T(Tc - 1.0);
+            sxy = 1.0;
+        }
+    } else {
+        for (int j = k; j < Qy; j += 16) {
+            const double* hb = I.Hy + j * (I.Ny + 1);
+            double g = 0.0;
+#pragma unroll
+            for (int l = 1; l <= kMaxN; ++l)
+                if (l <= I.Ny) g += c[l] * hb[l];
+            const T v = T(g);
+            dy[j] = v;
+            sxy += double(ld<T>(I.wy, j)) * (1.0 + double(v));
+        }
+    }
+    for (int m = lane; m < Qz; m += 32) {
+        const double* hb = I.Pz + m * (I.Nzq + 1);
+        double gp = 0.0, gm = 0.0;
+#pragma unroll
+        for (int l = 0; l <= kMaxN; ++l)
+            if (l <= K) {
+                gp += bp[l] * hb[l];
+                gm += bm[l] * hb[l];
+            }
+        const T vp = T(gp), vm = T(gm);
+        dz[m] = vp;
+        dz[Qz + m] = vm;
+        sz += double(ld<T>(I.wz, m)) * ((1.0 + double(vp)) + (1.0 + double(vm)));
     }
     // R_SCALE = n / (s_x s_y s_z) (see write_record)
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) sxy += __shfl_xor_sync(0xffffffffu, sxy, o, 16);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sz += __shfl_xor_sync(0xffffffffu, sz, o);
     const double sx = __shfl_sync(0xffffffffu, sxy, 0), sy = __shfl_sync(0xffffffffu, sxy, 16);
-    const double s2 = __shfl_sync(0xffffffffu, sz, 0) + __shfl_sync(0xffffffffu, sz, 16);
-    if (lane == 0) rec[R_SCALE1] = T(nn / (sx * sy * s2) - 1.0);
+    if (lane == 0) rec[R_SCALE1] = T(nn / (sx * sy * sz) - 1.0);
     return !bad;
 }
 
@@ -704,14 +746,11 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     const int G = Qx + Qy + nzm;                     // per-cell factors held in smem
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    const int nhx = Qx * (I.Nx + 1), nhy = Qy * (I.Ny + 1), npz = Qz * (I.Nzq + 1);
-    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(double), kD, nhx, nhy, npz);
+    const int rstride = I.rec_stride;
+    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(double), kD, rstride);
     T* Fs = reinterpret_cast<T*>(smem_raw + L.fin);   // d rows: cells z0-3 .. z0+zn+2
     T* Ds = reinterpret_cast<T*>(smem_raw + L.dr);    // increment rows, same cells (stages 2, 3)
     T* recs = reinterpret_cast<T*>(smem_raw + L.rec); // records of cells z0 .. z0+zn-1
-    T* hxs = reinterpret_cast<T*>(smem_raw + L.hx);
-    T* hys = reinterpret_cast<T*>(smem_raw + L.hy);
-    T* pzs = reinterpret_cast<T*>(smem_raw + L.pz);
     T* gsm = reinterpret_cast<T*>(smem_raw + L.g);
     T* idzs = reinterpret_cast<T*>(smem_raw + L.idz);
     double* red = reinterpret_cast<double*>(smem_raw + L.red);  // per-warp moment sums, summed in FP64
@@ -727,10 +766,10 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     T* Fout = STAGE == 2 ? static_cast<T*>(I.F2) : Og;
     const int s_lo = max(0, z0 - 3), s_hi = min(Nz - 1, z0 + zn + 2);
 
-    // ---- 1. stage the input rows, the cell records and the basis tables
-    //         (TMA bulk copies; plain loads if the rows are not 16-byte aligned)
-    const T* Rg = static_cast<const T*>(I.rec) + (size_t)z0 * kRecStride;
-    const size_t rec_bytes = (size_t)zn * kRecStride * sizeof(T);
+    // ---- 1. stage the input rows and the cell records (TMA bulk copies; plain loads
+    //         if the rows are not 16-byte aligned)
+    const T* Rg = static_cast<const T*>(I.rec) + (size_t)z0 * rstride;
+    const size_t rec_bytes = (size_t)zn * rstride * sizeof(T);
     if (I.bulk) {
         if (tid == 0) {
             mbar_init(&bar, 1);
@@ -740,19 +779,13 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         if (tid == 0) {
             const uint32_t bytes = kn * sizeof(T);
             uint32_t total = bytes * (s_hi - s_lo + 1) * (kD ? 2 : 1);
-            if (STAGE > 0)
-                total += rec_bytes + pad16(nhx * sizeof(T)) + pad16(nhy * sizeof(T)) + pad16(npz * sizeof(T));
+            if (STAGE > 0) total += rec_bytes;
             mbar_expect_tx(&bar, total);
             for (int s = s_lo; s <= s_hi; ++s) {
                 bulk_g2s(Fs + (size_t)(s - z0 + 3) * KC, Hg + (size_t)s * Q + k0, bytes, &bar);
                 if (kD) bulk_g2s(Ds + (size_t)(s - z0 + 3) * KC, Dg + (size_t)s * Q + k0, bytes, &bar);
             }
-            if (STAGE > 0) {
-                bulk_g2s(recs, Rg, rec_bytes, &bar);
-                bulk_g2s(hxs, I.Hx, pad16(nhx * sizeof(T)), &bar);  // tables are padded to 16 bytes
-                bulk_g2s(hys, I.Hy, pad16(nhy * sizeof(T)), &bar);
-                bulk_g2s(pzs, I.Pz, pad16(npz * sizeof(T)), &bar);
-            }
+            if (STAGE > 0) bulk_g2s(recs, Rg, rec_bytes, &bar);  // records are 16-byte multiples
         }
     } else {
         for (int s = s_lo; s <= s_hi; ++s)
@@ -760,12 +793,8 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 Fs[(size_t)(s - z0 + 3) * KC + kl] = Hg[(size_t)s * Q + k0 + kl];
                 if (kD) Ds[(size_t)(s - z0 + 3) * KC + kl] = Dg[(size_t)s * Q + k0 + kl];
             }
-        if (STAGE > 0) {
-            for (int e = tid; e < zn * kRecStride; e += kThreads) recs[e] = Rg[e];
-            for (int e = tid; e < nhx; e += kThreads) hxs[e] = ld<T>(I.Hx, e);
-            for (int e = tid; e < nhy; e += kThreads) hys[e] = ld<T>(I.Hy, e);
-            for (int e = tid; e < npz; e += kThreads) pzs[e] = ld<T>(I.Pz, e);
-        }
+        if (STAGE > 0)
+            for (int e = tid; e < zn * rstride; e += kThreads) recs[e] = Rg[e];
     }
     if (STAGE > 0)
         for (int c = tid; c < zn; c += kThreads) idzs[c] = ld<T>(I.inv_dz, z0 + c);
@@ -830,28 +859,21 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         return;
     }
 
-    // ---- 4a. per-cell factors of the truncated Hermite equilibrium (Sec. III) from
-    //          the staged records, as deviations from 1: dx[i] = R_SCALE Gx[i] - 1,
-    //          dy[j] = Gy[j] - 1, dz[zm] = Gz[zm] - 1 for this chunk's zm (the records
-    //          hold the coefficients minus those of the rest state)
+    // ---- 4a. per-cell factors of the truncated Hermite equilibrium (Sec. III) for this
+    //          chunk's nodes, as deviations from 1, from the staged records:
+    //          dx[i] with R_SCALE applied (R_SCALE (1 + dx) - 1), dy[j], dz[zm]
     if (STAGE > 0) {
         for (int e = tid; e < zn * G; e += kThreads) {
             const int c = e / G, r = e - c * G;
-            const T* rc = recs + (size_t)c * kRecStride;
-            T g = 0;
+            const T* rc = recs + (size_t)c * rstride;
+            T g;
             if (r < Qx) {
-                const T* h = hxs + r * (I.Nx + 1);
-                for (int l = 0; l <= I.Nx; ++l) g += rc[R_AX + l] * h[l];
                 const T s1 = rc[R_SCALE1];
-                g = s1 + (T(1) + s1) * g;
+                g = s1 + (T(1) + s1) * rc[R_DX + r];
             } else if (r < Qx + Qy) {
-                const T* h = hys + (r - Qx) * (I.Ny + 1);
-                for (int l = 0; l <= I.Ny; ++l) g += rc[R_AY + l] * h[l];
+                g = rc[R_DX + r];                               // dy[r - Qx]
             } else {
-                const int zm = zm_lo + r - Qx - Qy, sg = zm >= Qz, m = zm - sg * Qz;
-                const T* h = pzs + m * (I.Nzq + 1);
-                const T* b = rc + (sg ? R_BM : R_BP);
-                for (int l = 0; l <= I.Nzq; ++l) g += b[l] * h[l];
+                g = rc[R_DX + Qx + Qy + zm_lo + r - Qx - Qy];   // dz[zm]
             }
             gsm[e] = g;
         }
@@ -945,10 +967,21 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     const size_t orow0 = (size_t)(sgc ? z0 + zn - 1 : z0) * Q + k0;  // global offset of the first cell
     T* outp = Fout + orow0;
     unsigned short* lop = kLo && STAGE == 3 ? I.L0 + orow0 : nullptr;
+    // stage 3 (FP32): the residuals of the next cell are loaded one march step ahead, so
+    // that their global-memory latency overlaps a step's arithmetic
+    unsigned short lqn[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) lqn[v] = kLo && STAGE == 3 && ok[v] ? lop[kl[v]] : 0;
 #pragma unroll 1  // unrolling the z-march only adds instruction-cache misses
     for (int c = 0; c < zn; ++c) {
+        unsigned short lqc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            lqc[v] = lqn[v];
+            if (kLo && STAGE == 3 && ok[v] && c + 1 < zn) lqn[v] = lop[ostep + kl[v]];
+        }
         const int cc = sgc ? zn - 1 - c : c;  // the cell within the tile
-        const T* sc = recs + (size_t)cc * kRecStride;
+        const T* sc = recs + (size_t)cc * rstride;
         const T* gc = gsm + cc * G;
         const T* rn = rp + (c + 6) * rstep;
         const T* own = Fs + (size_t)(cc + 3) * KC;  // the cell's row of d
@@ -963,8 +996,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         for (int a = 0; a < 16; ++a) acc[a] = A(0);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            unsigned short lq = 0;
-            if (kLo && STAGE == 3 && ok[v]) lq = lop[kl[v]];
+            const unsigned short lq = lqc[v];
             const T wn = kD ? rn[kl[v]] + rn[doff + kl[v]] : rn[kl[v]];
             T out = w[v][3];  // the value whose moments are taken
             T ex = 0, ey = 0, ez = 0, xi2 = 0;  // xi = p - u of the cell's record
@@ -989,26 +1021,36 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 // the target's deviation from 1: (1 + dx)(1 + dy)(1 + dz)(1 + S) - 1
                 const T dx = gc[ii[v]], dy = gc[Qx + jj[v]], dz = gc[Qx + Qy + zz[v] - zm_lo];
                 const T a = dx + dy + dx * dy, b = a + dz + a * dz, tgt = b + S + b * S;
+                // the departure from the target, f - tgt: from the cell's d, increment and
+                // (stage 3, FP32) residual separately, (d - tgt) + increment + residual,
+                // so that its rounding is relative to the departure, which in the
+                // collision-dominated regime is much smaller than f itself
+                T h = f, dinc = T(0), lo = T(0);
+                if (STAGE >= 2) {
+                    h = own[kl[v]];
+                    dinc = own[doff + kl[v]];
+                }
+                if constexpr (kLo && STAGE == 3) lo = lo_decode(lq, h);
+                const T dep = STAGE >= 2 ? ((h - tgt) + dinc) + lo : f - tgt;
                 // Eq. (flux): (|p_z| (w3 + cp) - |p_z| (w2 + cm)) / dz, formed from the
                 // difference of the two upwind cells and of the two corrections, so that
                 // its rounding is relative to the divergence rather than to d.  The
                 // advection and relaxation increments nearly cancel near a steady state:
                 // combine them first.
-                const T Lv = -apz[v] * ((w[v][3] - w[v][2]) + (cp - cm[v])) * idz - (f - tgt) * itau;
+                const T Lv = -apz[v] * ((w[v][3] - w[v][2]) + (cp - cm[v])) * idz - dep * itau;
                 T st;  // the value stored
                 if (STAGE == 1) {
                     st = dt * Lv;
                     out = f + st;
                 } else if (STAGE == 2) {
-                    st = T(0.25) * (own[doff + kl[v]] + dt * Lv);
-                    out = own[kl[v]] + st;
+                    st = T(0.25) * (dinc + dt * Lv);
+                    out = h + st;
                 } else {
                     // Shu-Osher combine in increment form: F_l + 2/3 (d2 + dt L), added to the
                     // state with its rounding residual carried (FP32)
-                    const T inc = T(2.0 / 3.0) * (own[doff + kl[v]] + dt * Lv);
-                    const T h = own[kl[v]];
+                    const T inc = T(2.0 / 3.0) * (dinc + dt * Lv);
                     if constexpr (kLo) {
-                        const T t = lo_decode(lq, h) + inc;
+                        const T t = lo + inc;
                         const T h2 = h + t;
                         const T lo2 = t - (h2 - h);
                         if (ok[v]) lop[kl[v]] = lo_encode(lo2, h2);

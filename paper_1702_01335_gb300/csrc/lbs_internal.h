@@ -23,14 +23,15 @@ enum { QUAD_FULL = 0, QUAD_HALF = 1 };
 
 // Cell record (storage type T): n, ux, uy, uz, T, qx, qy, qz, 1/tau,
 // (1 - Pr)/(n T^2), 1/(5T), R_SCALE - 1 where R_SCALE = n / (discrete weighted sums of
-// the per-axis factors); then the expansion coefficients of the truncated equilibrium
-// minus those of the rest state (the populations are stored as deviations from it):
-// a_l (x), a_l (y) with a_0 - 1 = 0 in slot 0, b_l (z, p_z > 0), b_l (z, p_z < 0) with
-// b_0 - 1/2 in slot 0; kMaxN + 1 slots each.  A factor's deviation from 1 is then
-// sum_l slot_l basis_l, free of the cancellation of 1 + small - 1.
+// the per-axis factors); then the per-node factors of the truncated equilibrium as
+// deviations from the rest state's factor 1 (the populations are stored as deviations
+// from the rest state too): dx[Qx] = Gx / w - 1 (before R_SCALE), dy[Qy], dz[2 Qz]
+// (p_z > 0 nodes, then p_z < 0).  They are summed in FP64 in the finalisation and
+// rounded once to the storage type.  Records are rec_stride values apart.
 enum { R_N = 0, R_UX, R_UY, R_UZ, R_T, R_QX, R_QY, R_QZ, R_ITAU, R_CS, R_I5T, R_SCALE1 };
-constexpr int R_AX = kRecHead, R_AY = R_AX + kMaxN + 1, R_BP = R_AY + kMaxN + 1, R_BM = R_BP + kMaxN + 1;
-constexpr int kRecStride = R_BM + kMaxN + 1;
+constexpr int R_DX = kRecHead;
+// record length of an instance, rounded up to 16 bytes in either storage type
+inline int rec_stride_of(int Qx, int Qy, int Qz) { return (kRecHead + Qx + Qy + 2 * Qz + 3) & ~3; }
 
 // Everything a kernel needs to know about one instance (lives in device memory).
 struct InstDev {
@@ -45,8 +46,7 @@ struct InstDev {
     double Kn, visc_param, Pr, dt, tol;
     double iKn, isuth;            // 1 / Kn; Sutherland: 1 / (1 + S)
     double Dtop, Dbot;            // sum over incoming velocities of w p_z Gw (n_w = 1)
-    double wsum[4][kMaxN + 1];    // sum_i w_i basis_l(p_i) of the stored (rounded) tables:
-                                  // x, y, z (p_z > 0), z (p_z < 0); 1, 0, 0, ... exactly
+    int rec_stride;               // values per cell record
     double mrest[kNMom];          // raw moments of the rest state f = w (the stored weights and
                                   // nodes): the partials hold sums over the deviations only
     double frest_bot, frest_top;  // outgoing wall flux of the rest state (sum w p_z over the
@@ -55,7 +55,7 @@ struct InstDev {
     double ext_top[2][3];         // ghost Nz+1 <- (Nz, Nz-1, Nz-2); Nz+2 <- (Nz+1, Nz, Nz-1)
     double ext_bot[2][3];         // ghost 0 <- (1, 2, 3); ghost -1 <- (0, 1, 2)
     // tables
-    const void *Hx, *Hy, *Pz;     // storage type, [Q_a][N_a + 1] basis values He_l/l!, pi_l/h_l
+    const double *Hx, *Hy, *Pz;   // FP64, [Q_a][N_a + 1] basis values He_l/l!, pi_l/h_l
     const double *alpha, *beta;   // half-range recurrence, [kMaxN + 2]
     // storage-typed tables (float or double)
     const void *px, *py, *xi, *wx, *wy, *wz;
@@ -72,7 +72,7 @@ struct InstDev {
     void *F0, *F1, *F2;
     unsigned short *L0;           // [Nz][Q], FP32 storage only
     int *cur;                     // [1]
-    void *rec;                    // [Nz][kRecStride]
+    void *rec;                    // [Nz][rec_stride]
     double *partial;              // [nchunks][kNMom][Nz]
     double *flux_part;            // [nchunks][2]: bottom, top outgoing flux
     double *nw;                   // [2]: bottom, top wall density
