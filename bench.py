@@ -567,6 +567,9 @@ def main():
                            upd_step * (4 if a.precision == "f32" else 8) >> 20),
                        "parallelism": "replicas, independent batches per GPU",
                        "tiling": {"V": tuned["V"], "ZT": tuned["ZT"], "fused_finalise": tuned["fuse"],
+                                  "finalise_layout": {1: "thread per cell", 2: "warp per cell"}.get(
+                                      tuned.get("fin"), "default"),
+                                  "finalise_layout_ms_per_step": tuned.get("fin_ms_per_step"),
                                   "chosen_by": tuned.get("source", "autotune.py (CUDA-event timing of "
                                                                    "candidates, cached per kernel hash)")}},
             "roofline": roof,

@@ -69,12 +69,15 @@ def _load(path):
 
 
 def autotune(solver, candidates=CANDIDATES, steps=3, cache_file=None, verbose=False):
-    """Pick the fastest (V, ZT, fuse) for solver's batch; returns {"V", "ZT", "fuse", "ms_per_step", "table"}."""
+    """Pick the fastest (V, ZT, fuse) for solver's batch, then the faster finalisation
+    layout for it; returns {"V", "ZT", "fuse", "fin", "ms_per_step", "table", ...}."""
     key = signature(solver)
     disk = _load(cache_file)
     hit = _cache.get(key) or disk.get(key)
     if hit:
         solver.set_tiling(hit["V"], hit["ZT"], hit["fuse"])
+        if "fin" in hit:
+            solver.set_finalize(hit["fin"])
         return hit
     scratch = Solver(solver.instances, precision=solver.precision)
     table = []
@@ -95,9 +98,22 @@ def autotune(solver, candidates=CANDIDATES, steps=3, cache_file=None, verbose=Fa
     if not table:
         raise ValueError("no valid tiling among the candidates")
     best = min(table, key=lambda r: r["ms_per_step"])
-    res = {"V": best["V"], "ZT": best["ZT"], "fuse": best["fuse"], "ms_per_step": best["ms_per_step"],
-           "table": table}
+    # then the finalisation layout (one thread or one warp per cell) for that tiling
+    fin_times = {}
+    scratch = Solver(solver.instances, precision=solver.precision)
+    try:
+        scratch.set_tiling(best["V"], best["ZT"], best["fuse"])
+        for mode in (1, 2):
+            scratch.set_finalize(mode)
+            scratch.profile_steps(1)
+            fin_times[mode] = scratch.profile_steps(steps)[2] / steps
+    finally:
+        scratch.close()
+    fin = min(fin_times, key=fin_times.get)
+    res = {"V": best["V"], "ZT": best["ZT"], "fuse": best["fuse"], "fin": fin,
+           "ms_per_step": fin_times[fin], "fin_ms_per_step": fin_times, "table": table}
     solver.set_tiling(best["V"], best["ZT"], best["fuse"])
+    solver.set_finalize(fin)
     _cache[key] = res
     if cache_file:
         # entries of other kernel versions can never hit again

@@ -164,6 +164,58 @@ __device__ __forceinline__ float weno5_corr<float>(float v0, float v1, float v2,
     return fmaf(w1, e1, fmaf(w2, e2, w3 * e3)) * inv;
 }
 
+// ---- packed FP32 (two lanes of f32x2 per instruction, each element rounded exactly as
+// the scalar operation) ----------------------------------------------------------------
+#define LBS_OP2(name, op)                                                                       \
+    static __device__ __forceinline__ float2 name(float2 a, float2 b)                           \
+    {                                                                                           \
+        float2 d;                                                                               \
+        asm("{.reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n " op    \
+            " rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"                                           \
+            : "=f"(d.x), "=f"(d.y)                                                              \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                          \
+        return d;                                                                               \
+    }
+LBS_OP2(add2, "add.rn.f32x2")
+LBS_OP2(sub2, "sub.rn.f32x2")
+LBS_OP2(mul2, "mul.rn.f32x2")
+#undef LBS_OP2
+static __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+static __device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+
+// weno5_corr<float> for two velocities at once (the same operations, element by element;
+// the reciprocals stay scalar): half the issued arithmetic of two scalar calls
+static __device__ __forceinline__ float2 weno5_corr2(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4)
+{
+    const float2 d0 = sub2(v0, v2), d1 = sub2(v1, v2), d3 = sub2(v3, v2), d4 = sub2(v4, v2);
+    const float2 e1 = fma2(splat(2.f), d0, mul2(splat(-7.f), d1));
+    const float2 e2 = fma2(splat(2.f), d3, mul2(splat(-1.f), d1));
+    const float2 e3 = fma2(splat(5.f), d3, mul2(splat(-1.f), d4));
+    float2 a = fma2(splat(-2.f), d1, d0), b = fma2(splat(-4.f), d1, d0);
+    const float2 s1 = fma2(mul2(splat(13.f / 12.f), a), a, mul2(mul2(splat(0.25f), b), b));
+    a = add2(d1, d3);
+    b = sub2(d1, d3);
+    const float2 s2 = fma2(mul2(splat(13.f / 12.f), a), a, mul2(mul2(splat(0.25f), b), b));
+    a = fma2(splat(-2.f), d3, d4);
+    b = fma2(splat(-4.f), d3, d4);
+    const float2 s3 = fma2(mul2(splat(13.f / 12.f), a), a, mul2(mul2(splat(0.25f), b), b));
+    const float2 q1 = fma2(s1, s1, splat(1e-37f)), q2 = fma2(s2, s2, splat(1e-37f)), q3 = fma2(s3, s3, splat(1e-37f));
+    const float2 w1 = mul2(splat(0.1f), make_float2(rcp_approx(q1.x), rcp_approx(q1.y)));
+    const float2 w2 = mul2(splat(0.6f), make_float2(rcp_approx(q2.x), rcp_approx(q2.y)));
+    const float2 w3 = mul2(splat(0.3f), make_float2(rcp_approx(q3.x), rcp_approx(q3.y)));
+    const float2 sw = add2(add2(w1, w2), w3);
+    const float2 inv = mul2(splat(1.f / 6.f), make_float2(rcp_approx(sw.x), rcp_approx(sw.y)));
+    return mul2(fma2(w1, e1, fma2(w2, e2, mul2(w3, e3))), inv);
+}
+
 template <typename T>
 __device__ __forceinline__ T weno5(T v0, T v1, T v2, T v3, T v4)
 {
@@ -330,6 +382,7 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     // x: a_l, l >= 1, against He_l / l!
     full_coeffs(u0, Tc, I.Nx, c);
     s[0] = 0.0;
+#pragma unroll 4  // independent nodes: four FP64 chains in flight
     for (int i = 0; i < Qx; ++i) {
         const double* h = I.Hx + i * (I.Nx + 1);
         double g = 0.0;
@@ -348,6 +401,7 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
         s[1] = 1.0;
     } else {
         full_coeffs(u1, Tc, I.Ny, c);
+#pragma unroll 4
         for (int j = 0; j < Qy; ++j) {
             const double* h = I.Hy + j * (I.Ny + 1);
             double g = 0.0;
@@ -364,6 +418,7 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     c[0] -= 0.5;
     cm[0] -= 0.5;
     s[2] = 0.0;
+#pragma unroll 2
     for (int m = 0; m < Qz; ++m) {
         const double* h = I.Pz + m * (I.Nzq + 1);
         double gp = 0.0, gm = 0.0;
@@ -429,7 +484,7 @@ static __device__ __forceinline__ void state_about(const InstDev& I, double* mom
 // other CTAs of this launch, hence read past L1), the macroscopic state, the
 // profiles, W for the residual, and the cell record of the next stage.
 template <typename T>
-__device__ void finalize_cell(const InstDev& I, int cell, int stage)
+__device__ __noinline__ void finalize_cell(const InstDev& I, int cell, int stage)
 {
     const int Nz = I.Nz, nch = I.nchunks;
     double mom[kNMom];  // the partials: moments of the deviations about ur
@@ -599,7 +654,7 @@ __device__ bool write_record_warp(const InstDev& I, int cell, const CellState& s
 }
 
 template <typename T>
-__device__ void finalize_cell_warp(const InstDev& I, int cell, int lane, int stage)
+__device__ __noinline__ void finalize_cell_warp(const InstDev& I, int cell, int lane, int stage)
 {
     const int Nz = I.Nz, nch = I.nchunks, am = lane & 15, h = lane >> 4;
     // moment am: lanes am and 16 + am sum the even and the odd chunks (loads four
@@ -632,7 +687,7 @@ __device__ void finalize_cell_warp(const InstDev& I, int cell, int lane, int sta
 // One instance (whole CTA): wall densities n_w from the outgoing wall fluxes
 // (zero net mass flux, Appendix); after stage 3 the residual, the step count
 // and retirement; after the analysis pass W_old = W.
-static __device__ void finalize_instance(const InstDev& I, int stage, double* red)
+static __device__ __noinline__ void finalize_instance(const InstDev& I, int stage, double* red)
 {
     // red: kRedSlots doubles.  The wall fluxes and (stage 3) the residual's sums
     // ||W_new - W_old||^2, ||W_old||^2 for n, u_x, T are reduced together.
@@ -991,9 +1046,29 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             qx = sc[R_QX]; qy = sc[R_QY]; qz = sc[R_QZ];
             itau = sc[R_ITAU]; cS = sc[R_CS]; i5T = sc[R_I5T]; idz = idzs[cc];
         }
-        A acc[16];
+        // WENO corrections of the interfaces ahead, two velocities per packed FP32
+        // instruction where the storage is FP32
+        T cpv[V];
+        if (STAGE > 0) {
+            if constexpr (sizeof(T) == 4 && V % 2 == 0) {
 #pragma unroll
-        for (int a = 0; a < 16; ++a) acc[a] = A(0);
+                for (int p2 = 0; p2 < V / 2; ++p2) {
+                    const float2 r = weno5_corr2(make_float2(w[2 * p2][1], w[2 * p2 + 1][1]),
+                                                 make_float2(w[2 * p2][2], w[2 * p2 + 1][2]),
+                                                 make_float2(w[2 * p2][3], w[2 * p2 + 1][3]),
+                                                 make_float2(w[2 * p2][4], w[2 * p2 + 1][4]),
+                                                 make_float2(w[2 * p2][5], w[2 * p2 + 1][5]));
+                    cpv[2 * p2] = r.x;
+                    cpv[2 * p2 + 1] = r.y;
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) cpv[v] = weno5_corr<T>(w[v][1], w[v][2], w[v][3], w[v][4], w[v][5]);
+            }
+        }
+        A acc[16];  // the first velocity sets the sums (no adds to zero)
+#pragma unroll
+        for (int a = kNMom; a < 16; ++a) acc[a] = A(0);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const unsigned short lq = lqc[v];
@@ -1001,7 +1076,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             T out = w[v][3];  // the value whose moments are taken
             T ex = 0, ey = 0, ez = 0, xi2 = 0;  // xi = p - u of the cell's record
             if (STAGE > 0) {
-                const T cp = weno5_corr<T>(w[v][1], w[v][2], w[v][3], w[v][4], w[v][5]);
+                const T cp = cpv[v];
                 const T f = w[v][3];
                 // Shakhov target n Gx Gy Gz (1 + S), S = cS (xi^2/(5T) - 1) xi.q; in the
                 // phi / chi model (Eq. sred_def) S = cS ((xi_x^2 + xi_z^2)/(5T) - 4/5 or 2/5) xi.q
@@ -1075,22 +1150,25 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 // w of the velocity: wpsi[v][0] for phi and the full set, wpsi[v][5] for chi
                 // (whose other weighted moments are zero)
                 const A ow = o * (RED ? wpsi[v][0] + wpsi[v][5] : wpsi[v][0]);
+                A t[kNMom];
                 if (RED) {
                     const A owc = jj[v] ? ow : A(0), owp = ow - owc;  // chi, phi
                     const A opx = owp * A(ex), opz = owp * A(ez), r3 = owp * A(xi2) + owc;
-                    acc[0] += owp; acc[1] += opx; acc[3] += opz;
-                    acc[4] += opx * A(ex); acc[5] += owc; acc[6] += opz * A(ez); acc[8] += opx * A(ez);
-                    acc[10] += r3 * A(ex); acc[12] += r3 * A(ez);
+                    t[0] = owp; t[1] = opx; t[2] = A(0); t[3] = opz;
+                    t[4] = opx * A(ex); t[5] = owc; t[6] = opz * A(ez); t[7] = A(0); t[8] = opx * A(ez);
+                    t[9] = A(0); t[10] = r3 * A(ex); t[11] = A(0); t[12] = r3 * A(ez);
                 } else {
                     const A owx = ow * A(ex), owy = ow * A(ey), owz = ow * A(ez), ow2 = ow * A(xi2);
-                    acc[0] += ow; acc[1] += owx; acc[2] += owy; acc[3] += owz;
-                    acc[4] += owx * A(ex); acc[5] += owy * A(ey); acc[6] += owz * A(ez);
-                    acc[7] += owx * A(ey); acc[8] += owx * A(ez); acc[9] += owy * A(ez);
-                    acc[10] += ow2 * A(ex); acc[11] += ow2 * A(ey); acc[12] += ow2 * A(ez);
+                    t[0] = ow; t[1] = owx; t[2] = owy; t[3] = owz;
+                    t[4] = owx * A(ex); t[5] = owy * A(ey); t[6] = owz * A(ez);
+                    t[7] = owx * A(ey); t[8] = owx * A(ez); t[9] = owy * A(ez);
+                    t[10] = ow2 * A(ex); t[11] = ow2 * A(ey); t[12] = ow2 * A(ez);
                 }
+#pragma unroll
+                for (int a = 0; a < kNMom; ++a) acc[a] = v == 0 ? t[a] : acc[a] + t[a];
             } else {
 #pragma unroll
-                for (int a = 0; a < kNMom; ++a) acc[a] += o * wpsi[v][a];
+                for (int a = 0; a < kNMom; ++a) acc[a] = v == 0 ? o * wpsi[v][a] : acc[a] + o * wpsi[v][a];
             }
         }
         const A tot = reduce_scatter16<A>(acc, lane);

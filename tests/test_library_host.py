@@ -242,6 +242,10 @@ def test_autotuner_host_logic(monkeypatch, tmp_path):
         def tiling(self):
             return {"ctas": 1}
 
+        def set_finalize(self, mode):
+            self.fin = mode
+            return mode == 2
+
         def close(self):
             pass
 
@@ -254,14 +258,17 @@ def test_autotuner_host_logic(monkeypatch, tmp_path):
     r = AT.autotune(target, candidates=((1, 8, 0), (2, 12, 0), (2, 12, 1), (4, 99, 0)), steps=3,
                     cache_file=str(cache))
     assert (r["V"], r["ZT"], r["fuse"]) == (2, 12, 0) and target.t == (2, 12, 0)
-    assert len(r["table"]) == 3 and len(made) == 1  # one scratch solver; the invalid one skipped
+    assert r["fin"] in (1, 2) and target.fin == r["fin"]
+    # one scratch solver for the tilings (the invalid one skipped), one for the finalisation layouts
+    assert len(r["table"]) == 3 and len(made) == 2
     disk = json.loads(cache.read_text())
     key = AT.signature(target)
     assert list(disk) == [key] and key.startswith(AT.kernel_hash() + ":p1:")
-    assert key.endswith("2*16x128,24x128")
+    assert key.endswith(":2*16x128,24x128")
     monkeypatch.setattr(AT, "_cache", {})
     made.clear()
     again = FakeSolver(target.instances, precision=1)
     made.clear()
     r2 = AT.autotune(again, cache_file=str(cache))
     assert (r2["V"], r2["ZT"], r2["fuse"]) == (2, 12, 0) and again.t == (2, 12, 0) and not made
+    assert again.fin == r["fin"]
