@@ -463,7 +463,7 @@ def main():
         s.set_tiling(V, ZT, F)
         tuned = {"V": V, "ZT": ZT, "fuse": F, "source": "--tiling"}
     else:
-        tuned = autotune(s, candidates=tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (8, 10, 12, 16, 24)
+        tuned = autotune(s, candidates=tuple((V, ZT, F) for V in (1, 2, 4) for ZT in (8, 10, 12, 14, 16, 24)
                                              for F in (0, 1, 2)), steps=3,
                          cache_file=a.tuning_cache or DEFAULT_CACHE)
     st = s.torch_stream()

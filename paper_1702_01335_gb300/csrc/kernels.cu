@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ in
 size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride)
 {
     const int KC = kThreads * V;
-    return stage_smem(zn, KC, G, fp32 ? 4 : 8, 8, stage >= 2, rstride).total;
+    (void)stage;
+    return stage_smem(zn, KC, G, fp32 ? 4 : 8, 8, rstride).total;
 }
 
 template <typename T>

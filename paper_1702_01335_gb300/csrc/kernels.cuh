@@ -297,20 +297,18 @@ __device__ __forceinline__ A reduce_scatter16(A (&v)[16], int lane)
 }
 
 // shared-memory layout of a stage CTA (offsets in bytes): the staged rows of the
-// step's start state d (cells z0-3 .. z0+zn+2), the same rows of the stage input's
-// increment (stages 2 and 3), the cell records (all by bulk copy), the per-axis
-// factors of this chunk's nodes, 1/dz, and the per-warp moment sums.
+// step's start state d (cells z0-3 .. z0+zn+2) and the cell records (by bulk copy), the
+// per-axis factors of this chunk's nodes, 1/dz, and the per-warp moment sums.  The stage
+// input's increment (stages 2 and 3) is read from global memory during the march.
 struct StageSmem {
-    size_t fin, dr, rec, g, idz, red, total;
+    size_t fin, rec, g, idz, red, total;
 };
 __host__ __device__ inline size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
-__host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize, int asize, bool withD,
-                                                int rstride)
+__host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize, int asize, int rstride)
 {
     StageSmem L;
     size_t o = 0;
     L.fin = o; o += (size_t)(zn + 6) * KC * esize;
-    L.dr = o; o += withD ? (size_t)(zn + 6) * KC * esize : 0;  // directly after fin (row offset (zn+6) KC)
     L.rec = o; o += (size_t)zn * rstride * esize;
     L.g = o; o += pad16((size_t)zn * G * esize);
     L.idz = o; o += pad16((size_t)zn * esize);
@@ -328,19 +326,19 @@ __host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize
 // lo until it carries into hi; what is lost is below 2^-16 ulp(hi) per step.
 // ulp(hi) = 2^(E - 150) for the biased exponent E of a normal hi, so
 // lo / ulp(hi) * 2^15 = lo * 2^(165 - E), a power of two built in the exponent field
-// (valid for 38 <= E; a hi below 2^-89 keeps no residual).
+// from the masked exponent bits of hi (E clamped below at 38; the decoding scale
+// 2^(E - 165) is then zero: a hi below 2^-88 keeps no residual).
 static __device__ __forceinline__ unsigned short lo_encode(float lo, float hi)
 {
-    const unsigned E = (__float_as_uint(hi) >> 23) & 0xffu;
-    const float s = __uint_as_float((292u - E) << 23);  // 2^(165 - E)
-    const int q = E >= 38u ? __float2int_rn(lo * s) : 0;
-    return static_cast<unsigned short>(static_cast<short>(q));
+    const unsigned m = max(__float_as_uint(hi) & 0x7f800000u, 38u << 23);
+    const float s = __uint_as_float((292u << 23) - m);  // 2^(165 - E)
+    return static_cast<unsigned short>(static_cast<short>(__float2int_rn(lo * s)));
 }
 static __device__ __forceinline__ float lo_decode(unsigned short q, float hi)
 {
-    const unsigned E = (__float_as_uint(hi) >> 23) & 0xffu;
-    const float s = __uint_as_float((E - 38u) << 23);  // 2^(E - 165)
-    return E >= 39u ? float(static_cast<short>(q)) * s : 0.0f;
+    const unsigned m = max(__float_as_uint(hi) & 0x7f800000u, 38u << 23);
+    const float s = __uint_as_float(m - (38u << 23));  // 2^(E - 165), zero for E = 38
+    return float(static_cast<short>(q)) * s;
 }
 
 // ----------------------------------------------------------------------------
@@ -772,10 +770,14 @@ static __device__ __forceinline__ const InstDev& stage_descriptor(const InstDev*
 // Minimum resident CTAs per SM requested from the register allocator: the
 // per-velocity register window grows with V; the rarely taken finalisation
 // path may spill instead of lowering occupancy.
-template <int V> struct MinBlocks { static constexpr int value = V == 1 ? 8 : V == 2 ? 6 : 3; };
+template <typename T, int V> struct MinBlocks {
+    // FP32 at V = 4 fits 128 registers (four CTAs, sixteen warps per SM); FP64 values take
+    // two registers each and keep three
+    static constexpr int value = V == 1 ? 8 : V == 2 ? 6 : sizeof(T) == 4 ? 4 : 3;
+};
 
 template <typename T, int V, int STAGE, bool RED>
-__global__ void __launch_bounds__(kThreads, MinBlocks<V>::value)
+__global__ void __launch_bounds__(kThreads, MinBlocks<T, V>::value)
 stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, int fuse)
 {
     typedef typename Acc<T>::type A;
@@ -802,14 +804,12 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     const int rstride = I.rec_stride;
-    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(double), kD, rstride);
+    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(double), rstride);
     T* Fs = reinterpret_cast<T*>(smem_raw + L.fin);   // d rows: cells z0-3 .. z0+zn+2
-    T* Ds = reinterpret_cast<T*>(smem_raw + L.dr);    // increment rows, same cells (stages 2, 3)
     T* recs = reinterpret_cast<T*>(smem_raw + L.rec); // records of cells z0 .. z0+zn-1
     T* gsm = reinterpret_cast<T*>(smem_raw + L.g);
     T* idzs = reinterpret_cast<T*>(smem_raw + L.idz);
     double* red = reinterpret_cast<double*>(smem_raw + L.red);  // per-warp moment sums, summed in FP64
-    const long doff = (long)(zn + 6) * KC;            // Ds = Fs + doff
 
     // Buffers (Eq. rk3 in increment form, F_l the step's start state d):
     //   stage 1: d1 = dt L[F_l]                  -> the other of F0 / F1
@@ -817,7 +817,9 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     //   stage 3: F_l + 2/3 (d2 + dt L[F_l + d2]) -> the other of F0 / F1 (over d1)
     const T* Hg = static_cast<const T*>(cur ? I.F1 : I.F0);
     T* Og = static_cast<T*>(cur ? I.F0 : I.F1);
-    const T* Dg = STAGE == 2 ? Og : static_cast<const T*>(I.F2);
+    // the stage input's increment (stages 2, 3) is read from global memory through the
+    // read-only path (this launch does not write it), one march step ahead
+    const T* __restrict__ Dg = STAGE == 2 ? Og : static_cast<const T*>(I.F2);
     T* Fout = STAGE == 2 ? static_cast<T*>(I.F2) : Og;
     const int s_lo = max(0, z0 - 3), s_hi = min(Nz - 1, z0 + zn + 2);
 
@@ -833,32 +835,28 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         __syncthreads();
         if (tid == 0) {
             const uint32_t bytes = kn * sizeof(T);
-            uint32_t total = bytes * (s_hi - s_lo + 1) * (kD ? 2 : 1);
+            uint32_t total = bytes * (s_hi - s_lo + 1);
             if (STAGE > 0) total += rec_bytes;
             mbar_expect_tx(&bar, total);
-            for (int s = s_lo; s <= s_hi; ++s) {
+            for (int s = s_lo; s <= s_hi; ++s)
                 bulk_g2s(Fs + (size_t)(s - z0 + 3) * KC, Hg + (size_t)s * Q + k0, bytes, &bar);
-                if (kD) bulk_g2s(Ds + (size_t)(s - z0 + 3) * KC, Dg + (size_t)s * Q + k0, bytes, &bar);
-            }
             if (STAGE > 0) bulk_g2s(recs, Rg, rec_bytes, &bar);  // records are 16-byte multiples
         }
     } else {
         for (int s = s_lo; s <= s_hi; ++s)
-            for (int kl = tid; kl < kn; kl += kThreads) {
-                Fs[(size_t)(s - z0 + 3) * KC + kl] = Hg[(size_t)s * Q + k0 + kl];
-                if (kD) Ds[(size_t)(s - z0 + 3) * KC + kl] = Dg[(size_t)s * Q + k0 + kl];
-            }
+            for (int kl = tid; kl < kn; kl += kThreads) Fs[(size_t)(s - z0 + 3) * KC + kl] = Hg[(size_t)s * Q + k0 + kl];
         if (STAGE > 0)
             for (int e = tid; e < zn * rstride; e += kThreads) recs[e] = Rg[e];
     }
     if (STAGE > 0)
         for (int c = tid; c < zn; c += kThreads) idzs[c] = ld<T>(I.inv_dz, z0 + c);
 
-    // per-velocity constants: p (and |p_z| for the fluxes), w * psi(p) for the 13 raw moments
+    // per-velocity constants: p (and |p_z| for the fluxes), the weight w and |p|^2 for the
+    // moments (formed from them per cell: fewer registers than 13 weighted monomials)
     int ii[V], jj[V], zz[V], kl[V];
     T px[V], py[V], pz[V], apz[V];
-    A wpsi[V][kNMom];
-    bool ok[V];
+    A wv[V], yv[V], p2v[V], wm[V];  // weight; p_y for the moments; |p|^2; w of the mass flux
+    bool ok[V], chi[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         kl[v] = tid + v * kThreads;
@@ -873,24 +871,16 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         const T x = ld<T>(I.xi, m);
         pz[v] = sg ? -x : x;
         apz[v] = x;
-        const A w = ok[v] ? A(ld<T>(I.wx, ii[v]) * ld<T>(I.wy, jj[v]) * ld<T>(I.wz, m)) : A(0);
-        const A X = px[v], Y = py[v], Z = pz[v], p2 = X * X + Y * Y + Z * Z;
-        wpsi[v][0] = w;
-        wpsi[v][1] = w * X; wpsi[v][2] = w * Y; wpsi[v][3] = w * Z;
-        wpsi[v][4] = w * X * X; wpsi[v][5] = w * Y * Y; wpsi[v][6] = w * Z * Z;
-        wpsi[v][7] = w * X * Y; wpsi[v][8] = w * X * Z; wpsi[v][9] = w * Y * Z;
-        wpsi[v][10] = w * p2 * X; wpsi[v][11] = w * p2 * Y; wpsi[v][12] = w * p2 * Z;
+        wv[v] = ok[v] ? A(ld<T>(I.wx, ii[v]) * ld<T>(I.wy, jj[v]) * ld<T>(I.wz, m)) : A(0);
+        const A X = px[v], Y = py[v], Z = pz[v];
+        yv[v] = Y;
+        p2v[v] = X * X + Y * Y + Z * Z;
+        chi[v] = RED && jj[v] == 1;
+        wm[v] = chi[v] ? A(0) : wv[v];
         if (RED) {
             // p_y = 0 on both fields.  chi = int p_y^2 f dp_y carries the p_y^2 moments:
             // sum chi -> sum p_y^2 f, sum p_a chi -> sum p_y^2 p_a f (a = x, z), nothing else.
             // py[v] then holds -(the Shakhov offset of Eq. sred_def): -4/5 for phi, -2/5 for chi.
-            if (jj[v] == 1) {
-#pragma unroll
-                for (int a = 0; a < kNMom; ++a) wpsi[v][a] = A(0);
-                wpsi[v][5] = w;
-                wpsi[v][10] = w * X;
-                wpsi[v][12] = w * Z;
-            }
             py[v] = jj[v] ? T(-0.4) : T(-0.8);
         }
     }
@@ -935,10 +925,11 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     }
 
     // ---- 4b. ghost rows (each thread fills only its own columns).  A ghost row holds
-    //          the whole stage-input value d (+ increment) in Fs and zero in Ds.
+    //          the whole stage-input value d (+ increment); a cell's row holds d.
     const int rbase = 3 - z0;  // smem row of cell s is s + rbase
-    auto rowval = [&](int row, int col) -> T {
-        return kD ? Fs[(size_t)row * KC + col] + Ds[(size_t)row * KC + col] : Fs[(size_t)row * KC + col];
+    auto rowval = [&](int row, int col) -> T {  // the stage input of a cell's row
+        return kD ? Fs[(size_t)row * KC + col] + __ldg(Dg + (size_t)(row - rbase) * Q + k0 + col)
+                  : Fs[(size_t)row * KC + col];
     };
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -970,9 +961,6 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 if (-3 + rbase >= 0) col[(size_t)(-3 + rbase) * KC] = g1;  // never read for p_z < 0
             }
         }
-        if (kD && z0 < 3)
-            for (int s = -3; s <= -1; ++s)
-                if (s + rbase >= 0) col[doff + (size_t)(s + rbase) * KC] = T(0);
         if (z0 + zn + 3 > Nz) {
             const int smax = z0 + zn + 2;
             if (sgc) {
@@ -990,9 +978,6 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 if (Nz + 1 <= smax) col[(size_t)(Nz + 1 + rbase) * KC] = g1;
                 if (Nz + 2 <= smax) col[(size_t)(Nz + 2 + rbase) * KC] = g1;  // never read for p_z > 0
             }
-            if (kD)
-                for (int s = Nz; s <= Nz + 2; ++s)
-                    if (s <= smax) col[doff + (size_t)(s + rbase) * KC] = T(0);
         }
     }
 
@@ -1006,34 +991,57 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     // divergence of Eq. (flux) is (ahead - behind) / dz for the signed p_z either way.
     const long rstep = sgc ? -(long)KC : (long)KC;
     const T* rp = Fs + (sgc ? (size_t)(zn + 5) * KC : 0);  // window row d at step c: rp + (c + d) rstep
+    // stages 2, 3: the increment of the cell of each window row, read from global memory
+    // through the read-only path (this launch does not write it).  Window row cd at step c
+    // holds cell zw0 + (c + cd) sdir; a ghost row (a cell outside 0 .. Nz-1) takes zero,
+    // its shared-memory value being the whole stage input.  Thread-based pointers: the
+    // thread's velocity v sits at + v kThreads.
+    const int sdir = sgc ? -1 : 1;
+    const int zw0 = sgc ? z0 + zn + 2 : z0 - 3;
+    const T* __restrict__ dq = Dg + k0 + tid;
+    auto inc_row = [&](int s, T(&out)[V]) {
+        const bool in = kD && (unsigned)s < (unsigned)Nz;
+        const T* p = dq + (long)s * Q;
+#pragma unroll
+        for (int v = 0; v < V; ++v) out[v] = in && ok[v] ? __ldg(p + v * kThreads) : T(0);
+    };
     // cm: the WENO correction of the interface behind (its flux is |p_z| (w2 + cm))
-    T w[V][6], cm[V];
+    T w[V][6], cm[V], dn[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
+    for (int d = 0; d < 6; ++d) {
+        inc_row(zw0 + d * sdir, dn);
 #pragma unroll
-        for (int d = 0; d < 6; ++d) {
-            const T* q = rp + d * rstep + kl[v];
-            w[v][d] = kD ? q[0] + q[doff] : q[0];
-        }
-        cm[v] = weno5_corr<T>(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4]);
+        for (int v = 0; v < V; ++v) w[v][d] = rp[d * rstep + kl[v]] + dn[v];
     }
+#pragma unroll
+    for (int v = 0; v < V; ++v) cm[v] = weno5_corr<T>(w[v][0], w[v][1], w[v][2], w[v][3], w[v][4]);
+    int sn = zw0 + 6 * sdir;  // the cell of the row the next step loads
+    inc_row(sn, dn);
     const T dt = T(I.dt);
     const long ostep = sgc ? -(long)Q : (long)Q;
-    const size_t orow0 = (size_t)(sgc ? z0 + zn - 1 : z0) * Q + k0;  // global offset of the first cell
+    const size_t orow0 = (size_t)(sgc ? z0 + zn - 1 : z0) * Q + k0 + tid;  // the first cell, thread's column
     T* outp = Fout + orow0;
+    const T* __restrict__ dop = kD ? Dg + orow0 : nullptr;  // the increment of the cell
     unsigned short* lop = kLo && STAGE == 3 ? I.L0 + orow0 : nullptr;
     // stage 3 (FP32): the residuals of the next cell are loaded one march step ahead, so
     // that their global-memory latency overlaps a step's arithmetic
     unsigned short lqn[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) lqn[v] = kLo && STAGE == 3 && ok[v] ? lop[kl[v]] : 0;
+    for (int v = 0; v < V; ++v) lqn[v] = kLo && STAGE == 3 && ok[v] ? __ldcg(lop + v * kThreads) : 0;
+    constexpr bool kPack = sizeof(T) == 4 && V % 2 == 0;  // moments of two velocities per packed op
 #pragma unroll 1  // unrolling the z-march only adds instruction-cache misses
     for (int c = 0; c < zn; ++c) {
         unsigned short lqc[V];
+        T dc[V];  // increments of the window row this step loads
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             lqc[v] = lqn[v];
-            if (kLo && STAGE == 3 && ok[v] && c + 1 < zn) lqn[v] = lop[ostep + kl[v]];
+            if (kLo && STAGE == 3 && ok[v] && c + 1 < zn) lqn[v] = __ldcg(lop + ostep + v * kThreads);
+            dc[v] = dn[v];
+        }
+        if (kD && c + 1 < zn) {
+            sn += sdir;
+            inc_row(sn, dn);
         }
         const int cc = sgc ? zn - 1 - c : c;  // the cell within the tile
         const T* sc = recs + (size_t)cc * rstride;
@@ -1050,7 +1058,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         // instruction where the storage is FP32
         T cpv[V];
         if (STAGE > 0) {
-            if constexpr (sizeof(T) == 4 && V % 2 == 0) {
+            if constexpr (kPack) {
 #pragma unroll
                 for (int p2 = 0; p2 < V / 2; ++p2) {
                     const float2 r = weno5_corr2(make_float2(w[2 * p2][1], w[2 * p2 + 1][1]),
@@ -1066,13 +1074,12 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 for (int v = 0; v < V; ++v) cpv[v] = weno5_corr<T>(w[v][1], w[v][2], w[v][3], w[v][4], w[v][5]);
             }
         }
-        A acc[16];  // the first velocity sets the sums (no adds to zero)
-#pragma unroll
-        for (int a = kNMom; a < 16; ++a) acc[a] = A(0);
+        // ---- per velocity: the update, its store, and the moment variables
+        A ov[V], mx[V], my[V], mz[V], m2[V];  // value; the monomials' factors (p or p - u_r); |.|^2
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const unsigned short lq = lqc[v];
-            const T wn = kD ? rn[kl[v]] + rn[doff + kl[v]] : rn[kl[v]];
+            const T wn = rn[kl[v]] + dc[v];
             T out = w[v][3];  // the value whose moments are taken
             T ex = 0, ey = 0, ez = 0, xi2 = 0;  // xi = p - u of the cell's record
             if (STAGE > 0) {
@@ -1103,7 +1110,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 T h = f, dinc = T(0), lo = T(0);
                 if (STAGE >= 2) {
                     h = own[kl[v]];
-                    dinc = own[doff + kl[v]];
+                    dinc = ok[v] ? __ldg(dop + v * kThreads) : T(0);
                 }
                 if constexpr (kLo && STAGE == 3) lo = lo_decode(lq, h);
                 const T dep = STAGE >= 2 ? ((h - tgt) + dinc) + lo : f - tgt;
@@ -1128,53 +1135,89 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                         const T t = lo + inc;
                         const T h2 = h + t;
                         const T lo2 = t - (h2 - h);
-                        if (ok[v]) lop[kl[v]] = lo_encode(lo2, h2);
+                        if (ok[v]) __stcg(lop + v * kThreads, lo_encode(lo2, h2));
                         st = h2;
                     } else {
                         st = h + inc;
                     }
                     out = st;
                 }
-                if (ok[v]) outp[kl[v]] = st;
+                if (ok[v]) __stcg(outp + v * kThreads, st);
                 cm[v] = cp;
             }
 #pragma unroll
             for (int d = 0; d < 5; ++d) w[v][d] = w[v][d + 1];
             w[v][5] = wn;
-            const A o = ok[v] ? A(out) : A(0);  // columns past the chunk hold no data
+            // the moments: stages 0-2 of psi(p) (for the records), stage 3 of psi(p - u_r)
+            // about the velocity u_r of the cell's record, so that the third moments are
+            // close to the heat flux itself instead of its sum with terms of size u |p|^2
+            // that cancel it (160-fold in config C1); the finalisation adds the rest
+            // state's moments about u_r.  Columns past the chunk hold no data (their
+            // shared memory is never written) and contribute zero.
+            ov[v] = ok[v] ? A(out) * wv[v] : A(0);
             if (STAGE == 3) {
-                // the profiles' moments: of psi(p - u_r) about the velocity u_r of the cell's
-                // record, so that the third moments are close to the heat flux itself
-                // instead of its sum with terms of size u |p|^2 that cancel it (160-fold in
-                // config C1); the finalisation adds the rest state's moments about u_r
-                // w of the velocity: wpsi[v][0] for phi and the full set, wpsi[v][5] for chi
-                // (whose other weighted moments are zero)
-                const A ow = o * (RED ? wpsi[v][0] + wpsi[v][5] : wpsi[v][0]);
-                A t[kNMom];
-                if (RED) {
-                    const A owc = jj[v] ? ow : A(0), owp = ow - owc;  // chi, phi
-                    const A opx = owp * A(ex), opz = owp * A(ez), r3 = owp * A(xi2) + owc;
-                    t[0] = owp; t[1] = opx; t[2] = A(0); t[3] = opz;
-                    t[4] = opx * A(ex); t[5] = owc; t[6] = opz * A(ez); t[7] = A(0); t[8] = opx * A(ez);
-                    t[9] = A(0); t[10] = r3 * A(ex); t[11] = A(0); t[12] = r3 * A(ez);
+                mx[v] = A(ex); my[v] = A(ey); mz[v] = A(ez); m2[v] = A(xi2);
+            } else {
+                mx[v] = A(px[v]); my[v] = yv[v]; mz[v] = A(pz[v]); m2[v] = p2v[v];
+            }
+        }
+        // ---- the 13 weighted monomials summed over the thread's velocities: w f times
+        // 1, p_a, p_a p_b, |p|^2 p_a (RED: chi carries the p_y^2 parts: sum chi, sum chi p_x,
+        // sum chi p_z)
+        A acc[16];
+#pragma unroll
+        for (int a = kNMom; a < 16; ++a) acc[a] = A(0);
+        if constexpr (kPack && !RED) {
+            float2 s2[kNMom];
+#pragma unroll
+            for (int p2 = 0; p2 < V / 2; ++p2) {
+                const int v0 = 2 * p2, v1 = v0 + 1;
+                const float2 o = make_float2(ov[v0], ov[v1]), X = make_float2(mx[v0], mx[v1]),
+                             Y = make_float2(my[v0], my[v1]), Z = make_float2(mz[v0], mz[v1]),
+                             P = make_float2(m2[v0], m2[v1]);
+                const float2 oX = mul2(o, X), oY = mul2(o, Y), oZ = mul2(o, Z), oP = mul2(o, P);
+                if (p2 == 0) {
+                    s2[0] = o; s2[1] = oX; s2[2] = oY; s2[3] = oZ;
+                    s2[4] = mul2(oX, X); s2[5] = mul2(oY, Y); s2[6] = mul2(oZ, Z);
+                    s2[7] = mul2(oX, Y); s2[8] = mul2(oX, Z); s2[9] = mul2(oY, Z);
+                    s2[10] = mul2(oP, X); s2[11] = mul2(oP, Y); s2[12] = mul2(oP, Z);
                 } else {
-                    const A owx = ow * A(ex), owy = ow * A(ey), owz = ow * A(ez), ow2 = ow * A(xi2);
-                    t[0] = ow; t[1] = owx; t[2] = owy; t[3] = owz;
-                    t[4] = owx * A(ex); t[5] = owy * A(ey); t[6] = owz * A(ez);
-                    t[7] = owx * A(ey); t[8] = owx * A(ez); t[9] = owy * A(ez);
-                    t[10] = ow2 * A(ex); t[11] = ow2 * A(ey); t[12] = ow2 * A(ez);
+                    s2[0] = add2(s2[0], o); s2[1] = add2(s2[1], oX); s2[2] = add2(s2[2], oY);
+                    s2[3] = add2(s2[3], oZ);
+                    s2[4] = fma2(oX, X, s2[4]); s2[5] = fma2(oY, Y, s2[5]); s2[6] = fma2(oZ, Z, s2[6]);
+                    s2[7] = fma2(oX, Y, s2[7]); s2[8] = fma2(oX, Z, s2[8]); s2[9] = fma2(oY, Z, s2[9]);
+                    s2[10] = fma2(oP, X, s2[10]); s2[11] = fma2(oP, Y, s2[11]); s2[12] = fma2(oP, Z, s2[12]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < kNMom; ++a) acc[a] = s2[a].x + s2[a].y;
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                A t[kNMom];
+                const A o = ov[v], X = mx[v], Y = my[v], Z = mz[v], P = m2[v];
+                if (RED) {  // phi: p_y = 0; chi: the p_y^2 parts
+                    const A oc = chi[v] ? o : A(0), op = o - oc;
+                    const A oX = op * X, oZ = op * Z, r3 = op * P + oc;
+                    t[0] = op; t[1] = oX; t[2] = A(0); t[3] = oZ;
+                    t[4] = oX * X; t[5] = oc; t[6] = oZ * Z; t[7] = A(0); t[8] = oX * Z;
+                    t[9] = A(0); t[10] = r3 * X; t[11] = A(0); t[12] = r3 * Z;
+                } else {
+                    const A oX = o * X, oY = o * Y, oZ = o * Z, oP = o * P;
+                    t[0] = o; t[1] = oX; t[2] = oY; t[3] = oZ;
+                    t[4] = oX * X; t[5] = oY * Y; t[6] = oZ * Z;
+                    t[7] = oX * Y; t[8] = oX * Z; t[9] = oY * Z;
+                    t[10] = oP * X; t[11] = oP * Y; t[12] = oP * Z;
                 }
 #pragma unroll
                 for (int a = 0; a < kNMom; ++a) acc[a] = v == 0 ? t[a] : acc[a] + t[a];
-            } else {
-#pragma unroll
-                for (int a = 0; a < kNMom; ++a) acc[a] = v == 0 ? o * wpsi[v][a] : acc[a] + o * wpsi[v][a];
             }
         }
         const A tot = reduce_scatter16<A>(acc, lane);
         const int m = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
         if ((lane & 1) == 0) red[((size_t)cc * (kThreads / 32) + warp) * 16 + m] = tot;
         outp += ostep;
+        if (kD) dop += ostep;
         if (kLo && STAGE == 3) lop += ostep;
     }
     __syncthreads();
@@ -1204,7 +1247,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 const T f1 = outval(v, 0), f2 = outval(v, 1), f3 = outval(v, 2);
                 const T g0 = T(I.ext_bot[0][0]) * f1 + T(I.ext_bot[0][1]) * f2 + T(I.ext_bot[0][2]) * f3;
                 const T g1 = T(I.ext_bot[1][0]) * g0 + T(I.ext_bot[1][1]) * f1 + T(I.ext_bot[1][2]) * f2;
-                fl += double(wpsi[v][0]) * double(pz[v] * weno5<T>(f3, f2, f1, g0, g1));
+                fl += double(wm[v]) * double(pz[v] * weno5<T>(f3, f2, f1, g0, g1));
             }
         fl = block_sum(fl, wall_red);
         if (tid == 0) I.flux_part[tile.chunk * 2 + 0] = fl;
@@ -1217,7 +1260,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 const T f1 = outval(v, Nz - 1), f2 = outval(v, Nz - 2), f3 = outval(v, Nz - 3);
                 const T g0 = T(I.ext_top[0][0]) * f1 + T(I.ext_top[0][1]) * f2 + T(I.ext_top[0][2]) * f3;
                 const T g1 = T(I.ext_top[1][0]) * g0 + T(I.ext_top[1][1]) * f1 + T(I.ext_top[1][2]) * f2;
-                fl += double(wpsi[v][0]) * double(pz[v] * weno5<T>(f3, f2, f1, g0, g1));
+                fl += double(wm[v]) * double(pz[v] * weno5<T>(f3, f2, f1, g0, g1));
             }
         fl = block_sum(fl, wall_red);
         if (tid == 0) I.flux_part[tile.chunk * 2 + 1] = fl;
