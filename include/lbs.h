@@ -239,9 +239,13 @@ lbs_status lbs_moments_static(lbs_handle h, int inst, const void* f_dev, double*
  * Synchronises.  For measurement only; the arithmetic is that of lbs_step. */
 lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms);
 
-/* Work decomposition of the stage kernel (no effect on the arithmetic): each
- * CTA of 128 threads updates 128*V velocities (V in {1, 2, 4}) of about ZT
- * consecutive cells (3 <= ZT <= 64).  fuse = 1 folds the per-cell and
+/* Work decomposition of the stage kernel: each CTA of 128 threads updates 128*V
+ * velocities (V in {1, 2, 4}) of about ZT consecutive cells (3 <= ZT <= 64).  No
+ * effect on the arithmetic in FP64.  In FP32 the full model with V = 2 or 4 gives each
+ * thread adjacent velocity pairs, moved as 64-bit words and updated by packed
+ * two-lane FP32 instructions: the same operations up to the compiler's contraction
+ * choices (results agree to FP32 rounding); this layout needs Q / 2 even in every
+ * instance (LBS_ERR_ARG otherwise).  fuse = 1 folds the per-cell and
  * per-instance finalisation into the stage kernel (the last CTA of a z-tile /
  * of an instance does it: 3 launches per step); fuse = 0 runs it as one
  * further launch per stage; fuse = 2 does the
@@ -250,7 +254,7 @@ lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms);
  * (the step forks from and joins back into the handle's stream; a batch of one
  * instance steps as with fuse = 0).  Used by the tile autotuner.  Without a call
  * a solver starts with V = 1, ZT = 4 below 2^22 cell x velocity updates per step
- * and V = 4, ZT = 12 above, fuse = 0.  Waits for the handle's stream and
+ * and V = 4, ZT = 12 above (V = 1 where the FP32 pair layout does not apply), fuse = 0.  Waits for the handle's stream and
  * recomputes the moment partials of the current state.  LBS_ERR_ARG outside the
  * ranges. */
 lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT, int fuse);

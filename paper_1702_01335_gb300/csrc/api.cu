@@ -748,6 +748,12 @@ lbs_status lbs_batch_create(lbs_handle* out, const lbs_instance_desc* desc, int 
     // thread, more CTAs); large ones take the throughput tiling.  Finalisation apart.
     h->V = work >= (1L << 22) ? 4 : 1;
     h->ZT = work >= (1L << 22) ? 12 : 4;
+    // the FP32 full model with V = 2, 4 takes velocities in pairs (64-bit words), which
+    // needs Q / 2 even in every instance; else one velocity per thread
+    for (int b = 0; b < n; ++b)
+        if (h->fp32 && !h->reduced &&
+            (desc[b].orders.Qx * std::max(desc[b].orders.Qy, 2) * desc[b].orders.Qz_half) % 2)
+            h->V = 1;
     h->fuse = 0;
     if (cuda_stream) {
         h->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -913,6 +919,10 @@ lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT, int fuse)
 {
     if (!h || (V != 1 && V != 2 && V != 4) || ZT < 3 || ZT > kMaxZT || fuse < 0 || fuse > 2)
         return fail(LBS_ERR_ARG, "tiling needs V in {1, 2, 4}, 3 <= ZT <= 64 and fuse in {0, 1, 2}");
+    if (h->fp32 && !h->reduced && V != 1)
+        for (int b = 0; b < h->ninst; ++b)
+            if ((h->ih[b].Q / 2) % 2)
+                return fail(LBS_ERR_ARG, "V = 2, 4 in FP32 (velocity pairs) needs Q / 2 even in every instance");
     CK(cudaStreamSynchronize(h->stream));
     drop_graph(h);
     if (fuse == 2 && !h->stream2) {

@@ -83,7 +83,7 @@ size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride)
 {
     const int KC = kThreads * V;
     (void)stage;
-    return stage_smem(zn, KC, G, fp32 ? 4 : 8, 8, rstride).total;
+    return stage_smem(zn, KC, G, fp32 ? 4 : 8, fp32 ? 4 : 8, rstride).total;  // element, accumulator
 }
 
 template <typename T>

@@ -137,30 +137,33 @@ static __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
-// FP32 form: the same weights with sigma_q^2 floored at 1e-37 (branch free,
-// hardware reciprocals).  As sigma_q -> 0 the floor gives exactly the limits
-// of Table (weno); it changes nothing while sigma_q^2 > 1e-30, i.e. for
-// differences above the FP32 resolution of O(1) normalised populations.  The
-// rounded weights only multiply the small corrections e_q.
+// FP32 form, the same stencils in constant-light operations (the multiples 2, 4, 5, 7 of
+// the differences built by additions; two constants in all, which the packed form below
+// keeps in registers): 4 sigma_q = 13/3 a_q^2 + b_q^2 and the ideal weights scaled by 10
+// to (1, 6, 3), common factors that cancel in the normalised weights.  (4 sigma_q)^2 is
+// floored at 1.6e-36 (sigma_q^2 at 1e-37; branch free, hardware reciprocals): as
+// sigma_q -> 0 the floor gives exactly the limits of Table (weno), and it changes nothing
+// while sigma_q^2 > 1e-30, i.e. for differences above the FP32 resolution of O(1)
+// normalised populations.  The rounded weights only multiply the small corrections e_q.
+constexpr float kWenoK = 13.f / 3.f, kWenoFloor = 1.6e-36f;
 template <>
 __device__ __forceinline__ float weno5_corr<float>(float v0, float v1, float v2, float v3, float v4)
 {
     const float d0 = v0 - v2, d1 = v1 - v2, d3 = v3 - v2, d4 = v4 - v2;
-    const float e1 = fmaf(2.f, d0, -7.f * d1);   // 6 (c1 - v2)
-    const float e2 = fmaf(2.f, d3, -d1);         // 6 (c2 - v2)
-    const float e3 = fmaf(5.f, d3, -d4);         // 6 (c3 - v2)
-    float a = d0 - 2.f * d1, b = fmaf(-4.f, d1, d0);          // v0-2v1+v2, v0-4v1+3v2
-    const float s1 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
-    a = d1 + d3;                                             // v1-2v2+v3
-    b = d1 - d3;                                             // v1-v3
-    const float s2 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
-    a = fmaf(-2.f, d3, d4);                                  // v2-2v3+v4
-    b = fmaf(-4.f, d3, d4);                                  // 3v2-4v3+v4
-    const float s3 = fmaf(13.f / 12.f * a, a, 0.25f * b * b);
-    const float w1 = 0.1f * rcp_approx(fmaf(s1, s1, 1e-37f));
-    const float w2 = 0.6f * rcp_approx(fmaf(s2, s2, 1e-37f));
-    const float w3 = 0.3f * rcp_approx(fmaf(s3, s3, 1e-37f));
-    const float inv = (1.f / 6.f) * rcp_approx(w1 + w2 + w3);
+    const float t = d1 + d1, u = d3 + d3;
+    const float a1 = d0 - t, b1 = a1 - t;    // v0-2v1+v2, v0-4v1+3v2
+    const float a2 = d1 + d3, b2 = d1 - d3;  // v1-2v2+v3, v1-v3
+    const float a3 = d4 - u, b3 = a3 - u;    // v2-2v3+v4, 3v2-4v3+v4
+    const float e1 = (a1 + b1) - d1;         // 6 (c1 - v2) = 2 d0 - 7 d1
+    const float e2 = u - d1;                 // 6 (c2 - v2) = 2 d3 - d1
+    const float e3 = (u + d3) - a3;          // 6 (c3 - v2) = 5 d3 - d4
+    const float s1 = fmaf(kWenoK, a1 * a1, b1 * b1);
+    const float s2 = fmaf(kWenoK, a2 * a2, b2 * b2);
+    const float s3 = fmaf(kWenoK, a3 * a3, b3 * b3);
+    const float w1 = rcp_approx(fmaf(s1, s1, kWenoFloor));
+    const float w2 = 6.f * rcp_approx(fmaf(s2, s2, kWenoFloor));
+    const float w3 = 3.f * rcp_approx(fmaf(s3, s3, kWenoFloor));
+    const float inv = rcp_approx(6.f * ((w1 + w2) + w3));
     return fmaf(w1, e1, fmaf(w2, e2, w3 * e3)) * inv;
 }
 
@@ -192,27 +195,26 @@ static __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
 static __device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
 
 // weno5_corr<float> for two velocities at once (the same operations, element by element;
-// the reciprocals stay scalar): half the issued arithmetic of two scalar calls
+// the reciprocals and the multiplications by the scaled ideal weights stay scalar): about
+// half the issued arithmetic of two scalar calls
 static __device__ __forceinline__ float2 weno5_corr2(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4)
 {
     const float2 d0 = sub2(v0, v2), d1 = sub2(v1, v2), d3 = sub2(v3, v2), d4 = sub2(v4, v2);
-    const float2 e1 = fma2(splat(2.f), d0, mul2(splat(-7.f), d1));
-    const float2 e2 = fma2(splat(2.f), d3, mul2(splat(-1.f), d1));
-    const float2 e3 = fma2(splat(5.f), d3, mul2(splat(-1.f), d4));
-    float2 a = fma2(splat(-2.f), d1, d0), b = fma2(splat(-4.f), d1, d0);
-    const float2 s1 = fma2(mul2(splat(13.f / 12.f), a), a, mul2(mul2(splat(0.25f), b), b));
-    a = add2(d1, d3);
-    b = sub2(d1, d3);
-    const float2 s2 = fma2(mul2(splat(13.f / 12.f), a), a, mul2(mul2(splat(0.25f), b), b));
-    a = fma2(splat(-2.f), d3, d4);
-    b = fma2(splat(-4.f), d3, d4);
-    const float2 s3 = fma2(mul2(splat(13.f / 12.f), a), a, mul2(mul2(splat(0.25f), b), b));
-    const float2 q1 = fma2(s1, s1, splat(1e-37f)), q2 = fma2(s2, s2, splat(1e-37f)), q3 = fma2(s3, s3, splat(1e-37f));
-    const float2 w1 = mul2(splat(0.1f), make_float2(rcp_approx(q1.x), rcp_approx(q1.y)));
-    const float2 w2 = mul2(splat(0.6f), make_float2(rcp_approx(q2.x), rcp_approx(q2.y)));
-    const float2 w3 = mul2(splat(0.3f), make_float2(rcp_approx(q3.x), rcp_approx(q3.y)));
+    const float2 t = add2(d1, d1), u = add2(d3, d3);
+    const float2 a1 = sub2(d0, t), b1 = sub2(a1, t);
+    const float2 a2 = add2(d1, d3), b2 = sub2(d1, d3);
+    const float2 a3 = sub2(d4, u), b3 = sub2(a3, u);
+    const float2 e1 = sub2(add2(a1, b1), d1), e2 = sub2(u, d1), e3 = sub2(add2(u, d3), a3);
+    const float2 K = splat(kWenoK), F = splat(kWenoFloor);
+    const float2 s1 = fma2(K, mul2(a1, a1), mul2(b1, b1));
+    const float2 s2 = fma2(K, mul2(a2, a2), mul2(b2, b2));
+    const float2 s3 = fma2(K, mul2(a3, a3), mul2(b3, b3));
+    const float2 q1 = fma2(s1, s1, F), q2 = fma2(s2, s2, F), q3 = fma2(s3, s3, F);
+    const float2 w1 = make_float2(rcp_approx(q1.x), rcp_approx(q1.y));
+    const float2 w2 = make_float2(6.f * rcp_approx(q2.x), 6.f * rcp_approx(q2.y));
+    const float2 w3 = make_float2(3.f * rcp_approx(q3.x), 3.f * rcp_approx(q3.y));
     const float2 sw = add2(add2(w1, w2), w3);
-    const float2 inv = mul2(splat(1.f / 6.f), make_float2(rcp_approx(sw.x), rcp_approx(sw.y)));
+    const float2 inv = make_float2(rcp_approx(6.f * sw.x), rcp_approx(6.f * sw.y));
     return mul2(fma2(w1, e1, fma2(w2, e2, mul2(w3, e3))), inv);
 }
 
@@ -453,15 +455,15 @@ static __device__ __forceinline__ bool store_cell(const InstDev& I, int cell, co
     return !bad;
 }
 
-// The velocity the stage kernel took its moments about: the cell record's u after
-// stage 3 (the stage record is still in place when the finalisation reads it), else 0.
+// The velocity the stage kernel took its moments about: the u of the cell's record of
+// the stage (still in place when the finalisation reads it); 0 for the analysis pass.
 template <typename T>
 __device__ __forceinline__ void moment_origin(const InstDev& I, int cell, int stage, double* ur)
 {
     const T* rc = static_cast<const T*>(I.rec) + (size_t)cell * I.rec_stride;
-    ur[0] = stage == 3 ? double(rc[R_UX]) : 0.0;
-    ur[1] = stage == 3 ? double(rc[R_UY]) : 0.0;
-    ur[2] = stage == 3 ? double(rc[R_UZ]) : 0.0;
+    ur[0] = stage > 0 ? double(rc[R_UX]) : 0.0;
+    ur[1] = stage > 0 ? double(rc[R_UY]) : 0.0;
+    ur[2] = stage > 0 ? double(rc[R_UZ]) : 0.0;
 }
 
 // The macroscopic state from the partials' moments about ur (sums over the deviations
@@ -804,12 +806,12 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     const int rstride = I.rec_stride;
-    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(double), rstride);
+    const StageSmem L = stage_smem(zn, KC, G, sizeof(T), sizeof(A), rstride);
     T* Fs = reinterpret_cast<T*>(smem_raw + L.fin);   // d rows: cells z0-3 .. z0+zn+2
     T* recs = reinterpret_cast<T*>(smem_raw + L.rec); // records of cells z0 .. z0+zn-1
     T* gsm = reinterpret_cast<T*>(smem_raw + L.g);
     T* idzs = reinterpret_cast<T*>(smem_raw + L.idz);
-    double* red = reinterpret_cast<double*>(smem_raw + L.red);  // per-warp moment sums, summed in FP64
+    A* red = reinterpret_cast<A*>(smem_raw + L.red);  // per-warp moment sums
 
     // Buffers (Eq. rk3 in increment form, F_l the step's start state d):
     //   stage 1: d1 = dt L[F_l]                  -> the other of F0 / F1
@@ -853,13 +855,20 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
 
     // per-velocity constants: p (and |p_z| for the fluxes), the weight w and |p|^2 for the
     // moments (formed from them per cell: fewer registers than 13 weighted monomials)
+    // FP32 with an even V: the thread's velocities are adjacent pairs (2 tid, 2 tid + 1,
+    // 2 tid + 2 kThreads, ...), so that a pair is one 64-bit word in memory and one
+    // operand of the packed FP32 instructions; else tid + v kThreads.  voff(v) is v's
+    // offset from the thread's first velocity tbase.
+    constexpr bool kPair = sizeof(T) == 4 && V % 2 == 0;
+    const int tbase = kPair ? 2 * tid : tid;
+    auto voff = [](int v) { return kPair ? (v & 1) + (v >> 1) * 2 * kThreads : v * kThreads; };
     int ii[V], jj[V], zz[V], kl[V];
     T px[V], py[V], pz[V], apz[V];
     A wv[V], yv[V], p2v[V], wm[V];  // weight; p_y for the moments; |p|^2; w of the mass flux
     bool ok[V], chi[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        kl[v] = tid + v * kThreads;
+        kl[v] = tbase + voff(v);
         ok[v] = kl[v] < kn;
         const int kc = ok[v] ? k0 + kl[v] : kend - 1;
         jj[v] = kc % Qy;
@@ -983,6 +992,181 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
 
     __syncthreads();  // per-cell factors complete
 
+    if constexpr (kPair && !RED) {
+        // ---- 5 (FP32, full model). The march of section 5 below with the thread's
+        // velocities as adjacent pairs: the same operations, two velocities per packed
+        // FP32 instruction; rows, increments and outputs move as 64-bit pairs and the two
+        // 16-bit residuals of a pair as one 32-bit word.  Q / 2 is even (the host's
+        // condition for this layout), so a chunk start k0 and its length kn are even, a
+        // pair lies wholly inside or wholly past the chunk, and every pair address is
+        // 8-byte aligned.
+        constexpr int NP = V / 2;
+        const long rstep2 = sgc ? -(long)(KC / 2) : (long)(KC / 2);  // a row, in pairs
+        const float2* rp2 = reinterpret_cast<const float2*>(Fs + (sgc ? (size_t)(zn + 5) * KC : 0)) + tid;
+        const int sdir = sgc ? -1 : 1;
+        const int zw0 = sgc ? z0 + zn + 2 : z0 - 3;  // the cell of window row 0 at step 0
+        const float* __restrict__ Dgf = reinterpret_cast<const float*>(Dg);
+        // the increments of the cell of a window row (zero for a ghost row)
+        auto inc_row2 = [&](int s, float2(&out)[NP]) {
+            const bool in = kD && (unsigned)s < (unsigned)Nz;
+            const float2* q = reinterpret_cast<const float2*>(Dgf + (long)s * Q + k0) + tid;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) out[p] = in && ok[2 * p] ? __ldg(q + p * kThreads) : make_float2(0.f, 0.f);
+        };
+        float2 PX[NP], PY[NP], PZ[NP], NAPZ[NP], WV[NP];  // per pair: p, -|p_z|, weights
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            PX[p] = make_float2(px[2 * p], px[2 * p + 1]);
+            PY[p] = make_float2(py[2 * p], py[2 * p + 1]);
+            PZ[p] = make_float2(pz[2 * p], pz[2 * p + 1]);
+            NAPZ[p] = make_float2(-apz[2 * p], -apz[2 * p + 1]);
+            WV[p] = make_float2(wv[2 * p], wv[2 * p + 1]);
+        }
+        float2 W[NP][6], CM[NP], DN[NP], DIN[NP];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            inc_row2(zw0 + d * sdir, DN);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) W[p][d] = add2(rp2[d * rstep2 + p * kThreads], DN[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) CM[p] = weno5_corr2(W[p][0], W[p][1], W[p][2], W[p][3], W[p][4]);
+        int sn = zw0 + 6 * sdir;
+        inc_row2(sn, DN);
+        const float2 DT = splat(float(I.dt));
+        const long ostep2 = sgc ? -(long)(Q / 2) : (long)(Q / 2);
+        const size_t orow0 = (size_t)(sgc ? z0 + zn - 1 : z0) * Q + k0 + tbase;
+        float2* outp = reinterpret_cast<float2*>(reinterpret_cast<float*>(Fout) + orow0);
+        const float2* __restrict__ dop = kD ? reinterpret_cast<const float2*>(Dgf + orow0) : nullptr;
+        unsigned* lop = kLo && STAGE == 3 ? reinterpret_cast<unsigned*>(I.L0 + orow0) : nullptr;
+        unsigned LQN[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            LQN[p] = kLo && STAGE == 3 && ok[2 * p] ? __ldcg(lop + p * kThreads) : 0u;
+            DIN[p] = kD && ok[2 * p] ? __ldg(dop + p * kThreads) : make_float2(0.f, 0.f);
+        }
+#pragma unroll 1
+        for (int c = 0; c < zn; ++c) {
+            unsigned LQC[NP];
+            float2 DC[NP], DIC[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                LQC[p] = LQN[p];
+                if (kLo && STAGE == 3 && ok[2 * p] && c + 1 < zn) LQN[p] = __ldcg(lop + ostep2 + p * kThreads);
+                DIC[p] = DIN[p];
+                if (kD && ok[2 * p] && c + 1 < zn) DIN[p] = __ldg(dop + ostep2 + p * kThreads);
+                DC[p] = DN[p];
+            }
+            if (kD && c + 1 < zn) {
+                sn += sdir;
+                inc_row2(sn, DN);
+            }
+            const int cc = sgc ? zn - 1 - c : c;
+            const float* sc = reinterpret_cast<const float*>(recs) + (size_t)cc * rstride;
+            const float* gc = reinterpret_cast<const float*>(gsm) + cc * G;
+            const float2* rn2 = rp2 + (c + 6) * rstep2;
+            const float2* own2 = reinterpret_cast<const float2*>(Fs + (size_t)(cc + 3) * KC) + tid;
+            float2 UX, UY, UZ, QX, QY, QZ, NITAU, CS, I5T, IDZ;
+            if (STAGE > 0) {
+                UX = splat(sc[R_UX]); UY = splat(sc[R_UY]); UZ = splat(sc[R_UZ]);
+                QX = splat(sc[R_QX]); QY = splat(sc[R_QY]); QZ = splat(sc[R_QZ]);
+                NITAU = splat(-sc[R_ITAU]); CS = splat(sc[R_CS]); I5T = splat(sc[R_I5T]);
+                IDZ = splat(float(idzs[cc]));
+            }
+            float2 S2[kNMom];  // the thread's moment sums, one lane per velocity of a pair
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int v0 = 2 * p, v1 = v0 + 1;
+                const float2 f = W[p][3];
+                float2 out = f, X = PX[p], Y = PY[p], Z = PZ[p], P2;
+                if (STAGE > 0) {
+                    const float2 cp = weno5_corr2(W[p][1], W[p][2], W[p][3], W[p][4], W[p][5]);
+                    // the Shakhov target's deviation from 1, (1 + dx)(1 + dy)(1 + dz)(1 + S) - 1
+                    X = sub2(PX[p], UX);
+                    Y = sub2(PY[p], UY);
+                    Z = sub2(PZ[p], UZ);
+                    P2 = fma2(Z, Z, fma2(Y, Y, mul2(X, X)));
+                    const float2 xq = fma2(Z, QZ, fma2(Y, QY, mul2(X, QX)));
+                    const float2 S = mul2(mul2(CS, fma2(P2, I5T, splat(-1.f))), xq);
+                    const float2 DXf = make_float2(gc[ii[v0]], gc[ii[v1]]);
+                    const float2 DYf = make_float2(gc[Qx + jj[v0]], gc[Qx + jj[v1]]);
+                    const float2 DZf = make_float2(gc[Qx + Qy + zz[v0] - zm_lo], gc[Qx + Qy + zz[v1] - zm_lo]);
+                    const float2 a = fma2(DXf, DYf, add2(DXf, DYf));
+                    const float2 b = fma2(a, DZf, add2(a, DZf));
+                    const float2 tgt = fma2(b, S, add2(b, S));
+                    // the departure from the target from its parts (see section 5)
+                    float2 h = f, dinc = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);
+                    if (STAGE >= 2) {
+                        h = own2[p * kThreads];
+                        dinc = DIC[p];
+                    }
+                    if constexpr (kLo && STAGE == 3)
+                        lo = make_float2(lo_decode(static_cast<unsigned short>(LQC[p] & 0xffffu), h.x),
+                                         lo_decode(static_cast<unsigned short>(LQC[p] >> 16), h.y));
+                    const float2 dep = STAGE >= 2 ? add2(add2(sub2(h, tgt), dinc), lo) : sub2(f, tgt);
+                    // Eq. (flux) and the relaxation: -|p_z| div / dz - dep / tau
+                    const float2 div = add2(sub2(W[p][3], W[p][2]), sub2(cp, CM[p]));
+                    const float2 Lv = fma2(dep, NITAU, mul2(mul2(NAPZ[p], div), IDZ));
+                    float2 st;
+                    if (STAGE == 1) {
+                        st = mul2(DT, Lv);
+                        out = add2(f, st);
+                    } else if (STAGE == 2) {
+                        st = mul2(splat(0.25f), fma2(DT, Lv, dinc));
+                        out = add2(h, st);
+                    } else {
+                        const float2 inc = mul2(splat(float(2.0 / 3.0)), fma2(DT, Lv, dinc));
+                        if constexpr (kLo) {
+                            const float2 t = add2(lo, inc);
+                            const float2 h2 = add2(h, t);
+                            const float2 lo2 = sub2(t, sub2(h2, h));
+                            if (ok[v0])
+                                __stcg(lop + p * kThreads, unsigned(lo_encode(lo2.x, h2.x)) |
+                                                               (unsigned(lo_encode(lo2.y, h2.y)) << 16));
+                            st = h2;
+                        } else {
+                            st = add2(h, inc);
+                        }
+                        out = st;
+                    }
+                    if (ok[v0]) __stcg(outp + p * kThreads, st);
+                    CM[p] = cp;
+                } else {
+                    P2 = fma2(Z, Z, fma2(Y, Y, mul2(X, X)));
+                }
+#pragma unroll
+                for (int d = 0; d < 5; ++d) W[p][d] = W[p][d + 1];
+                W[p][5] = kD ? add2(rn2[p * kThreads], DC[p]) : rn2[p * kThreads];
+                // the moments about the record's u (section 5): w f times 1, xi_a,
+                // xi_a xi_b, |xi|^2 xi_a; pairs past the chunk contribute zero
+                const float2 o = ok[v0] ? mul2(out, WV[p]) : make_float2(0.f, 0.f);
+                const float2 oX = mul2(o, X), oY = mul2(o, Y), oZ = mul2(o, Z), oP = mul2(o, P2);
+                if (p == 0) {
+                    S2[0] = o; S2[1] = oX; S2[2] = oY; S2[3] = oZ;
+                    S2[4] = mul2(oX, X); S2[5] = mul2(oY, Y); S2[6] = mul2(oZ, Z);
+                    S2[7] = mul2(oX, Y); S2[8] = mul2(oX, Z); S2[9] = mul2(oY, Z);
+                    S2[10] = mul2(oP, X); S2[11] = mul2(oP, Y); S2[12] = mul2(oP, Z);
+                } else {
+                    S2[0] = add2(S2[0], o); S2[1] = add2(S2[1], oX); S2[2] = add2(S2[2], oY);
+                    S2[3] = add2(S2[3], oZ);
+                    S2[4] = fma2(oX, X, S2[4]); S2[5] = fma2(oY, Y, S2[5]); S2[6] = fma2(oZ, Z, S2[6]);
+                    S2[7] = fma2(oX, Y, S2[7]); S2[8] = fma2(oX, Z, S2[8]); S2[9] = fma2(oY, Z, S2[9]);
+                    S2[10] = fma2(oP, X, S2[10]); S2[11] = fma2(oP, Y, S2[11]); S2[12] = fma2(oP, Z, S2[12]);
+                }
+            }
+            float acc[16];
+#pragma unroll
+            for (int a = 0; a < kNMom; ++a) acc[a] = S2[a].x + S2[a].y;
+#pragma unroll
+            for (int a = kNMom; a < 16; ++a) acc[a] = 0.f;
+            const float tot = reduce_scatter16<float>(acc, lane);
+            const int m = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+            if ((lane & 1) == 0) red[((size_t)cc * (kThreads / 32) + warp) * 16 + m] = tot;
+            outp += ostep2;
+            if (kD) dop += ostep2;
+            if (kLo && STAGE == 3) lop += ostep2;
+        }
+    } else {
     // ---- 5. march through the z-range in the upwind direction of the chunk: up
     // (p_z > 0) from z0, down (p_z < 0) from z0+zn-1.  At march step c the register
     // window holds the cells s-3 .. s+2 seen from upwind (s+3 .. s-2 going down), so
@@ -995,15 +1179,15 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     // through the read-only path (this launch does not write it).  Window row cd at step c
     // holds cell zw0 + (c + cd) sdir; a ghost row (a cell outside 0 .. Nz-1) takes zero,
     // its shared-memory value being the whole stage input.  Thread-based pointers: the
-    // thread's velocity v sits at + v kThreads.
+    // thread's velocity v sits at + voff(v).
     const int sdir = sgc ? -1 : 1;
     const int zw0 = sgc ? z0 + zn + 2 : z0 - 3;
-    const T* __restrict__ dq = Dg + k0 + tid;
+    const T* __restrict__ dq = Dg + k0 + tbase;
     auto inc_row = [&](int s, T(&out)[V]) {
         const bool in = kD && (unsigned)s < (unsigned)Nz;
         const T* p = dq + (long)s * Q;
 #pragma unroll
-        for (int v = 0; v < V; ++v) out[v] = in && ok[v] ? __ldg(p + v * kThreads) : T(0);
+        for (int v = 0; v < V; ++v) out[v] = in && ok[v] ? __ldg(p + voff(v)) : T(0);
     };
     // cm: the WENO correction of the interface behind (its flux is |p_z| (w2 + cm))
     T w[V][6], cm[V], dn[V];
@@ -1019,24 +1203,31 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     inc_row(sn, dn);
     const T dt = T(I.dt);
     const long ostep = sgc ? -(long)Q : (long)Q;
-    const size_t orow0 = (size_t)(sgc ? z0 + zn - 1 : z0) * Q + k0 + tid;  // the first cell, thread's column
+    const size_t orow0 = (size_t)(sgc ? z0 + zn - 1 : z0) * Q + k0 + tbase;  // the first cell, thread's column
     T* outp = Fout + orow0;
     const T* __restrict__ dop = kD ? Dg + orow0 : nullptr;  // the increment of the cell
     unsigned short* lop = kLo && STAGE == 3 ? I.L0 + orow0 : nullptr;
     // stage 3 (FP32): the residuals of the next cell are loaded one march step ahead, so
     // that their global-memory latency overlaps a step's arithmetic
+    // the increments of the next cell (stages 2, 3) likewise
     unsigned short lqn[V];
+    T din[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) lqn[v] = kLo && STAGE == 3 && ok[v] ? __ldcg(lop + v * kThreads) : 0;
+    for (int v = 0; v < V; ++v) {
+        lqn[v] = kLo && STAGE == 3 && ok[v] ? __ldcg(lop + voff(v)) : 0;
+        din[v] = kD && ok[v] ? __ldg(dop + voff(v)) : T(0);
+    }
     constexpr bool kPack = sizeof(T) == 4 && V % 2 == 0;  // moments of two velocities per packed op
 #pragma unroll 1  // unrolling the z-march only adds instruction-cache misses
     for (int c = 0; c < zn; ++c) {
         unsigned short lqc[V];
-        T dc[V];  // increments of the window row this step loads
+        T dc[V], dic[V];  // increments of the window row this step loads and of the cell
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             lqc[v] = lqn[v];
-            if (kLo && STAGE == 3 && ok[v] && c + 1 < zn) lqn[v] = __ldcg(lop + ostep + v * kThreads);
+            if (kLo && STAGE == 3 && ok[v] && c + 1 < zn) lqn[v] = __ldcg(lop + ostep + voff(v));
+            dic[v] = din[v];
+            if (kD && ok[v] && c + 1 < zn) din[v] = __ldg(dop + ostep + voff(v));
             dc[v] = dn[v];
         }
         if (kD && c + 1 < zn) {
@@ -1110,7 +1301,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                 T h = f, dinc = T(0), lo = T(0);
                 if (STAGE >= 2) {
                     h = own[kl[v]];
-                    dinc = ok[v] ? __ldg(dop + v * kThreads) : T(0);
+                    dinc = dic[v];
                 }
                 if constexpr (kLo && STAGE == 3) lo = lo_decode(lq, h);
                 const T dep = STAGE >= 2 ? ((h - tgt) + dinc) + lo : f - tgt;
@@ -1135,27 +1326,28 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                         const T t = lo + inc;
                         const T h2 = h + t;
                         const T lo2 = t - (h2 - h);
-                        if (ok[v]) __stcg(lop + v * kThreads, lo_encode(lo2, h2));
+                        if (ok[v]) __stcg(lop + voff(v), lo_encode(lo2, h2));
                         st = h2;
                     } else {
                         st = h + inc;
                     }
                     out = st;
                 }
-                if (ok[v]) __stcg(outp + v * kThreads, st);
+                if (ok[v]) __stcg(outp + voff(v), st);
                 cm[v] = cp;
             }
 #pragma unroll
             for (int d = 0; d < 5; ++d) w[v][d] = w[v][d + 1];
             w[v][5] = wn;
-            // the moments: stages 0-2 of psi(p) (for the records), stage 3 of psi(p - u_r)
-            // about the velocity u_r of the cell's record, so that the third moments are
+            // the moments: of psi(p - u_r) about the velocity u_r of the cell's record
+            // (stage 0, which has no record: of psi(p)), so that the third moments are
             // close to the heat flux itself instead of its sum with terms of size u |p|^2
-            // that cancel it (160-fold in config C1); the finalisation adds the rest
+            // that cancel it (160-fold in config C1), and the Shakhov factor's xi and
+            // |xi|^2 serve as the monomials' factors; the finalisation adds the rest
             // state's moments about u_r.  Columns past the chunk hold no data (their
             // shared memory is never written) and contribute zero.
             ov[v] = ok[v] ? A(out) * wv[v] : A(0);
-            if (STAGE == 3) {
+            if (STAGE > 0) {
                 mx[v] = A(ex); my[v] = A(ey); mz[v] = A(ez); m2[v] = A(xi2);
             } else {
                 mx[v] = A(px[v]); my[v] = yv[v]; mz[v] = A(pz[v]); m2[v] = p2v[v];
@@ -1220,13 +1412,17 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         if (kD) dop += ostep;
         if (kLo && STAGE == 3) lop += ostep;
     }
+    }  // the scalar march
     __syncthreads();
+    // the chunk's partial of each cell: the warps' sums added in the accumulation type
+    // (FP32 storage: the FP64 pipe, a small fraction of the FP32 rate here, converts
+    // once per cell and moment), stored in FP64 for the sum over chunks
     for (int e = tid; e < zn * kNMom; e += kThreads) {
         const int c = e / kNMom, a = e - c * kNMom;
-        double s = 0.0;
+        A s = red[(size_t)c * (kThreads / 32) * 16 + a];
 #pragma unroll
-        for (int q = 0; q < kThreads / 32; ++q) s += red[((size_t)c * (kThreads / 32) + q) * 16 + a];
-        I.partial[((size_t)tile.chunk * kNMom + a) * Nz + z0 + c] = s;
+        for (int q = 1; q < kThreads / 32; ++q) s += red[((size_t)c * (kThreads / 32) + q) * 16 + a];
+        I.partial[((size_t)tile.chunk * kNMom + a) * Nz + z0 + c] = double(s);
     }
 
     // ---- 6. outgoing WENO flux of the stage output through the wall interfaces (for
