@@ -15,11 +15,12 @@
 
 namespace lbs {
 cudaError_t launch_stage(int fp32, int red, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
-                         int ntiles, size_t smem, int fuse, int ninst, int maxNz, int fin_warp, cudaStream_t st);
+                         int ntiles, size_t smem, int fuse, int ninst, int maxNz, int fin_warp, int nb,
+                         cudaStream_t st);
 cudaError_t launch_stage_only(int fp32, int red, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
                               int ntiles, size_t smem, int fuse, cudaStream_t st);
 cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int ninst, int maxNz, int fin_warp,
-                            cudaStream_t st);
+                            int nb, cudaStream_t st);
 cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,
                         cudaStream_t st);
 size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride);
@@ -69,7 +70,7 @@ struct Pool {  // bump allocator over one device allocation
 struct lbs_solver {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int fp32 = 0, esize = 8, V = 1, ZT = 16, fuse = 1, ninst = 0, maxNz = 0;
+    int fp32 = 0, esize = 8, V = 1, ZT = 16, fuse = 1, ninst = 0, maxNz = 0, nb = 0;
     int fin_mode = 0, fin_warp = 0;  // finalisation: 0 auto, 1 thread per cell, 2 warp per cell
     int reduced = 0;                 // the batch runs the phi / chi model (all instances alike)
     std::vector<InstHost> ih;
@@ -270,6 +271,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         I.Ny = I.reduced ? 1 : std::min(d.orders.N_eq, I.Qy - 1);
         I.Nzq = std::min(d.orders.N_eq, I.Qz - 1);
         h->maxNz = std::max(h->maxNz, I.Nz);
+        h->nb = std::max(h->nb, std::max(I.Nx, std::max(I.Ny, I.Nzq)));  // the batch's largest order
     }
     build_tiles(h, tiles);
     for (int b = 0; b < h->ninst; ++b) {
@@ -532,7 +534,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
 static lbs_status analyse(lbs_solver* h)
 {
     CK(launch_stage(h->fp32, h->reduced, h->V, 0, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->ninst, h->maxNz,
-                    h->fin_warp, h->stream));
+                    h->fin_warp, h->nb, h->stream));
     return LBS_OK;
 }
 
@@ -546,7 +548,7 @@ static lbs_status enqueue_step(lbs_solver* h)
     if (!split(h)) {
         for (int s = 1; s <= 3; ++s)
             CK(launch_stage(h->fp32, h->reduced, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->ninst,
-                            h->maxNz, h->fin_warp, h->stream));
+                            h->maxNz, h->fin_warp, h->nb, h->stream));
         return LBS_OK;
     }
     CK(cudaEventRecord(h->ev_fork, h->stream));
@@ -555,10 +557,10 @@ static lbs_status enqueue_step(lbs_solver* h)
     // array, a range of tiles); the finalisation kernels take a range of instances
     for (int s = 1; s <= 3; ++s) {
         CK(launch_stage_only(h->fp32, h->reduced, h->V, s, h->d_inst, h->d_tiles, h->ntilesA, h->smem, 0, h->stream));
-        CK(launch_finalize(h->fp32, s, h->d_inst, h->nA, h->maxNz, h->fin_warp, h->stream));
+        CK(launch_finalize(h->fp32, s, h->d_inst, h->nA, h->maxNz, h->fin_warp, h->nb, h->stream));
         CK(launch_stage_only(h->fp32, h->reduced, h->V, s, h->d_inst, h->d_tiles + h->ntilesA, h->ntiles - h->ntilesA, h->smem,
                              0, h->stream2));
-        CK(launch_finalize(h->fp32, s, h->d_inst + h->nA, h->ninst - h->nA, h->maxNz, h->fin_warp, h->stream2));
+        CK(launch_finalize(h->fp32, s, h->d_inst + h->nA, h->ninst - h->nA, h->maxNz, h->fin_warp, h->nb, h->stream2));
     }
     CK(cudaEventRecord(h->ev_join, h->stream2));
     CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
@@ -893,7 +895,7 @@ lbs_status lbs_profile_steps(lbs_handle h, long nsteps, double* out_ms)
         for (int s = 1; s <= 3; ++s) {
             CK(launch_stage_only(h->fp32, h->reduced, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->stream));
             CK(cudaEventRecord(ev[2 * s - 1], h->stream));
-            if (!(h->fuse & 1)) CK(launch_finalize(h->fp32, s, h->d_inst, h->ninst, h->maxNz, h->fin_warp, h->stream));
+            if (!(h->fuse & 1)) CK(launch_finalize(h->fp32, s, h->d_inst, h->ninst, h->maxNz, h->fin_warp, h->nb, h->stream));
             CK(cudaEventRecord(ev[2 * s], h->stream));
         }
         CK(cudaEventSynchronize(ev[6]));

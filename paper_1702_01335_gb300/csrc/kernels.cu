@@ -5,8 +5,10 @@
 
 namespace lbs {
 
-// ---- separate finalisation launches (used when the stage kernel does not fuse them)
-template <typename T>
+// ---- separate finalisation launches (used when the stage kernel does not fuse them).
+// NB bounds the expansion orders of the batch (the unrolled coefficient loops of the
+// record run to NB, not to the largest order kMaxN).
+template <typename T, int NB>
 __global__ void __launch_bounds__(32) finalize_cells(const InstDev* __restrict__ insts, int stage)
 {
     __shared__ double red[kRedSlots];
@@ -16,7 +18,7 @@ __global__ void __launch_bounds__(32) finalize_cells(const InstDev* __restrict__
     const int nblk = (I.Nz + 31) >> 5;
     if (blockIdx.x >= nblk || *I.active == 0) return;
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell < I.Nz) finalize_cell<T>(I, cell, stage);
+    if (cell < I.Nz) finalize_cell<T, NB>(I, cell, stage);
     // the instance's last block to finish (threadfence ticket) forms n_w and, after
     // stage 3, the residual; the counter is reset by its last user
     __threadfence();
@@ -88,12 +90,17 @@ size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride)
 
 template <typename T>
 static cudaError_t launch_finalize_t(int stage, const InstDev* d_inst, int ninst, int maxNz, int fin_warp,
-                                     cudaStream_t st)
+                                     int nb, cudaStream_t st)
 {
+    const dim3 g((maxNz + 31) / 32, ninst);
     if (fin_warp)
         finalize_cells_warp<T><<<dim3((maxNz + 3) / 4, ninst), 128, 0, st>>>(d_inst, stage);
+    else if (nb <= 4)
+        finalize_cells<T, 4><<<g, 32, 0, st>>>(d_inst, stage);
+    else if (nb <= 6)
+        finalize_cells<T, 6><<<g, 32, 0, st>>>(d_inst, stage);
     else
-        finalize_cells<T><<<dim3((maxNz + 31) / 32, ninst), 32, 0, st>>>(d_inst, stage);
+        finalize_cells<T, kMaxN><<<g, 32, 0, st>>>(d_inst, stage);
     return cudaGetLastError();
 }
 
@@ -110,20 +117,21 @@ cudaError_t launch_stage_only(int fp32, int red, int V, int stage, const InstDev
 
 // the separate finalisation launches of an unfused stage
 cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int ninst, int maxNz, int fin_warp,
-                            cudaStream_t st)
+                            int nb, cudaStream_t st)
 {
-    return fp32 ? launch_finalize_t<float>(stage, d_inst, ninst, maxNz, fin_warp, st)
-                : launch_finalize_t<double>(stage, d_inst, ninst, maxNz, fin_warp, st);
+    return fp32 ? launch_finalize_t<float>(stage, d_inst, ninst, maxNz, fin_warp, nb, st)
+                : launch_finalize_t<double>(stage, d_inst, ninst, maxNz, fin_warp, nb, st);
 }
 
 // one RK stage (stage 1..3) or the analysis pass (stage 0); without fusion the
 // finalisation follows as two more launches
 cudaError_t launch_stage(int fp32, int red, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
-                         int ntiles, size_t smem, int fuse, int ninst, int maxNz, int fin_warp, cudaStream_t st)
+                         int ntiles, size_t smem, int fuse, int ninst, int maxNz, int fin_warp, int nb,
+                         cudaStream_t st)
 {
     cudaError_t e = launch_stage_only(fp32, red, V, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
     if (e != cudaSuccess || fuse) return e;
-    return launch_finalize(fp32, stage, d_inst, ninst, maxNz, fin_warp, st);
+    return launch_finalize(fp32, stage, d_inst, ninst, maxNz, fin_warp, nb, st);
 }
 
 cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,

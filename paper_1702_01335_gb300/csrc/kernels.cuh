@@ -357,7 +357,7 @@ static __device__ __forceinline__ float lo_decode(unsigned short q, float hi)
 // mass, so the sums are taken over the stored values.  Returns false for a non-finite
 // or non-positive state (a neutral state is written instead).
 // ----------------------------------------------------------------------------
-template <typename T>
+template <typename T, int NB = kMaxN>
 __device__ bool write_record(const InstDev& I, int cell, double n, double in, const double* u, double T_,
                              const double* q)
 {
@@ -380,14 +380,14 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     T* dz = dy + Qy;
     double c[kMaxN + 1], cm[kMaxN + 1], s[3];
     // x: a_l, l >= 1, against He_l / l!
-    full_coeffs(u0, Tc, I.Nx, c);
+    full_coeffs<NB>(u0, Tc, I.Nx, c);
     s[0] = 0.0;
 #pragma unroll 4  // independent nodes: four FP64 chains in flight
     for (int i = 0; i < Qx; ++i) {
         const double* h = I.Hx + i * (I.Nx + 1);
         double g = 0.0;
 #pragma unroll
-        for (int l = 1; l <= kMaxN; ++l)
+        for (int l = 1; l <= NB; ++l)
             if (l <= I.Nx) g += c[l] * h[l];
         const T v = T(g);
         dx[i] = v;
@@ -400,13 +400,13 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
         dy[1] = T(Tc - 1.0);
         s[1] = 1.0;
     } else {
-        full_coeffs(u1, Tc, I.Ny, c);
+        full_coeffs<NB>(u1, Tc, I.Ny, c);
 #pragma unroll 4
         for (int j = 0; j < Qy; ++j) {
             const double* h = I.Hy + j * (I.Ny + 1);
             double g = 0.0;
 #pragma unroll
-            for (int l = 1; l <= kMaxN; ++l)
+            for (int l = 1; l <= NB; ++l)
                 if (l <= I.Ny) g += c[l] * h[l];
             const T v = T(g);
             dy[j] = v;
@@ -414,7 +414,7 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
         }
     }
     // z: b_l on each half range against pi_l / h_l, b_0 - 1/2 in place of b_0
-    half_coeffs_pm(u2, Tc, iT, I.Nzq, I.alpha, I.beta, c, cm);
+    half_coeffs_pm<NB>(u2, Tc, iT, I.Nzq, I.alpha, I.beta, c, cm);
     c[0] -= 0.5;
     cm[0] -= 0.5;
     s[2] = 0.0;
@@ -423,7 +423,7 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
         const double* h = I.Pz + m * (I.Nzq + 1);
         double gp = 0.0, gm = 0.0;
 #pragma unroll
-        for (int l = 0; l <= kMaxN; ++l)
+        for (int l = 0; l <= NB; ++l)
             if (l <= I.Nzq) {
                 gp += c[l] * h[l];
                 gm += cm[l] * h[l];
@@ -483,7 +483,7 @@ static __device__ __forceinline__ void state_about(const InstDev& I, double* mom
 // One cell (one thread): FP64 sum of the per-chunk moment partials (written by
 // other CTAs of this launch, hence read past L1), the macroscopic state, the
 // profiles, W for the residual, and the cell record of the next stage.
-template <typename T>
+template <typename T, int NB = kMaxN>
 __device__ __noinline__ void finalize_cell(const InstDev& I, int cell, int stage)
 {
     const int Nz = I.Nz, nch = I.nchunks;
@@ -509,7 +509,7 @@ __device__ __noinline__ void finalize_cell(const InstDev& I, int cell, int stage
     CellState st;
     state_about(I, mom, ur, st);
     bool bad = !store_cell(I, cell, st);
-    bad |= !write_record<T>(I, cell, st.n, st.in, st.u, st.T, st.q);
+    bad |= !write_record<T, NB>(I, cell, st.n, st.in, st.u, st.T, st.q);
     if (bad) atomicOr(I.status, STATUS_NONFINITE);
 }
 

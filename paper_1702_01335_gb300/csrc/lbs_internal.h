@@ -98,21 +98,23 @@ struct Tile { int inst, z0, zn, chunk, zt; };
 
 // a_l = int g(p; u, T) He_l(p) dp: a_0 = 1, a_1 = u, a_{l+1} = u a_l + l (T - 1) a_{l-1}
 // (from int g p He_l = u a_l + T l a_{l-1} and He_{l+1} = p He_l - l He_{l-1}).
-// Loops below run to the largest order kMaxN and test the actual order inside, so
-// that, unrolled, every array index is a constant and device code keeps the arrays
-// in registers instead of local memory.
+// Loops below run to a bound NB on the order (the largest order kMaxN by default;
+// device code instantiates smaller bounds for batches of low order) and test the
+// actual order inside, so that, unrolled, every array index is a constant and device
+// code keeps the arrays in registers instead of local memory.
 #if defined(__CUDACC__)
 #define LBS_UNROLL _Pragma("unroll")
 #else
 #define LBS_UNROLL
 #endif
 
+template <int NB = kMaxN>
 LBS_HD void full_coeffs(double u, double T, int N, double* a)
 {
     a[0] = 1.0;
     a[1] = u;  // read only when N >= 1
     LBS_UNROLL
-    for (int l = 1; l < kMaxN; ++l)
+    for (int l = 1; l < NB; ++l)
         if (l < N) a[l + 1] = u * a[l] + l * (T - 1.0) * a[l - 1];
 }
 
@@ -170,6 +172,7 @@ LBS_HD double erfc_nonneg(double x)
 // range, written in xi = -p_z >= 0).  The two share g(0) and, through
 // erfc(x) + erfc(-x) = 2, one erfc: the one of |x| is evaluated (no cancellation)
 // and the other is 2 minus it (a value in [1, 2], exact to an ulp).
+template <int NB = kMaxN>
 LBS_HD void half_coeffs_pm(double u, double T, double iT, int N, const double* alpha, const double* beta,
                            double* bp, double* bm)
 {
@@ -185,7 +188,7 @@ LBS_HD void half_coeffs_pm(double u, double T, double iT, int N, const double* a
     Pc[1] = u * Pc[0] + T * g0;                  // used only when K >= 1
     Mc[1] = -u * Mc[0] + T * g0;
     LBS_UNROLL
-    for (int k = 1; k < kMaxN; ++k)
+    for (int k = 1; k < NB; ++k)
         if (k < K) {
             Pc[k + 1] = u * Pc[k] + k * T * Pc[k - 1];
             Mc[k + 1] = -u * Mc[k] + k * T * Mc[k - 1];
@@ -193,18 +196,18 @@ LBS_HD void half_coeffs_pm(double u, double T, double iT, int N, const double* a
     bp[0] = Pc[0];
     bm[0] = Mc[0];
     LBS_UNROLL
-    for (int l = 0; l < kMaxN; ++l) {
+    for (int l = 0; l < NB; ++l) {
         if (l < N) {
             const double al = alpha[l], be = l > 0 ? beta[l] : 0.0;
             double Pn[kMaxN + 1], Mn[kMaxN + 1];
             LBS_UNROLL
-            for (int k = 0; k + l + 1 <= kMaxN; ++k)
+            for (int k = 0; k + l + 1 <= NB; ++k)
                 if (k + l + 1 <= K) {
                     Pn[k] = Pc[k + 1] - al * Pc[k] - (l > 0 ? be * Pp[k] : 0.0);
                     Mn[k] = Mc[k + 1] - al * Mc[k] - (l > 0 ? be * Mp[k] : 0.0);
                 }
             LBS_UNROLL
-            for (int k = 0; k + l + 1 <= kMaxN; ++k) {
+            for (int k = 0; k + l + 1 <= NB; ++k) {
                 Pp[k] = Pc[k];
                 Pc[k] = Pn[k];
                 Mp[k] = Mc[k];
