@@ -172,9 +172,10 @@ def cpu_baseline(p=None, seconds=12.0):
 
 
 def time_to_steady():
-    """Wall time to R < 1e-8 of 256 held-out sweep draws: the plain single-instance
-    solver from rest (a sample of 16, extrapolated), one batched launch from rest, and
-    one batched launch from the warm-start network trained on 2000 steady solves."""
+    """Wall time to R < 1e-7 (FP32 storage; 60000-step budget) of 256 held-out sweep
+    draws: the plain single-instance solver from rest (a sample of 16, extrapolated),
+    one batched launch from rest, and one batched launch from the warm-start network
+    trained on 2000 steady solves."""
     try:
         from paper_1702_01335_gb300.warmstart import evaluate
         r = evaluate(W.warm_start_draws(2000, W.TRAIN_SEED), W.warm_start_draws(256, W.HELDOUT_SEED),

@@ -158,8 +158,13 @@ lbs_status lbs_moments(lbs_handle h, int inst, double* host_out);
 lbs_status lbs_profiles(lbs_handle h, int inst, double* host_out);
 
 /* Residual of the last step of instance inst:
- * R = max over W in {n, u_x, T} of ||W_new - W_old||_2 / max(||W_old||_2, 1e-30)
- * over the interior cells (the paper states no criterion; this is the solver's). */
+ * R = max over W in {n, u_x, T} of ||W_new - W_old||_2 / max(||W_old||_2, s_W)
+ * over the interior cells (the paper states no criterion; this is the solver's),
+ * s_n = s_T = 1e-30 and s_u = max(|u_w| sqrt(Nz), 1e-30): the velocity is measured on
+ * the wall speed where the profile is smaller (it vanishes in the free-molecular limit
+ * and at u_w = 0).  With FP32 storage the moment sums carry FP32 rounding: R levels
+ * off near 1e-8 (a few 1e-8 for strongly rarefied flows), so FP32 targets should be
+ * about 1e-7; FP64 reaches 1e-15. */
 lbs_status lbs_residual(lbs_handle h, int inst, double* out);
 
 /* Number of steps instance inst has taken. */

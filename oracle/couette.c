@@ -482,10 +482,13 @@ static void res_profiles(const oracle_cfg *c, const double *F, double *W)
     }
 }
 
-/* R = max over W in {n, u_x, T} of ||W_new - W_old||_2 / max(||W_old||_2, 1e-30);
+/* R = max over W in {n, u_x, T} of ||W_new - W_old||_2 / max(||W_old||_2, s_W);
  * W[3][Nz] holds n, u_x, T of the interior cells (the paper states no criterion:
- * this is the solver's).  Exported for its pin.                              */
-double oracle_residual(int Nz, const double *Wo, const double *Wn)
+ * this is the solver's).  s_n = s_T = 1e-30; the velocity is measured on the wall
+ * speed where it is smaller, s_u = max(|u_w| sqrt(Nz), 1e-30) (the norm of a profile
+ * at the wall speed), since u_x itself vanishes in the free-molecular limit and at
+ * u_w = 0.  Exported for its pin.                                             */
+double oracle_residual(int Nz, const double *Wo, const double *Wn, double uw)
 {
     double R = 0.0;
     for (int a = 0; a < 3; ++a) {
@@ -495,7 +498,8 @@ double oracle_residual(int Nz, const double *Wo, const double *Wn)
             d += e * e;
             o += Wo[a * Nz + s] * Wo[a * Nz + s];
         }
-        double r = sqrt(d) / fmax(sqrt(o), 1e-30);
+        double floor = a == 1 ? fmax(fabs(uw) * sqrt((double)Nz), 1e-30) : 1e-30;
+        double r = sqrt(d) / fmax(sqrt(o), floor);
         if (r > R) R = r;
     }
     return R;
@@ -526,7 +530,7 @@ void oracle_step(const oracle_cfg *c, double *F0, long nsteps, double *res)
             F0[e] = F0[e] / 3.0 + 2.0 * F2[e] / 3.0 + 2.0 * dt * L[e] / 3.0;
         if (res) {
             res_profiles(c, F0, Wn);
-            res[it] = oracle_residual(Nz, Wo, Wn);
+            res[it] = oracle_residual(Nz, Wo, Wn, c->uw);
             double *t = Wo; Wo = Wn; Wn = t;
         }
     }

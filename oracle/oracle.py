@@ -76,7 +76,7 @@ def _load():
             lib.oracle_weno5.restype = C.c_double
             lib.oracle_tau.argtypes = [P, C.c_double, C.c_double]
             lib.oracle_tau.restype = C.c_double
-            lib.oracle_residual.argtypes = [C.c_int, D, D]
+            lib.oracle_residual.argtypes = [C.c_int, D, D, C.c_double]
             lib.oracle_residual.restype = C.c_double
             _lib = lib
     return _lib
@@ -233,12 +233,13 @@ class Oracle:
         return float(np.sum(self.profiles()["n"] * self.cell_widths()))
 
 
-def residual(W_old, W_new):
-    """The oracle's residual of one step from W[3][Nz] = (n, u_x, T) before and after."""
+def residual(W_old, W_new, uw=0.0):
+    """The oracle's residual of one step from W[3][Nz] = (n, u_x, T) before and after,
+    the velocity measured on the wall speed uw where u_x is smaller."""
     a = np.ascontiguousarray(W_old, dtype=np.float64)
     b = np.ascontiguousarray(W_new, dtype=np.float64)
     assert a.shape == b.shape and a.shape[0] == 3
-    return _load().oracle_residual(a.shape[1], _ptr(a), _ptr(b))
+    return _load().oracle_residual(a.shape[1], _ptr(a), _ptr(b), float(uw))
 
 
 def weno5(v):

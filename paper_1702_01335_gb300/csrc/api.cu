@@ -2,6 +2,7 @@
 // (velocity set, Hermite bases, grid, wall equilibria, time step), one device
 // memory pool per handle, and the launch sequence of a time step.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -362,6 +363,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         D.iKn = 1.0 / d.Kn;
         D.isuth = d.visc.law == 1 ? 1.0 / (1.0 + d.visc.omega_or_S) : 0.0;
         D.dt = I.dt; D.tol = 0.0;
+        D.res_uscale = std::max(std::fabs(d.u_w) * std::sqrt((double)Nz), 1e-30);
         const std::vector<double>& xc = I.xc;  // xc[s + 3]
         lagrange3(xc[Nz + 3], xc[Nz + 2], xc[Nz + 1], xc[Nz], D.ext_top[0]);
         lagrange3(xc[Nz + 4], xc[Nz + 3], xc[Nz + 2], xc[Nz + 1], D.ext_top[1]);
@@ -530,9 +532,21 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
     return LBS_OK;
 }
 
+// NVTX ranges on the host thread (no cost without an attached profiler): one per C
+// call that queues GPU work and one per RK stage as it is enqueued (inside a CUDA-graph
+// capture they mark the capture, the graph launches carry their own range)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+static const char* const kStageRange[4] = {"lbs analysis", "lbs RK stage 1", "lbs RK stage 2", "lbs RK stage 3"};
+
 // moments, records, wall densities and W_old of the current F0 (every active instance)
 static lbs_status analyse(lbs_solver* h)
 {
+    NvtxRange r(kStageRange[0]);
     CK(launch_stage(h->fp32, h->reduced, h->V, 0, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->ninst, h->maxNz,
                     h->fin_warp, h->nb, h->stream));
     return LBS_OK;
@@ -546,9 +560,11 @@ static bool split(const lbs_solver* h) { return h->fuse == 2 && h->nA > 0 && h->
 static lbs_status enqueue_step(lbs_solver* h)
 {
     if (!split(h)) {
-        for (int s = 1; s <= 3; ++s)
+        for (int s = 1; s <= 3; ++s) {
+            NvtxRange r(kStageRange[s]);
             CK(launch_stage(h->fp32, h->reduced, h->V, s, h->d_inst, h->d_tiles, h->ntiles, h->smem, h->fuse & 1, h->ninst,
                             h->maxNz, h->fin_warp, h->nb, h->stream));
+        }
         return LBS_OK;
     }
     CK(cudaEventRecord(h->ev_fork, h->stream));
@@ -556,6 +572,7 @@ static lbs_status enqueue_step(lbs_solver* h)
     // the stage kernel finds a tile's instance by its absolute index (full descriptor
     // array, a range of tiles); the finalisation kernels take a range of instances
     for (int s = 1; s <= 3; ++s) {
+        NvtxRange r(kStageRange[s]);
         CK(launch_stage_only(h->fp32, h->reduced, h->V, s, h->d_inst, h->d_tiles, h->ntilesA, h->smem, 0, h->stream));
         CK(launch_finalize(h->fp32, s, h->d_inst, h->nA, h->maxNz, h->fin_warp, h->nb, h->stream));
         CK(launch_stage_only(h->fp32, h->reduced, h->V, s, h->d_inst, h->d_tiles + h->ntilesA, h->ntiles - h->ntilesA, h->smem,
@@ -810,11 +827,13 @@ lbs_status lbs_destroy(lbs_handle h)
 lbs_status lbs_step(lbs_handle h, long nsteps)
 {
     if (!h || nsteps < 0) return fail(LBS_ERR_ARG, "invalid handle or negative step count");
+    NvtxRange r("lbs_step");
     const int G = 8;  // steps per CUDA-graph launch
     const long full = nsteps / G, rest = nsteps % G;
     if (full > 0) {
         lbs_status s = get_graph(h, G);
         if (s != LBS_OK) return s;
+        NvtxRange rg("lbs 8-step graph launches");
         for (long i = 0; i < full; ++i) CK(cudaGraphLaunch(h->gexec, h->stream));
     }
     for (long i = 0; i < rest; ++i) {
@@ -824,10 +843,35 @@ lbs_status lbs_step(lbs_handle h, long nsteps)
     return LBS_OK;
 }
 
+// The stage kernel's tile list over the instances still marching (act[b] != 0), or
+// over all instances (act == nullptr).  run_to_steady drops the tiles of retired
+// instances, whose CTAs would only read the descriptor and leave; only whole
+// instances are dropped, so the per-instance counts of the fused finalisation hold.
+// The split point of fuse = 2 stays at instance nA; a half left without tiles launches
+// nothing.  Invalidates the captured graph.
+static lbs_status upload_tiles(lbs_solver* h, const std::vector<int>* act)
+{
+    std::vector<Tile> all, tiles;
+    build_tiles(h, all);
+    int tA = 0;
+    for (const Tile& t : all)
+        if (!act || (*act)[t.inst]) {
+            tiles.push_back(t);
+            tA += t.inst < h->nA;
+        }
+    if (tiles.empty()) return LBS_OK;  // nothing left to launch: keep the current list
+    if (act) h->ntilesA = tA;
+    CK(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
+    h->ntiles = (int)tiles.size();
+    drop_graph(h);
+    return LBS_OK;
+}
+
 lbs_status lbs_run_to_steady(lbs_handle h, double tol, long max_steps, int check_every, long* steps_out)
 {
     if (!h || !(tol > 0.0) || max_steps < 1 || check_every < 1)
         return fail(LBS_ERR_ARG, "need tol > 0, max_steps >= 1, check_every >= 1");
+    NvtxRange r("lbs_run_to_steady");
     // arm the device-side retirement test
     for (int b = 0; b < h->ninst; ++b) h->idev[b].tol = tol;
     CK(cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->ninst, cudaMemcpyHostToDevice, h->stream));
@@ -847,8 +891,32 @@ lbs_status lbs_run_to_steady(lbs_handle h, double tol, long max_steps, int check
             CK(cudaMemcpyAsync(&act[b], h->idev[b].active, 4, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         for (int b = 0; b < h->ninst; ++b) all &= act[b] == 0;
+        // once a quarter of the launched tiles belong to retired instances, launch only
+        // the live ones; once few cells are left, finalise them with a warp per cell
+        // (the automatic layout), whose FP64 chains are shorter
+        long live = 0, cells = 0;
+        for (int b = 0; b < h->ninst; ++b) {
+            live += act[b] ? (long)h->ih[b].nchunks * h->ih[b].nzt : 0;
+            cells += act[b] ? h->ih[b].Nz : 0;
+        }
+        bool regraph = false;
+        if (!all && 4 * live <= 3L * h->ntiles) {
+            s = upload_tiles(h, &act);
+            regraph = true;
+        }
+        if (!all && s == LBS_OK && h->fin_mode == 0 && !h->fin_warp && cells <= kFinWarpMaxCells) {
+            h->fin_warp = 1;
+            for (int b = 0; b < h->ninst; ++b) h->idev[b].fin_warp = 1;
+            CK(cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->ninst, cudaMemcpyHostToDevice,
+                               h->stream));
+            drop_graph(h);
+            regraph = true;
+        }
+        if (regraph && s == LBS_OK) s = get_graph(h, check_every);
     }
-    // disarm and reactivate every instance
+    // disarm and reactivate every instance, with every tile and the batch's own
+    // finalisation layout
+    choose_finalize(h);
     for (int b = 0; b < h->ninst; ++b) h->idev[b].tol = 0.0;
     CK(cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->ninst, cudaMemcpyHostToDevice, h->stream));
     const int one = 1;
@@ -856,6 +924,7 @@ lbs_status lbs_run_to_steady(lbs_handle h, double tol, long max_steps, int check
         CK(cudaMemcpyAsync(&st[b], h->idev[b].steps, 8, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaMemcpyAsync(h->idev[b].active, &one, 4, cudaMemcpyHostToDevice, h->stream));
     }
+    if (s == LBS_OK) s = upload_tiles(h, nullptr);
     CK(cudaStreamSynchronize(h->stream));
     if (s != LBS_OK) return s;
     if (steps_out)

@@ -85,7 +85,11 @@ size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride)
 {
     const int KC = kThreads * V;
     (void)stage;
-    return stage_smem(zn, KC, G, fp32 ? 4 : 8, fp32 ? 4 : 8, rstride).total;  // element, accumulator
+    // element and accumulator sizes from the kernel's own types, so that the host's
+    // dynamic shared-memory size always covers the kernel's layout
+    return stage_smem(zn, KC, G, fp32 ? (int)sizeof(float) : (int)sizeof(double),
+                      fp32 ? (int)sizeof(Acc<float>::type) : (int)sizeof(Acc<double>::type), rstride)
+        .total;
 }
 
 template <typename T>
@@ -108,6 +112,7 @@ static cudaError_t launch_finalize_t(int stage, const InstDev* d_inst, int ninst
 cudaError_t launch_stage_only(int fp32, int red, int V, int stage, const InstDev* d_inst, const Tile* d_tiles,
                               int ntiles, size_t smem, int fuse, cudaStream_t st)
 {
+    if (ntiles <= 0) return cudaSuccess;  // a split half whose instances have all retired
     if (fp32)
         return red ? launch_stage_f32_red(V, stage, d_inst, d_tiles, ntiles, smem, fuse, st)
                    : launch_stage_f32_full(V, stage, d_inst, d_tiles, ntiles, smem, fuse, st);

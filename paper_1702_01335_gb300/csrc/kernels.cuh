@@ -722,7 +722,8 @@ static __device__ __noinline__ void finalize_instance(const InstDev& I, int stag
     if (stage == 3) {
         double R = 0.0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) R = fmax(R, sqrt(v[2 + 2 * a]) / fmax(sqrt(v[3 + 2 * a]), 1e-30));
+        for (int a = 0; a < 3; ++a)  // the velocity on the wall speed where u_x is smaller
+            R = fmax(R, sqrt(v[2 + 2 * a]) / fmax(sqrt(v[3 + 2 * a]), a == 1 ? I.res_uscale : 1e-30));
         // every W_old read above is complete (block_sum_n ends with a barrier)
         for (int e = t; e < 3 * Nz; e += blockDim.x) I.Wold[e] = __ldcg(I.Wnew + e);
         if (t == 0) {

@@ -44,6 +44,7 @@ struct InstDev {
     int reduced;                  // 1: the phi / chi model (Qy = 2: j = 0 phi, j = 1 chi; p_y unused)
     int visc_law;
     double Kn, visc_param, Pr, dt, tol;
+    double res_uscale;            // the residual's velocity scale max(|u_w| sqrt(Nz), 1e-30)
     double iKn, isuth;            // 1 / Kn; Sutherland: 1 / (1 + S)
     double Dtop, Dbot;            // sum over incoming velocities of w p_z Gw (n_w = 1)
     int rec_stride;               // values per cell record

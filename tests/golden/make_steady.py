@@ -80,9 +80,10 @@ def main():
             os.replace(a.checkpoint + ".tmp.npz", a.checkpoint)
         if a.tol in done or min(done, default=1.0) <= a.tol:
             break
-    rec["source"] = ("FP64 oracle (oracle/couette.c) from the rest Maxwellian, residual R of the "
-                     "solver's definition (max over n, u_x, T of the relative L2 change per step); "
-                     "written by tests/golden/make_steady.py")
+    rec["source"] = ("FP64 oracle (oracle/couette.c) from the rest Maxwellian; the marks are the first "
+                     "steps with R below each tol, R the solver's residual (max over n, u_x, T of the L2 "
+                     "change per step relative to the profile's L2 norm, the velocity's floored at "
+                     "|u_w| sqrt(Nz)); written by tests/golden/make_steady.py")
     out = os.path.join(HERE, "steady_%s.json" % a.workload)
     with open(out, "w") as fh:
         json.dump(rec, fh, indent=1)

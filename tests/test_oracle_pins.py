@@ -474,9 +474,11 @@ def test_paper_printed_values():
 
 def test_residual_hand_computed():
     """The steady-state residual (the paper states no criterion; the solver's definition
-    R = max over W in {n, u_x, T} of ||W_new - W_old||_2 / max(||W_old||_2, 1e-30)) on
-    3-cell cases computed by hand.  A squared norm, an L1 norm, a missing max over the
-    three profiles, or the new state in the denominator each give another number."""
+    R = max over W in {n, u_x, T} of ||W_new - W_old||_2 / max(||W_old||_2, s_W), with
+    s_n = s_T = 1e-30 and s_u = max(|u_w| sqrt(Nz), 1e-30)) on 3-cell cases computed by
+    hand.  A squared norm, an L1 norm, a missing max over the three profiles, the new
+    state in the denominator, or the wall-speed scale missing, applied to n or T, or
+    without the sqrt(Nz), each give another number."""
     from oracle.oracle import residual
     one = [1.0, 1.0, 1.0]
     # only u_x changes: R = 0.003 / sqrt(0.1^2 + 0.1^2) = 0.0212132034...
@@ -494,6 +496,23 @@ def test_residual_hand_computed():
     assert abs(residual(Wo, Wn) / 1e27 - 1.0) < 1e-12
     # nothing changes
     assert residual(Wo, Wo) == 0.0
+    # the wall speed as the velocity scale: u_w = 0.5 puts s_u = 0.5 sqrt 3 = 0.8660254
+    # above ||u_x|| = 0.1414..., so R = 0.003 / 0.8660254 = 0.0034641016...; T's change
+    # (0.0004 / sqrt 3 = 2.3e-4) stays below it
+    Wo = [one, [0.1, 0.0, -0.1], one]
+    Wn = [one, [0.1, 0.003, -0.1], [1.0, 1.0004, 1.0]]
+    assert abs(residual(Wo, Wn, uw=0.5) - 0.0034641016151377) < 1e-15
+    assert abs(residual(Wo, Wn, uw=-0.5) - 0.0034641016151377) < 1e-15
+    # a wall speed below the profile's own norm (0.01 sqrt 3 = 0.0173 < 0.1414) changes
+    # nothing
+    assert abs(residual(Wo, Wn, uw=0.01) - 0.003 / math.sqrt(0.02)) < 1e-15
+    # u_x from rest at u_w = 0.2: 1e-3 / (0.2 sqrt 3) = 0.0028867513...
+    Wo = [one, [0.0, 0.0, 0.0], one]
+    Wn = [one, [1e-3, 0.0, 0.0], one]
+    assert abs(residual(Wo, Wn, uw=0.2) - 0.0028867513459481) < 1e-15
+    # n and T keep their own norms: a change of n by 0.01 in one cell at u_w = 0.5
+    Wn = [[1.01, 1.0, 1.0], [0.0, 0.0, 0.0], one]
+    assert abs(residual(Wo, Wn, uw=0.5) - 0.01 / math.sqrt(3.0)) < 1e-15
 
 
 def test_residual_of_a_step_is_that_of_n_ux_T():
@@ -505,6 +524,8 @@ def test_residual_of_a_step_is_that_of_n_ux_T():
     a = o.profiles()
     r = o.step(1, residuals=True)[0]
     b = o.profiles()
-    assert abs(r / residual([a["n"], a["ux"], a["T"]], [b["n"], b["ux"], b["T"]]) - 1.0) < 1e-12
+    assert abs(r / residual([a["n"], a["ux"], a["T"]], [b["n"], b["ux"], b["T"]], uw=0.3) - 1.0) < 1e-12
     mom = [b["n"], b["n"] * b["ux"], b["T"]]
-    assert abs(r / residual([a["n"], a["n"] * a["ux"], a["T"]], mom) - 1.0) > 1e-6
+    assert abs(r / residual([a["n"], a["n"] * a["ux"], a["T"]], mom, uw=0.3) - 1.0) > 1e-6
+    # and the run's wall speed is the one it is measured on
+    assert abs(r / residual([a["n"], a["ux"], a["T"]], [b["n"], b["ux"], b["T"]], uw=3.0) - 1.0) > 1e-6

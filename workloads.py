@@ -14,6 +14,7 @@ plain dict of instance parameters with the field names of
       channel: 16 cells stretched with A = 0.98, 7 x 7 x (2 x Q_n) velocities with
       N_eq = 6, Sutherland viscosity, Pr = 2/3, delta = 1/(Kn sqrt 2) in
       {0.1, 1, 10, 20, 40}, u_w in {sqrt 2, 0.1 sqrt 2}; Q_n and dt from Table sharipov
+  paper_tables_small_delta()  the same at delta = 0.01 with Q_n = 100, at dt = 1e-4
   luo_runs()  the low-Mach runs of Sec. IV (Table luo): phi / chi model, Qx = 2,
       BGK, tau = k / sqrt 2, u_w = 1e-5, half channel with S = 64 or 32, A = 0.98
   sweep(n, seed)  instances drawn like the batched Kn / wall-speed / gas-law sweep:
@@ -32,12 +33,14 @@ C3 = dict(Qx=16, Qy=4, Qz=64, N_eq=4, Nz=256, A=0.0, Kn=100.0, u_w=0.05, T_w=1.0
           visc_law=0, visc_param=0.5)
 
 # Sec. VI: Sutherland constants of the two gases, the rarefaction parameters and the
-# per-delta normal-axis order and time step of Table sharipov.  delta = 0.01 is left
-# out: at its Q_n = 100 the largest |p_z| is 22.2, and the printed dt = 2.5e-4 puts the
-# CFL number of the first stretched cell at 1.65, above the RK-3 / WENO-5 limit.
+# per-delta normal-axis order and time step of Table sharipov.  delta = 0.01 is not in
+# paper_tables(): at its Q_n = 100 the largest |p_z| is 22.2, and the printed dt = 2.5e-4
+# puts the CFL number of the first stretched cell at 1.65, above the RK-3 / WENO-5
+# limit; paper_tables_small_delta() runs it at the stable dt = 1e-4 (CFL 0.66).
 SUTHERLAND_S = {"Ar": 0.5239, "He": 0.3101}
 TABLE_DELTAS = (0.1, 1.0, 10.0, 20.0, 40.0)
 TABLE_RUN = {0.01: (100, 2.5e-4), 0.1: (30, 2.5e-4)}   # delta -> (Q_n, dt); else (7, 5e-4)
+SMALL_DELTA_DT = 1e-4
 
 
 def paper_tables(reduced=False):
@@ -54,6 +57,20 @@ def paper_tables(reduced=False):
                             dict(Qx=7, Qy=0 if reduced else 7, Qz=Qn, N_eq=6, Nz=16, A=0.98, half=1, Kn=1.0 / (d * 2.0 ** 0.5),
                                  u_w=uw, T_w=1.0, Pr=2.0 / 3.0, visc_law=1, visc_param=SUTHERLAND_S[gas],
                                  dt=dt)))
+    return out
+
+
+def paper_tables_small_delta(reduced=False):
+    """The 4 delta = 0.01 runs of the Sec. VI tables (both gases, u_w = sqrt 2 and
+    0.1 sqrt 2) with Table sharipov's Q_n = 100 and every other parameter as in
+    paper_tables(), at dt = SMALL_DELTA_DT instead of the printed, unstable 2.5e-4."""
+    out = []
+    for gas in ("Ar", "He"):
+        for uw in (2.0 ** 0.5, 0.1 * 2.0 ** 0.5):
+            out.append((dict(gas=gas, delta=0.01, uw=uw),
+                        dict(Qx=7, Qy=0 if reduced else 7, Qz=TABLE_RUN[0.01][0], N_eq=6, Nz=16, A=0.98, half=1,
+                             Kn=1.0 / (0.01 * 2.0 ** 0.5), u_w=uw, T_w=1.0, Pr=2.0 / 3.0, visc_law=1,
+                             visc_param=SUTHERLAND_S[gas], dt=SMALL_DELTA_DT)))
     return out
 
 
