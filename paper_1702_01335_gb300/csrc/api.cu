@@ -157,6 +157,18 @@ static void put(std::vector<unsigned char>& host, size_t off, const std::vector<
     for (size_t i = 0; i < v.size(); ++i) p[i] = T(v[i]);
 }
 
+// FP32 (hi, lo) pairs of FP64 values: hi the nearest float, lo the nearest float to
+// the remainder
+static void put_pairs(std::vector<unsigned char>& host, size_t off, const std::vector<double>& v)
+{
+    float* p = reinterpret_cast<float*>(host.data() + off);
+    for (size_t i = 0; i < v.size(); ++i) {
+        const float hi = float(v[i]);
+        p[2 * i] = hi;
+        p[2 * i + 1] = float(v[i] - double(hi));
+    }
+}
+
 template <typename T>
 static std::vector<double> rounded(const std::vector<double>& v)
 {
@@ -246,7 +258,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
     std::vector<std::vector<double>> tabs_d;  // per instance, concatenated later
     Pool pool;
     struct Off {
-        size_t Hx, Hy, Pz, alpha, beta, px, py, xi, wx, wy, wz, gxt, gxb, gwy, gwz, idz;
+        size_t Hx, Hy, Pz, Hx2, Hy2, Pz2, alpha, beta, px, py, xi, wx, wy, wz, gxt, gxb, gwy, gwz, idz;
         size_t F0, F1, F2, L0, cur, rec, partial, flux, nw, prof, Wold, Wnew, res, steps, active, status, zcount,
             icount;
     };
@@ -413,6 +425,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         Off& o = off[b];
         const size_t es = sizeof(T);
         o.Hx = pool.take(t.Hx.size() * 8); o.Hy = pool.take(t.Hy.size() * 8); o.Pz = pool.take(t.Pz.size() * 8);
+        o.Hx2 = pool.take(t.Hx.size() * 8); o.Hy2 = pool.take(t.Hy.size() * 8); o.Pz2 = pool.take(t.Pz.size() * 8);
         o.alpha = pool.take(t.alpha.size() * 8); o.beta = pool.take(t.beta.size() * 8);
         o.px = pool.take(I.Qx * es); o.py = pool.take(I.Qy * es); o.xi = pool.take(I.Qz * es);
         o.wx = pool.take(I.Qx * es); o.wy = pool.take(I.Qy * es); o.wz = pool.take(I.Qz * es);
@@ -482,6 +495,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         const Tables& t = tb[b];
         const InstHost& I = h->ih[b];
         put<double>(img, o.Hx, t.Hx); put<double>(img, o.Hy, t.Hy); put<double>(img, o.Pz, t.Pz);
+        put_pairs(img, o.Hx2, t.Hx); put_pairs(img, o.Hy2, t.Hy); put_pairs(img, o.Pz2, t.Pz);
         put<double>(img, o.alpha, t.alpha); put<double>(img, o.beta, t.beta);
         put<T>(img, o.px, t.px); put<T>(img, o.py, t.py); put<T>(img, o.xi, t.xi);
         put<T>(img, o.wx, t.wx); put<T>(img, o.wy, t.wy); put<T>(img, o.wz, t.wz);
@@ -494,6 +508,13 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         D.Hx = reinterpret_cast<const double*>(P + o.Hx);
         D.Hy = reinterpret_cast<const double*>(P + o.Hy);
         D.Pz = reinterpret_cast<const double*>(P + o.Pz);
+        D.Hx2 = reinterpret_cast<const float2*>(P + o.Hx2);
+        D.Hy2 = reinterpret_cast<const float2*>(P + o.Hy2);
+        D.Pz2 = reinterpret_cast<const float2*>(P + o.Pz2);
+        D.sumw_x = D.sumw_y = D.sumw_z = 0.0;  // of the weights as stored
+        for (int i = 0; i < I.Qx; ++i) D.sumw_x += double(T(t.wx[i]));
+        for (int j = 0; j < I.Qy; ++j) D.sumw_y += double(T(t.wy[j]));
+        for (int m = 0; m < I.Qz; ++m) D.sumw_z += 2.0 * double(T(t.wz[m]));
         D.alpha = reinterpret_cast<const double*>(P + o.alpha);
         D.beta = reinterpret_cast<const double*>(P + o.beta);
         D.px = P + o.px; D.py = P + o.py; D.xi = P + o.xi; D.wx = P + o.wx; D.wy = P + o.wy; D.wz = P + o.wz;

@@ -343,6 +343,41 @@ static __device__ __forceinline__ float lo_decode(unsigned short q, float hi)
     return float(static_cast<short>(q)) * s;
 }
 
+// ---- double-float arithmetic (an FP32 pair hi + lo, |lo| <= ulp(hi) / 2) for the
+// FP32 records' node sums.  On this GPU an FP64 instruction occupies a scheduler's
+// FP64 unit for about 70 cycles whatever the number of active lanes, FP32 instructions
+// issue every cycle: the error-free transforms below (Knuth's TwoSum, the FMA form of
+// TwoProduct, a Fast2Sum renormalisation) cost a few FP32 instructions per term and
+// carry about 2^-44 of the largest term, well inside the half ulp of FP32 the factors
+// are rounded to.
+struct DF {
+    float hi, lo;
+};
+static __device__ __forceinline__ DF df_of(double x)
+{
+    const float h = __double2float_rn(x);
+    return DF{h, __double2float_rn(x - double(h))};
+}
+static __device__ __forceinline__ void df_add(DF& S, float p, float e)  // S += p + e, |e| << |p|
+{
+    const float s = S.hi + p, bb = s - S.hi;
+    float t = (S.hi - (s - bb)) + (p - bb);  // TwoSum(S.hi, p)
+    t += S.lo + e;
+    S.hi = s + t;
+    S.lo = t - (S.hi - s);  // Fast2Sum
+}
+static __device__ __forceinline__ void df_fma(DF& S, DF c, float2 h)  // S += c h (h = (hi, lo))
+{
+    const float p = c.hi * h.x;
+    const float e = fmaf(c.hi, h.y, fmaf(c.lo, h.x, fmaf(c.hi, h.x, -p)));
+    df_add(S, p, e);
+}
+static __device__ __forceinline__ void df_add_prod(DF& S, float a, float b)  // S += a b, exact product
+{
+    const float p = a * b;
+    df_add(S, p, fmaf(a, b, -p));
+}
+
 // ----------------------------------------------------------------------------
 // Cell record of a macroscopic state: the scalars and the per-node factors of the
 // truncated Hermite equilibrium (Sec. III, Eqs. fyz, Fmn_def), computed in FP64 (the
@@ -382,16 +417,34 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     // x: a_l, l >= 1, against He_l / l!
     full_coeffs<NB>(u0, Tc, I.Nx, c);
     s[0] = 0.0;
-#pragma unroll 4  // independent nodes: four FP64 chains in flight
-    for (int i = 0; i < Qx; ++i) {
-        const double* h = I.Hx + i * (I.Nx + 1);
-        double g = 0.0;
+    if constexpr (sizeof(T) == 4) {  // FP32 records: the node sums in double-float
+        DF cd[NB + 1], sw = {0.f, 0.f};
 #pragma unroll
-        for (int l = 1; l <= NB; ++l)
-            if (l <= I.Nx) g += c[l] * h[l];
-        const T v = T(g);
-        dx[i] = v;
-        s[0] += double(ld<T>(I.wx, i)) * (1.0 + double(v));
+        for (int l = 1; l <= NB; ++l) cd[l] = l <= I.Nx ? df_of(c[l]) : DF{0.f, 0.f};
+#pragma unroll 2
+        for (int i = 0; i < Qx; ++i) {
+            const float2* h = I.Hx2 + i * (I.Nx + 1);
+            DF g = {0.f, 0.f};
+#pragma unroll
+            for (int l = 1; l <= NB; ++l)
+                if (l <= I.Nx) df_fma(g, cd[l], h[l]);
+            const float v = g.hi + g.lo;
+            dx[i] = T(v);
+            df_add_prod(sw, ld<float>(I.wx, i), v);
+        }
+        s[0] = I.sumw_x + (double(sw.hi) + double(sw.lo));  // sum w (1 + v)
+    } else {
+#pragma unroll 4  // independent nodes: four FP64 chains in flight
+        for (int i = 0; i < Qx; ++i) {
+            const double* h = I.Hx + i * (I.Nx + 1);
+            double g = 0.0;
+#pragma unroll
+            for (int l = 1; l <= NB; ++l)
+                if (l <= I.Nx) g += c[l] * h[l];
+            const T v = T(g);
+            dx[i] = v;
+            s[0] += double(ld<T>(I.wx, i)) * (1.0 + double(v));
+        }
     }
     // y: the reduced model's factors 1 and T (phi and chi; its mass is phi's alone)
     s[1] = 0.0;
@@ -401,16 +454,34 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
         s[1] = 1.0;
     } else {
         full_coeffs<NB>(u1, Tc, I.Ny, c);
-#pragma unroll 4
-        for (int j = 0; j < Qy; ++j) {
-            const double* h = I.Hy + j * (I.Ny + 1);
-            double g = 0.0;
+        if constexpr (sizeof(T) == 4) {
+            DF cd[NB + 1], sw = {0.f, 0.f};
 #pragma unroll
-            for (int l = 1; l <= NB; ++l)
-                if (l <= I.Ny) g += c[l] * h[l];
-            const T v = T(g);
-            dy[j] = v;
-            s[1] += double(ld<T>(I.wy, j)) * (1.0 + double(v));
+            for (int l = 1; l <= NB; ++l) cd[l] = l <= I.Ny ? df_of(c[l]) : DF{0.f, 0.f};
+#pragma unroll 2
+            for (int j = 0; j < Qy; ++j) {
+                const float2* h = I.Hy2 + j * (I.Ny + 1);
+                DF g = {0.f, 0.f};
+#pragma unroll
+                for (int l = 1; l <= NB; ++l)
+                    if (l <= I.Ny) df_fma(g, cd[l], h[l]);
+                const float v = g.hi + g.lo;
+                dy[j] = T(v);
+                df_add_prod(sw, ld<float>(I.wy, j), v);
+            }
+            s[1] = I.sumw_y + (double(sw.hi) + double(sw.lo));
+        } else {
+#pragma unroll 4
+            for (int j = 0; j < Qy; ++j) {
+                const double* h = I.Hy + j * (I.Ny + 1);
+                double g = 0.0;
+#pragma unroll
+                for (int l = 1; l <= NB; ++l)
+                    if (l <= I.Ny) g += c[l] * h[l];
+                const T v = T(g);
+                dy[j] = v;
+                s[1] += double(ld<T>(I.wy, j)) * (1.0 + double(v));
+            }
         }
     }
     // z: b_l on each half range against pi_l / h_l, b_0 - 1/2 in place of b_0
@@ -418,20 +489,46 @@ __device__ bool write_record(const InstDev& I, int cell, double n, double in, co
     c[0] -= 0.5;
     cm[0] -= 0.5;
     s[2] = 0.0;
-#pragma unroll 2
-    for (int m = 0; m < Qz; ++m) {
-        const double* h = I.Pz + m * (I.Nzq + 1);
-        double gp = 0.0, gm = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        DF bp[NB + 1], bm[NB + 1], sw = {0.f, 0.f};
 #pragma unroll
-        for (int l = 0; l <= NB; ++l)
-            if (l <= I.Nzq) {
-                gp += c[l] * h[l];
-                gm += cm[l] * h[l];
-            }
-        const T vp = T(gp), vm = T(gm);
-        dz[m] = vp;
-        dz[Qz + m] = vm;
-        s[2] += double(ld<T>(I.wz, m)) * ((1.0 + double(vp)) + (1.0 + double(vm)));
+        for (int l = 0; l <= NB; ++l) {
+            bp[l] = l <= I.Nzq ? df_of(c[l]) : DF{0.f, 0.f};
+            bm[l] = l <= I.Nzq ? df_of(cm[l]) : DF{0.f, 0.f};
+        }
+        for (int m = 0; m < Qz; ++m) {
+            const float2* h = I.Pz2 + m * (I.Nzq + 1);
+            DF gp = {0.f, 0.f}, gm = {0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l <= NB; ++l)
+                if (l <= I.Nzq) {
+                    df_fma(gp, bp[l], h[l]);
+                    df_fma(gm, bm[l], h[l]);
+                }
+            const float vp = gp.hi + gp.lo, vm = gm.hi + gm.lo;
+            dz[m] = T(vp);
+            dz[Qz + m] = T(vm);
+            const float w = ld<float>(I.wz, m);
+            df_add_prod(sw, w, vp);
+            df_add_prod(sw, w, vm);
+        }
+        s[2] = I.sumw_z + (double(sw.hi) + double(sw.lo));  // sum over both half ranges
+    } else {
+#pragma unroll 2
+        for (int m = 0; m < Qz; ++m) {
+            const double* h = I.Pz + m * (I.Nzq + 1);
+            double gp = 0.0, gm = 0.0;
+#pragma unroll
+            for (int l = 0; l <= NB; ++l)
+                if (l <= I.Nzq) {
+                    gp += c[l] * h[l];
+                    gm += cm[l] * h[l];
+                }
+            const T vp = T(gp), vm = T(gm);
+            dz[m] = vp;
+            dz[Qz + m] = vm;
+            s[2] += double(ld<T>(I.wz, m)) * ((1.0 + double(vp)) + (1.0 + double(vm)));
+        }
     }
     rec[R_SCALE1] = T(nn / (s[0] * s[1] * s[2]) - 1.0);
     return !bad;

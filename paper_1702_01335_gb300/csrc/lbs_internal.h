@@ -1,6 +1,8 @@
 // Internal definitions shared by the host set-up and the CUDA kernels.
 #pragma once
 
+#include <vector_types.h>  // float2 (also for the host-only translation units)
+
 #include <cmath>
 #include <vector>
 
@@ -57,6 +59,9 @@ struct InstDev {
     double ext_bot[2][3];         // ghost 0 <- (1, 2, 3); ghost -1 <- (0, 1, 2)
     // tables
     const double *Hx, *Hy, *Pz;   // FP64, [Q_a][N_a + 1] basis values He_l/l!, pi_l/h_l
+    const float2 *Hx2, *Hy2, *Pz2;  // the same as FP32 (hi, lo) pairs, hi + lo = the FP64 value
+                                    // to 2^-48 (FP32 storage: the records' node sums)
+    double sumw_x, sumw_y, sumw_z;  // sums of the stored weights (z: over both half ranges)
     const double *alpha, *beta;   // half-range recurrence, [kMaxN + 2]
     // storage-typed tables (float or double)
     const void *px, *py, *xi, *wx, *wy, *wz;
