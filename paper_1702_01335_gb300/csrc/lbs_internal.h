@@ -1,7 +1,11 @@
 // Internal definitions shared by the host set-up and the CUDA kernels.
 #pragma once
 
+#if __has_include(<vector_types.h>)
 #include <vector_types.h>  // float2 (also for the host-only translation units)
+#else
+struct float2;  // host code built without the CUDA headers holds only pointers to it
+#endif
 
 #include <cmath>
 #include <vector>
