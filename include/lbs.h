@@ -198,7 +198,11 @@ lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host)
  * CTA waits up to a further 2^28 spins for its copies in flight to land, so that none
  * writes shared memory after it has left, then returns without output; the next
  * call that checks the status returns LBS_ERR_TIMEOUT.  spins = 0 gives up at once
- * (the copies still land).  Applies to every instance; synchronises the stream. */
+ * (the copies still land).  If the second wait also runs out (a copy that has not
+ * landed after some seconds), the CTA leaves anyway, and a late copy may still write
+ * the shared memory of a later CTA on that SM: after LBS_ERR_TIMEOUT, restore the
+ * state (lbs_clear_status, lbs_set_state) before stepping again, and treat a repeated
+ * timeout as a device fault.  Applies to every instance; synchronises the stream. */
 lbs_status lbs_set_wait_limit(lbs_handle h, unsigned spins);
 
 /* Clear the status words of every instance (after LBS_ERR_TIMEOUT or
