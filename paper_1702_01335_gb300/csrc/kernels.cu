@@ -92,20 +92,42 @@ size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride)
         .total;
 }
 
+// Finalisation launches carry the device's highest priority: when the batch's halves step
+// on two streams, the block scheduler then dispatches one half's finalisation blocks as soon
+// as the other half's stage CTAs free room on an SM, instead of after all of them.  (The
+// attribute is kept by CUDA-graph capture.)
+static int highest_priority()
+{
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    return greatest;
+}
+template <typename K>
+static cudaError_t launch_first(K kernel, dim3 g, dim3 b, cudaStream_t st, const InstDev* d_inst, int stage)
+{
+    static const int prio = highest_priority();
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, d_inst, stage);
+}
+
 template <typename T>
 static cudaError_t launch_finalize_t(int stage, const InstDev* d_inst, int ninst, int maxNz, int fin_warp,
                                      int nb, cudaStream_t st)
 {
     const dim3 g((maxNz + 31) / 32, ninst);
-    if (fin_warp)
-        finalize_cells_warp<T><<<dim3((maxNz + 3) / 4, ninst), 128, 0, st>>>(d_inst, stage);
-    else if (nb <= 4)
-        finalize_cells<T, 4><<<g, 32, 0, st>>>(d_inst, stage);
-    else if (nb <= 6)
-        finalize_cells<T, 6><<<g, 32, 0, st>>>(d_inst, stage);
-    else
-        finalize_cells<T, kMaxN><<<g, 32, 0, st>>>(d_inst, stage);
-    return cudaGetLastError();
+    if (fin_warp) return launch_first(finalize_cells_warp<T>, dim3((maxNz + 3) / 4, ninst), dim3(128), st, d_inst, stage);
+    if (nb <= 4) return launch_first(finalize_cells<T, 4>, g, dim3(32), st, d_inst, stage);
+    if (nb <= 6) return launch_first(finalize_cells<T, 6>, g, dim3(32), st, d_inst, stage);
+    return launch_first(finalize_cells<T, kMaxN>, g, dim3(32), st, d_inst, stage);
 }
 
 // the stage kernel alone

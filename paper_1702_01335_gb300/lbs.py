@@ -23,6 +23,7 @@ PROFILE_NAMES = ("n", "ux", "uy", "uz", "T", "qx", "qy", "qz",
                  "Pxx", "Pyy", "Pzz", "Pxy", "Pxz", "Pyz")
 STATUS = {0: "LBS_OK", 1: "LBS_ERR_ARG", 2: "LBS_ERR_CUDA", 3: "LBS_ERR_NONFINITE",
           4: "LBS_ERR_NO_CONVERGENCE", 5: "LBS_ERR_QUADRATURE", 6: "LBS_ERR_TIMEOUT"}
+LBS_ERR_ARG = 1
 LBS_ERR_NONFINITE = 3
 LBS_ERR_NO_CONVERGENCE = 4
 LBS_ERR_TIMEOUT = 6

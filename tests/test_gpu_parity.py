@@ -70,6 +70,49 @@ def test_fp32_profiles_match_oracle(params):
     assert max(errs.values()) < FP32_TOL, "profile errors: " + repr(sorted(errs.items(), key=lambda kv: -kv[1]))
 
 
+# Q / 2 = 1350 (even): the velocity-pair layout of FP32 storage applies at V = 2 and 4, with
+# a ragged last chunk at each (1350 = 5 x 256 + 70 = 2 x 512 + 326 velocities)
+PAIRS = dict(RAGGED, Qx=9, Qy=6, Qz=25, Nz=21)
+
+
+@pytest.mark.parametrize("V,ZT,fuse", [(2, 5, 0), (4, 16, 2), (4, 7, 0), (2, 24, 1)])
+def test_fp32_velocity_pair_tilings_match_oracle(V, ZT, fuse):
+    """FP32 storage in every velocity-pair tiling (the packed two-lane update) against the
+    FP64 oracle, and against the one-velocity-per-thread layout (V = 1) to FP32 rounding."""
+    P = _lbs()
+    o = oracle_of(PAIRS, dt=None)
+    s = solver_of(PAIRS, o.dt, P.LBS_FP32)
+    s.set_tiling(V, ZT, fuse)
+    t = s.tiling()
+    assert t["V"] == V and t["fuse"] == fuse
+    one = solver_of(PAIRS, o.dt, P.LBS_FP32)
+    one.set_tiling(1, 4, 0)
+    o.step(25)
+    s.step(25)
+    one.step(25)
+    errs = profile_errors(s.profiles(), o.profiles())
+    assert max(errs.values()) < FP32_TOL, "profile errors: " + repr(sorted(errs.items(), key=lambda kv: -kv[1]))
+    a, b = s.populations(), one.populations()
+    assert np.abs(a - b).max() < 1e-5 * np.abs(b).max()
+
+
+def test_fp32_pair_layout_needs_even_half_range():
+    """Q / 2 odd: V = 2 and 4 are refused in FP32 (a pair would straddle a chunk start) and
+    the untuned default takes one velocity per thread; FP64 takes them, and no V = 8."""
+    P = _lbs()
+    p = dict(RAGGED, Qx=3, Qy=3, Qz=5, Nz=12)  # Q / 2 = 45
+    s = solver_of(p, 0.002, P.LBS_FP32)
+    assert s.tiling()["V"] == 1
+    for V in (2, 4):
+        with pytest.raises(P.LbsError) as e:
+            s.set_tiling(V, 8, 0)
+        assert e.value.status == P.LBS_ERR_ARG
+    d = solver_of(p, 0.002, P.LBS_FP64)
+    d.set_tiling(4, 8, 0)
+    with pytest.raises(P.LbsError):
+        d.set_tiling(8, 8, 0)
+
+
 @pytest.mark.parametrize("fuse", [None, 2])
 def test_batch_of_uneven_instances_matches_single_runs(fuse):
     """A batch of instances of different Nz, Q and gas laws equals each run alone, also
