@@ -523,7 +523,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
         D.F0 = P + o.F0; D.F1 = P + o.F1; D.F2 = P + o.F2; D.rec = P + o.rec;
         D.L0 = h->fp32 ? reinterpret_cast<unsigned short*>(P + o.L0) : nullptr;
         D.cur = reinterpret_cast<int*>(P + o.cur);
-        D.partial = reinterpret_cast<double*>(P + o.partial);
+        D.partial = P + o.partial;
         D.flux_part = reinterpret_cast<double*>(P + o.flux);
         D.nw = reinterpret_cast<double*>(P + o.nw);
         D.prof = reinterpret_cast<double*>(P + o.prof);

@@ -584,23 +584,35 @@ template <typename T, int NB = kMaxN>
 __device__ __noinline__ void finalize_cell(const InstDev& I, int cell, int stage)
 {
     const int Nz = I.Nz, nch = I.nchunks;
+    typedef typename Acc<T>::type A;
+    const A* part = static_cast<const A*>(I.partial);
     double mom[kNMom];  // the partials: moments of the deviations about ur
-    for (int a = 0; a < kNMom; ++a) mom[a] = 0.0;
     // chunks in order, four at a time with every load issued before the adds (the
-    // partials come from L2: one round trip per four chunks instead of per chunk)
-    for (int c = 0; c < nch; c += 4) {
-        double p[4][kNMom];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int a = 0; a < kNMom; ++a)
-                p[j][a] = c + j < nch ? __ldcg(I.partial + ((size_t)(c + j) * kNMom + a) * Nz + cell) : 0.0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int a = 0; a < kNMom; ++a)
-                if (c + j < nch) mom[a] += p[j][a];
+    // partials come from L2: one round trip per four chunks instead of per chunk);
+    // FP32 partials summed in double-float (no FP64 instruction per chunk)
+    DF md[kNMom];
+    for (int a = 0; a < kNMom; ++a) {
+        mom[a] = 0.0;
+        md[a] = DF{0.f, 0.f};
     }
+    for (int c = 0; c < nch; c += 4) {
+        A p[4][kNMom];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int a = 0; a < kNMom; ++a)
+                p[j][a] = c + j < nch ? __ldcg(part + ((size_t)(c + j) * kNMom + a) * Nz + cell) : A(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int a = 0; a < kNMom; ++a)
+                if (c + j < nch) {
+                    if constexpr (sizeof(A) == 4) df_add(md[a], p[j][a], 0.f);
+                    else mom[a] += p[j][a];
+                }
+    }
+    if constexpr (sizeof(A) == 4)
+        for (int a = 0; a < kNMom; ++a) mom[a] = double(md[a].hi) + double(md[a].lo);
     double ur[3];
     moment_origin<T>(I, cell, stage, ur);
     CellState st;
@@ -762,7 +774,10 @@ __device__ __noinline__ void finalize_cell_warp(const InstDev& I, int cell, int 
             double p[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                p[j] = c + 2 * j < nch ? __ldcg(I.partial + ((size_t)(c + 2 * j) * kNMom + am) * Nz + cell) : 0.0;
+                p[j] = c + 2 * j < nch
+                           ? double(__ldcg(static_cast<const typename Acc<T>::type*>(I.partial) +
+                                           ((size_t)(c + 2 * j) * kNMom + am) * Nz + cell))
+                           : 0.0;
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if (c + 2 * j < nch) part += p[j];
@@ -1512,15 +1527,15 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
     }
     }  // the scalar march
     __syncthreads();
-    // the chunk's partial of each cell: the warps' sums added in the accumulation type
-    // (FP32 storage: the FP64 pipe, a small fraction of the FP32 rate here, converts
-    // once per cell and moment), stored in FP64 for the sum over chunks
+    // the chunk's partial of each cell: the warps' sums added and stored in the
+    // accumulation type (FP32 storage: no FP64 instruction here; the finalisation sums
+    // the chunks exactly enough in double-float)
     for (int e = tid; e < zn * kNMom; e += kThreads) {
         const int c = e / kNMom, a = e - c * kNMom;
         A s = red[(size_t)c * (kThreads / 32) * 16 + a];
 #pragma unroll
         for (int q = 1; q < kThreads / 32; ++q) s += red[((size_t)c * (kThreads / 32) + q) * 16 + a];
-        I.partial[((size_t)tile.chunk * kNMom + a) * Nz + z0 + c] = double(s);
+        static_cast<A*>(I.partial)[((size_t)tile.chunk * kNMom + a) * Nz + z0 + c] = s;
     }
 
     // ---- 6. outgoing WENO flux of the stage output through the wall interfaces (for

@@ -83,7 +83,7 @@ struct InstDev {
     unsigned short *L0;           // [Nz][Q], FP32 storage only
     int *cur;                     // [1]
     void *rec;                    // [Nz][rec_stride]
-    double *partial;              // [nchunks][kNMom][Nz]
+    void *partial;                // [nchunks][kNMom][Nz] in the accumulation type (FP32 sums of FP32 storage)
     double *flux_part;            // [nchunks][2]: bottom, top outgoing flux
     double *nw;                   // [2]: bottom, top wall density
     double *prof;                 // [14][Nz]
