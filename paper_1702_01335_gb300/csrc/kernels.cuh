@@ -330,17 +330,30 @@ __host__ __device__ inline StageSmem stage_smem(int zn, int KC, int G, int esize
 // lo / ulp(hi) * 2^15 = lo * 2^(165 - E), a power of two built in the exponent field
 // from the masked exponent bits of hi (E clamped below at 38; the decoding scale
 // 2^(E - 165) is then zero: a hi below 2^-88 keeps no residual).
-static __device__ __forceinline__ unsigned short lo_encode(float lo, float hi)
+// Both without int/float conversion instructions: for |x| < 2^22, fma(lo, s, 1.5 2^23)
+// holds round-to-nearest-even(lo s) in its low mantissa bits (s is a power of two, so the
+// product is exact and rounded once, as __float2int_rn rounds it), and 2^23 + u is exact
+// for a 16-bit u, so q = float bits of (2^23 + 2^15 + q) minus (2^23 + 2^15).
+static __device__ __forceinline__ unsigned lo_bits(float lo, float hi)  // q in the low 16 bits
 {
     const unsigned m = max(__float_as_uint(hi) & 0x7f800000u, 38u << 23);
     const float s = __uint_as_float((292u << 23) - m);  // 2^(165 - E)
-    return static_cast<unsigned short>(static_cast<short>(__float2int_rn(lo * s)));
+    return __float_as_uint(fmaf(lo, s, 12582912.0f));
 }
-static __device__ __forceinline__ float lo_decode(unsigned short q, float hi)
+static __device__ __forceinline__ unsigned short lo_encode(float lo, float hi)
+{
+    return static_cast<unsigned short>(lo_bits(lo, hi));
+}
+static __device__ __forceinline__ unsigned lo_encode2(float2 lo, float2 hi)  // two residuals, x low
+{
+    return __byte_perm(lo_bits(lo.x, hi.x), lo_bits(lo.y, hi.y), 0x5410);
+}
+static __device__ __forceinline__ float lo_decode(unsigned q16, float hi)  // q in the low 16 bits
 {
     const unsigned m = max(__float_as_uint(hi) & 0x7f800000u, 38u << 23);
     const float s = __uint_as_float(m - (38u << 23));  // 2^(E - 165), zero for E = 38
-    return float(static_cast<short>(q)) * s;
+    const float q = __uint_as_float((q16 & 0xffffu) ^ 0x4B008000u) - 8421376.0f;  // the int16 q
+    return q * s;
 }
 
 // ---- double-float arithmetic (an FP32 pair hi + lo, |lo| <= ulp(hi) / 2) for the
@@ -1158,7 +1171,9 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             LQN[p] = kLo && STAGE == 3 && ok[2 * p] ? __ldcg(lop + p * kThreads) : 0u;
             DIN[p] = kD && ok[2 * p] ? __ldg(dop + p * kThreads) : make_float2(0.f, 0.f);
         }
-#pragma unroll 1
+        // stage 1 unrolled by two steps (the window's shift halves; 80 vs 86 us on 64 x C2);
+        // stages 2 and 3, with their increment and residual streams, lose by unrolling
+#pragma unroll(STAGE == 1 ? 2 : 1)
         for (int c = 0; c < zn; ++c) {
             unsigned LQC[NP];
             float2 DC[NP], DIC[NP];
@@ -1214,8 +1229,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                         dinc = DIC[p];
                     }
                     if constexpr (kLo && STAGE == 3)
-                        lo = make_float2(lo_decode(static_cast<unsigned short>(LQC[p] & 0xffffu), h.x),
-                                         lo_decode(static_cast<unsigned short>(LQC[p] >> 16), h.y));
+                        lo = make_float2(lo_decode(LQC[p], h.x), lo_decode(LQC[p] >> 16, h.y));
                     const float2 dep = STAGE >= 2 ? add2(add2(sub2(h, tgt), dinc), lo) : sub2(f, tgt);
                     // Eq. (flux) and the relaxation: -|p_z| div / dz - dep / tau
                     const float2 div = add2(sub2(W[p][3], W[p][2]), sub2(cp, CM[p]));
@@ -1233,9 +1247,7 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
                             const float2 t = add2(lo, inc);
                             const float2 h2 = add2(h, t);
                             const float2 lo2 = sub2(t, sub2(h2, h));
-                            if (ok[v0])
-                                __stcg(lop + p * kThreads, unsigned(lo_encode(lo2.x, h2.x)) |
-                                                               (unsigned(lo_encode(lo2.y, h2.y)) << 16));
+                            if (ok[v0]) __stcg(lop + p * kThreads, lo_encode2(lo2, h2));
                             st = h2;
                         } else {
                             st = add2(h, inc);
