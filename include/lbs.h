@@ -216,6 +216,15 @@ lbs_status lbs_clear_status(lbs_handle h);
  * LBS_ERR_NONFINITE if a value is not finite or n <= 0 or T <= 0. */
 lbs_status lbs_init_from_profiles(lbs_handle h, int inst, const double* prof);
 
+/* Start for strongly rarefied instances: seed every cell of instance inst with the
+ * free-molecular state of the channel, each velocity carrying the discrete equilibrium
+ * of the wall it left (the incoming-ghost formula of the Appendix with n_w = 1: p_z > 0
+ * the bottom wall at -u_w, p_z < 0 the top wall at +u_w), each cell rescaled to unit
+ * density (the rest start's mass); FP32 residuals zero.  Not a step of the paper's
+ * method: a choice of initial state.  Queued on the handle's stream; the analysis pass
+ * that follows synchronises it.  LBS_ERR_ARG for an invalid handle or instance. */
+lbs_status lbs_init_free_molecular(lbs_handle h, int inst);
+
 /* Profiles of a distribution the caller holds in device memory, computed
  * without allocating device memory.  The paper has no counterpart: this is a
  * service for callers that cannot call cudaMalloc where they need moments, for

@@ -24,6 +24,7 @@ cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int nins
                             int nb, cudaStream_t st);
 cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,
                         cudaStream_t st);
+cudaError_t launch_seed_free_molecular(int fp32, const InstDev* d_inst, int inst, int Nz, cudaStream_t st);
 size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride);
 }  // namespace lbs
 
@@ -1272,6 +1273,16 @@ lbs_status lbs_init_from_profiles(lbs_handle h, int inst, const double* prof)
     }
     CK(cudaMemcpyAsync(h->d_macro, macro.data(), macro.size() * 8, cudaMemcpyHostToDevice, h->stream));
     CK(launch_seed(h->fp32, h->d_inst, inst, Nz, h->d_macro, h->stream));
+    s = analyse(h);
+    if (s != LBS_OK) return s;
+    return check_status(h);
+}
+
+lbs_status lbs_init_free_molecular(lbs_handle h, int inst)
+{
+    lbs_status s = inst_ok(h, inst);
+    if (s != LBS_OK) return s;
+    CK(launch_seed_free_molecular(h->fp32, h->d_inst, inst, h->ih[inst].Nz, h->stream));
     s = analyse(h);
     if (s != LBS_OK) return s;
     return check_status(h);

@@ -80,6 +80,37 @@ __global__ void __launch_bounds__(128) seed_cells(const InstDev* __restrict__ in
     }
 }
 
+// ---- seed a cell with the free-molecular state of the channel: each velocity carries the
+// discrete equilibrium of the wall it left (Appendix, with n_w = 1: p_z > 0 the bottom
+// wall, p_z < 0 the top wall; the incoming ghosts' formula), then the cell is rescaled to
+// unit density.  The collisionless limit of Couette flow between diffuse walls; a start
+// for strongly rarefied instances.  One block per cell; residual 0.
+template <typename T>
+__global__ void __launch_bounds__(128) seed_free_molecular(const InstDev* __restrict__ insts, int inst)
+{
+    __shared__ double red[kRedSlots];
+    const InstDev& I = insts[inst];
+    const int cell = blockIdx.x;
+    T* F = static_cast<T*>(*I.cur ? I.F1 : I.F0) + (size_t)cell * I.Q;
+    double m = 0.0;  // the cell's density sum w (1 + d), phi's alone in the reduced model
+    for (int k = threadIdx.x; k < I.Q; k += blockDim.x) {
+        const int j = k % I.Qy, i = (k / I.Qy) % I.Qx, zm = k / I.QxQy;
+        const int sg = zm >= I.Qz, mz = zm - sg * I.Qz;
+        const T ax = ld<T>(sg ? I.gwx_top : I.gwx_bot, i), ay = ld<T>(I.gwy, j), az = ld<T>(I.gwz, zm);
+        const T a = ax + ay + ax * ay, b = a + az + a * az;
+        F[k] = b;
+        if (!(I.reduced && j == 1))
+            m += double(ld<T>(I.wx, i)) * double(ld<T>(I.wy, j)) * double(ld<T>(I.wz, mz)) * (1.0 + double(b));
+    }
+    m = block_sum(m, red);
+    const T c = T(1.0 / m - 1.0);  // (1 + d) / m - 1 = d + c (1 + d)
+    for (int k = threadIdx.x; k < I.Q; k += blockDim.x) {
+        const T d = F[k];
+        F[k] = d + c * (T(1) + d);
+        if (I.L0) I.L0[(size_t)cell * I.Q + k] = 0;
+    }
+}
+
 // ---- host launchers ---------------------------------------------------------
 size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride)
 {
@@ -159,6 +190,13 @@ cudaError_t launch_stage(int fp32, int red, int V, int stage, const InstDev* d_i
     cudaError_t e = launch_stage_only(fp32, red, V, stage, d_inst, d_tiles, ntiles, smem, fuse, st);
     if (e != cudaSuccess || fuse) return e;
     return launch_finalize(fp32, stage, d_inst, ninst, maxNz, fin_warp, nb, st);
+}
+
+cudaError_t launch_seed_free_molecular(int fp32, const InstDev* d_inst, int inst, int Nz, cudaStream_t st)
+{
+    if (fp32) seed_free_molecular<float><<<Nz, 128, 0, st>>>(d_inst, inst);
+    else seed_free_molecular<double><<<Nz, 128, 0, st>>>(d_inst, inst);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,

@@ -65,7 +65,7 @@ class _Desc(C.Structure):
 
 EXPORTS = ("lbs_create", "lbs_batch_create", "lbs_destroy", "lbs_step", "lbs_run_to_steady",
            "lbs_moments", "lbs_profiles", "lbs_residual", "lbs_steps_taken", "lbs_info",
-           "lbs_get_state", "lbs_set_state", "lbs_init_from_profiles", "lbs_quadrature",
+           "lbs_get_state", "lbs_set_state", "lbs_init_from_profiles", "lbs_init_free_molecular", "lbs_quadrature",
            "lbs_get_stream", "lbs_profile_steps", "lbs_moments_static", "lbs_set_tiling",
            "lbs_get_tiling", "lbs_last_error", "lbs_couette_diagnostics", "lbs_diagnostics",
            "lbs_set_finalize", "lbs_couette_nonlinear_velocity", "lbs_set_wait_limit", "lbs_clear_status",
@@ -104,6 +104,7 @@ def load(build_if_missing=True):
         lib.lbs_get_state.argtypes = [P, C.c_int, P, C.c_int]
         lib.lbs_set_state.argtypes = [P, C.c_int, P, C.c_int]
         lib.lbs_init_from_profiles.argtypes = [P, C.c_int, D]
+        lib.lbs_init_free_molecular.argtypes = [P, C.c_int]
         lib.lbs_quadrature.argtypes = [C.c_int, C.c_int, D, D]
         lib.lbs_couette_diagnostics.argtypes = [D, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
                                                 C.POINTER(_Diag)]
@@ -429,3 +430,8 @@ class Solver:
         """prof: [8, Nz] in the order of MOMENT_NAMES (P rows unused)."""
         prof = np.ascontiguousarray(prof, dtype=np.float64)
         _check(self.lib.lbs_init_from_profiles(self.h, inst, _dptr(prof)))
+
+    def init_free_molecular(self, inst):
+        """Seed instance inst with the free-molecular state (each velocity the equilibrium of
+        the wall it left, cells at unit density): a start for strongly rarefied flows."""
+        _check(self.lib.lbs_init_free_molecular(self.h, inst))

@@ -25,12 +25,15 @@ import numpy as np
 from . import lbs as L
 
 NPTS = 64            # points per profile
-# Instances are seeded only below this Knudsen number.  Seeding the near-equilibrium
-# Shakhov target of the predicted moments halves the steps to the steady state of
+# The network seeds instances below this Knudsen number; above it they start from the
+# free-molecular state (lbs_init_free_molecular).  Seeding the near-equilibrium Shakhov
+# target of the predicted moments halves the steps to the steady state of
 # collision-dominated flows but roughly doubles them in nearly free-molecular ones
-# (measured on the held-out sweep draws: Kn < 0.2 median 3296 -> 1417 steps,
-# Kn in [0.2, 1) 2298 -> 1545, [1, 5) 3573 -> 3788, [5, 20] 4353 -> 7482), where the
-# steady distribution is far from any Maxwellian; those start from rest.
+# (held-out sweep draws: Kn < 0.2 median 3296 -> 1417 steps, Kn in [0.2, 1) 2298 -> 1545,
+# [1, 5) 3573 -> 3788, [5, 20] 4353 -> 7482), whose steady distribution is far from any
+# Maxwellian; the free-molecular start, the collisionless limit, takes [1, 5) 3566 -> 3420
+# and [5, 20] 4353 -> 3455.
+FREE_MOLECULAR = "free-molecular"  # a seed in steady_solves' warm list
 WARM_KN_MAX = 1.0
 NPROF = 8            # profiles n, u_x, T, q_x, q_z, P_xx, P_xz, P_zz
 SIZES = (6, 256, 256, NPROF * NPTS)
@@ -228,7 +231,9 @@ def steady_solves(params, precision=L.LBS_FP32, tol=1e-8, max_steps=200_000, che
         s.set_tiling(*tiling)
     if warm is not None:
         for b, prof in enumerate(warm):
-            if prof is not None:  # None: this instance starts from rest
+            if isinstance(prof, str) and prof == FREE_MOLECULAR:
+                s.init_free_molecular(b)
+            elif prof is not None:  # None: this instance starts from rest
                 s.init_from_profiles(b, prof)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -277,10 +282,10 @@ class WarmStart:
         return last
 
     def seeds(self, params, kn_max=WARM_KN_MAX):
-        """The predicted profiles of the instances below kn_max, None for the others
-        (which start from rest): the argument warm of steady_solves."""
+        """The predicted profiles of the instances below kn_max, FREE_MOLECULAR for the
+        others: the argument warm of steady_solves."""
         pred = self.predict(params)
-        return [pr if p["Kn"] < kn_max else None for p, pr in zip(params, pred)]
+        return [pr if p["Kn"] < kn_max else FREE_MOLECULAR for p, pr in zip(params, pred)]
 
     def predict(self, params):
         """Profiles [8, Nz] on each instance's cells, density rescaled to unit mass."""
@@ -365,9 +370,14 @@ def evaluate(train_params, eval_params, n_plain=16, tol=1e-7, max_steps=60000, e
         "steps_median": {"cold": float(np.median(steps_cold)), "warm": float(np.median(steps_warm))},
         "steps_mean": {"cold": float(np.mean(steps_cold)), "warm": float(np.mean(steps_warm))},
         "converged": {"cold": int(conv_cold.sum()), "warm": int(conv_warm.sum())},
-        "seeded": {"instances": int(sum(w is not None for w in warm)), "kn_max": WARM_KN_MAX,
-                   "steps_mean_cold": float(np.mean([st for st, w in zip(steps_cold, warm) if w is not None] or [0])),
-                   "steps_mean_warm": float(np.mean([st for st, w in zip(steps_warm, warm) if w is not None] or [0]))},
+        "seeded": {"network": int(sum(not isinstance(w, str) for w in warm)),
+                   "free_molecular": int(sum(isinstance(w, str) for w in warm)), "kn_max": WARM_KN_MAX,
+                   "network_steps_mean": {
+                       "cold": float(np.mean([st for st, w in zip(steps_cold, warm) if not isinstance(w, str)] or [0])),
+                       "warm": float(np.mean([st for st, w in zip(steps_warm, warm) if not isinstance(w, str)] or [0]))},
+                   "free_molecular_steps_mean": {
+                       "cold": float(np.mean([st for st, w in zip(steps_cold, warm) if isinstance(w, str)] or [0])),
+                       "warm": float(np.mean([st for st, w in zip(steps_warm, warm) if isinstance(w, str)] or [0]))}},
         "wall_s": {"plain_single_instance_per_instance": per_plain,
                    "plain_single_instance_extrapolated_all": per_plain * n,
                    "plain_sample": n_plain,

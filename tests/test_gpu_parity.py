@@ -193,6 +193,31 @@ def test_warm_start_and_checkpoint():
     assert rel_err(gpu_f(s, o), o.f[3:3 + o.Nz]) < FP64_TOL
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_free_molecular_seed(prec):
+    """lbs_init_free_molecular: every velocity carries the discrete equilibrium of the wall
+    it left (the oracle's equilibrium at n = 1, u = -u_w for p_z > 0, +u_w for p_z < 0,
+    T_w), each cell at unit density; FP64 to 1e-12, FP32 to its rounding."""
+    P = _lbs()
+    p = RAGGED
+    o = oracle_of(p, None)
+    s = solver_of(p, o.dt, P.LBS_FP64 if prec == "fp64" else P.LBS_FP32)
+    s.init_free_molecular(0)
+    z = np.zeros(3)
+    fb = o.equilibrium(1.0, np.array([-p["u_w"], 0.0, 0.0]), p["T_w"], z, with_S=False)
+    ft = o.equilibrium(1.0, np.array([p["u_w"], 0.0, 0.0]), p["T_w"], z, with_S=False)
+    f = np.where(o.velocities()[:, 2] > 0, fb, ft)
+    f = f / f.sum()
+    got = gpu_f(s, o)
+    tol = FP64_TOL if prec == "fp64" else 1e-6
+    assert rel_err(got, np.broadcast_to(f, got.shape)) < tol
+    prof = s.profiles()
+    assert np.abs(prof["n"] - 1.0).max() < (1e-13 if prec == "fp64" else 1e-6)
+    assert np.abs(prof["ux"]).max() < 1e-12 + (0 if prec == "fp64" else 1e-6)
+    s.step(5)  # and steps from there
+    assert np.all(np.isfinite(s.profiles()["T"]))
+
+
 def test_nonfinite_inputs_rejected():
     P = _lbs()
     s = solver_of(W.C1, 0.004, P.LBS_FP64)
