@@ -1159,6 +1159,11 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
         for (int p = 0; p < NP; ++p) CM[p] = weno5_corr2(W[p][0], W[p][1], W[p][2], W[p][3], W[p][4]);
         int sn = zw0 + 6 * sdir;
         inc_row2(sn, DN);
+        // the increments' row of cell sn as a running offset in pairs (one add per march
+        // step instead of the row's product; a pointer is formed only inside the channel)
+        const float2* __restrict__ dbase = reinterpret_cast<const float2*>(Dgf + k0) + tid;
+        long doff = (long)sn * (Q / 2);
+        const long dstep = sdir * (long)(Q / 2);
         const float2 DT = splat(float(I.dt));
         const long ostep2 = sgc ? -(long)(Q / 2) : (long)(Q / 2);
         const size_t orow0 = (size_t)(sgc ? z0 + zn - 1 : z0) * Q + k0 + tbase;
@@ -1187,7 +1192,11 @@ stage_kernel(const InstDev* __restrict__ insts, const Tile* __restrict__ tiles, 
             }
             if (kD && c + 1 < zn) {
                 sn += sdir;
-                inc_row2(sn, DN);
+                doff += dstep;
+                const bool in = (unsigned)sn < (unsigned)Nz;
+#pragma unroll
+                for (int p = 0; p < NP; ++p)
+                    DN[p] = in && ok[2 * p] ? __ldg(dbase + doff + p * kThreads) : make_float2(0.f, 0.f);
             }
             const int cc = sgc ? zn - 1 - c : c;
             const float* sc = reinterpret_cast<const float*>(recs) + (size_t)cc * rstride;

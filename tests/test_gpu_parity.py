@@ -245,6 +245,36 @@ def test_run_to_steady_c1():
     assert rel_err(gpu_f(s, o), o.f[3:3 + o.Nz]) < 1e-10
 
 
+@pytest.mark.parametrize("fuse", [0, 2])
+def test_run_to_steady_batch_retires_and_restores(fuse):
+    """A batch whose instances converge at different steps: run_to_steady drops the tiles of
+    retired instances and, once few cells are live, finalises them a warp each.  Each
+    instance takes the steps it takes alone and ends in the same state (the layouts agree
+    to FP64 rounding); afterwards the full tile list and the batch's layout are back, so a
+    further step of the batch equals a step of each instance alone."""
+    P = _lbs()
+    # 740 cells: one thread per cell at first, a warp per cell once fewer than 608 are live
+    ps = [dict(W.C1, Kn=kn, Nz=nz) for kn, nz in ((0.1, 160), (0.3, 120), (1.0, 140), (0.15, 100), (3.0, 120),
+                                                 (0.2, 100))]
+    dt = min(oracle_of(p, None).dt for p in ps)
+    s = solver_of(ps, dt, P.LBS_FP64)
+    t = s.tiling()
+    s.set_tiling(t["V"], t["ZT"], fuse)
+    t = s.tiling()
+    steps = s.run_to_steady(1e-8, max_steps=30000, check_every=50)
+    assert len(set(steps)) > 2  # they retire at different checks
+    assert s.tiling() == t  # every tile is back
+    s.step(3)
+    for b, p in enumerate(ps):
+        a = solver_of(p, dt, P.LBS_FP64)
+        sa = a.run_to_steady(1e-8, max_steps=30000, check_every=50)[0]
+        assert sa == steps[b], (b, sa, steps[b])
+        a.step(3)
+        ref = a.populations()
+        assert np.abs(s.populations(b) - ref).max() < 1e-11 * np.abs(ref).max(), b
+        a.close()
+
+
 def test_c2_full_size_sampled_parity():
     """Config C2 at full size in the benchmark's launch shape (a batch of replicas):
     after a few steps every sampled replica matches the oracle's single solve."""
