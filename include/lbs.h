@@ -150,7 +150,8 @@ lbs_status lbs_run_to_steady(lbs_handle h, double tol, long max_steps, int check
 
 /* Profiles of instance inst, host_out[8][Nz]: n, u_x, T, q_x, q_z, P_xx,
  * P_xz, P_zz (Eq. qdef, pressure tensor P_ij = sum xi_i xi_j f with xi = p - u).
- * inst = -1: every instance, concatenated in instance order ([8][Nz_b] each). */
+ * inst = -1: every instance, concatenated in instance order ([8][Nz_b] each):
+ * gathered on the device, then one copy to host_out.  Synchronises the stream. */
 lbs_status lbs_moments(lbs_handle h, int inst, double* host_out);
 
 /* All 14 profiles of instance inst, host_out[14][Nz]: n, u_x, u_y, u_z, T,
@@ -188,8 +189,10 @@ lbs_status lbs_get_state(lbs_handle h, int inst, void* dst, int to_host);
 /* Resume / warm start: set the distribution of instance inst from src (layout
  * and precision of lbs_get_state; host if from_host, else device) and
  * recompute its moments and wall densities.  inst = -1: every instance from
- * one buffer laid out as lbs_get_state's.  LBS_ERR_NONFINITE if the state has
- * non-finite values or n <= 0 or T <= 0 in a cell. */
+ * one buffer laid out as lbs_get_state's; the copy then runs in up to four groups of
+ * instances, and each group's moments are computed on a second stream while the
+ * next group is copied.  LBS_ERR_NONFINITE if the state has non-finite values or
+ * n <= 0 or T <= 0 in a cell.  Synchronises the stream. */
 lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host);
 
 /* Tests of failure detection: the number of spins a stage CTA waits for its bulk

@@ -25,6 +25,8 @@ cudaError_t launch_finalize(int fp32, int stage, const InstDev* d_inst, int nins
 cudaError_t launch_seed(int fp32, const InstDev* d_inst, int inst, int Nz, const double* d_macro,
                         cudaStream_t st);
 cudaError_t launch_seed_free_molecular(int fp32, const InstDev* d_inst, int inst, int Nz, cudaStream_t st);
+cudaError_t launch_gather_moments(const InstDev* d_inst, int ninst, const double* prof_all, double* out,
+                                  cudaStream_t st);
 size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride);
 }  // namespace lbs
 
@@ -88,12 +90,17 @@ struct lbs_solver {
     // instance order: whole-batch reads are one copy each
     double* prof_all = nullptr;
     size_t prof_all_n = 0;
+    double* mom_all = nullptr;  // [8][Nz] per instance: lbs_moments' rows, gathered for one copy
     int* status_all = nullptr;
     int* cur_all = nullptr;  // per instance: which of F0 / F1 holds the state
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0;
     // split stepping (fuse = 2): instances [0, nA) on stream, [nA, ninst) on stream2
     int nA = 0, ntilesA = 0;
+    // first tile of each instance in the full tile list (ninst + 1 entries), and whether
+    // the list on the device is the full one (run_to_steady launches a compacted list)
+    std::vector<int> tile_first;
+    bool tiles_full = true;
     cudaStream_t stream2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
@@ -218,6 +225,9 @@ static void build_tiles(lbs_solver* h, std::vector<Tile>& tiles)
         }
     }
     h->smem = smem;
+    h->tile_first.assign(h->ninst + 1, 0);
+    for (const Tile& x : tiles) ++h->tile_first[x.inst + 1];
+    for (int b = 0; b < h->ninst; ++b) h->tile_first[b + 1] += h->tile_first[b];
     // split point of the batch for fuse = 2: about half the tiles on each side
     h->nA = 0;
     h->ntilesA = 0;
@@ -485,6 +495,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
     h->max_tiles = max_tiles;
     const size_t tile_off = pool.take(sizeof(Tile) * max_tiles);
     const size_t macro_off = pool.take(8 * (size_t)h->maxNz * 8);
+    const size_t mom_off = pool.take(8 * (h->prof_all_n / 14) * 8);
     void* mem = nullptr;
     CK(cudaMalloc(&mem, pool.bytes));
     h->pool = static_cast<unsigned char*>(mem);
@@ -546,6 +557,7 @@ static lbs_status setup(lbs_solver* h, const lbs_instance_desc* desc)
     h->d_tiles = reinterpret_cast<Tile*>(P + tile_off);
     h->d_macro = reinterpret_cast<double*>(P + macro_off);
     h->prof_all = reinterpret_cast<double*>(P + prof_base);
+    h->mom_all = reinterpret_cast<double*>(P + mom_off);
     h->status_all = reinterpret_cast<int*>(P + status_base);
     h->cur_all = reinterpret_cast<int*>(P + cur_base);
     h->ntiles = (int)tiles.size();
@@ -578,6 +590,17 @@ static lbs_status analyse(lbs_solver* h)
 // (unfused) finalisation, so that one half's FP64 finalisation overlaps the other
 // half's stage kernel; the step forks from and joins back into the handle's stream
 static bool split(const lbs_solver* h) { return h->fuse == 2 && h->nA > 0 && h->stream2; }
+
+// the second stream and its fork / join events, made on first use (split stepping, the
+// pipelined lbs_set_state)
+static lbs_status ensure_stream2(lbs_solver* h)
+{
+    if (h->stream2) return LBS_OK;
+    CK(cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    return LBS_OK;
+}
 
 static lbs_status enqueue_step(lbs_solver* h)
 {
@@ -885,6 +908,7 @@ static lbs_status upload_tiles(lbs_solver* h, const std::vector<int>* act)
     if (act) h->ntilesA = tA;
     CK(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
     h->ntiles = (int)tiles.size();
+    h->tiles_full = tiles.size() == all.size();
     drop_graph(h);
     return LBS_OK;
 }
@@ -946,7 +970,8 @@ lbs_status lbs_run_to_steady(lbs_handle h, double tol, long max_steps, int check
         CK(cudaMemcpyAsync(&st[b], h->idev[b].steps, 8, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaMemcpyAsync(h->idev[b].active, &one, 4, cudaMemcpyHostToDevice, h->stream));
     }
-    if (s == LBS_OK) s = upload_tiles(h, nullptr);
+    const lbs_status su = upload_tiles(h, nullptr);
+    if (s == LBS_OK) s = su;
     CK(cudaStreamSynchronize(h->stream));
     if (s != LBS_OK) return s;
     if (steps_out)
@@ -1018,10 +1043,9 @@ lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT, int fuse)
                 return fail(LBS_ERR_ARG, "V = 2, 4 in FP32 (velocity pairs) needs Q / 2 even in every instance");
     CK(cudaStreamSynchronize(h->stream));
     drop_graph(h);
-    if (fuse == 2 && !h->stream2) {
-        CK(cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    if (fuse == 2) {
+        const lbs_status s2 = ensure_stream2(h);
+        if (s2 != LBS_OK) return s2;
     }
     h->V = V;
     h->ZT = ZT;
@@ -1037,6 +1061,7 @@ lbs_status lbs_set_tiling(lbs_handle h, int V, int ZT, int fuse)
     CK(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->ninst, cudaMemcpyHostToDevice, h->stream));
     h->ntiles = (int)tiles.size();
+    h->tiles_full = true;
     lbs_status s = analyse(h);  // partial sums of the new chunking
     if (s != LBS_OK) return s;
     return check_status(h);
@@ -1111,18 +1136,11 @@ lbs_status lbs_diagnostics(lbs_handle h, int inst, lbs_diag* out)
 
 lbs_status lbs_moments(lbs_handle h, int inst, double* host_out)
 {
-    if (h && inst == -1 && host_out) {  // every instance: one copy of the packed profiles
-        std::vector<double> all(h->prof_all_n);
-        CK(cudaMemcpyAsync(all.data(), h->prof_all, 8 * h->prof_all_n, cudaMemcpyDeviceToHost, h->stream));
+    if (h && inst == -1 && host_out) {
+        // every instance: the reported rows gathered on the device, then one copy
+        CK(launch_gather_moments(h->d_inst, h->ninst, h->prof_all, h->mom_all, h->stream));
+        CK(cudaMemcpyAsync(host_out, h->mom_all, 8 * 8 * (h->prof_all_n / 14), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
-        const int rows[8] = {0, 1, 4, 5, 7, 8, 12, 10};  // n, u_x, T, q_x, q_z, P_xx, P_xz, P_zz
-        size_t in = 0, out = 0;
-        for (int b = 0; b < h->ninst; ++b) {
-            const size_t Nz = h->ih[b].Nz;
-            for (int r = 0; r < 8; ++r) std::memcpy(host_out + out + r * Nz, all.data() + in + rows[r] * Nz, 8 * Nz);
-            in += 14 * Nz;
-            out += 8 * Nz;
-        }
         return LBS_OK;
     }
     lbs_status s = inst_ok(h, inst);
@@ -1176,16 +1194,18 @@ lbs_status lbs_info(lbs_handle h, int inst, long* out, double* dt_out)
 
 // The state of instances b0 .. b1-1 as the C ABI exposes it (see lbs_get_state): the
 // deviations d of every instance, concatenated, then (FP32) their rounding residuals,
-// concatenated.  Consecutive instances whose device buffers are adjacent go in one copy.
-// sel[b] picks F1 instead of F0 for instance b (get: where the state is; set: always F0).
-static lbs_status copy_state(lbs_solver* h, int b0, int b1, unsigned char* ext, bool to_ext, bool ext_host,
-                             const std::vector<int>& sel)
+// concatenated.  ext + off0 is where instance b0's d lies in the external buffer, ext +
+// off1 where its residuals lie (a range of a larger whole-batch buffer).  Consecutive
+// instances whose device buffers are adjacent go in one copy.  sel[b] picks F1 instead of
+// F0 for instance b (get: where the state is; set: always F0).
+static lbs_status copy_state(lbs_solver* h, int b0, int b1, unsigned char* ext, size_t off0, size_t off1,
+                             bool to_ext, bool ext_host, const std::vector<int>& sel)
 {
     const cudaMemcpyKind kind = to_ext ? (ext_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice)
                                        : (ext_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice);
-    size_t off = 0;
     for (int part = 0; part < (h->fp32 ? 2 : 1); ++part) {
         const size_t es = part ? 2 : h->esize;
+        size_t off = part ? off1 : off0;
         for (int b = b0; b < b1;) {
             auto dev = [&](int e) -> unsigned char* {
                 if (part) return reinterpret_cast<unsigned char*>(h->idev[e].L0);
@@ -1207,6 +1227,14 @@ static lbs_status copy_state(lbs_solver* h, int b0, int b1, unsigned char* ext, 
     return LBS_OK;
 }
 
+// bytes of the deviations d of instances b0 .. b1-1 as stored
+static size_t state_d_bytes(const lbs_solver* h, int b0, int b1)
+{
+    size_t n = 0;
+    for (int b = b0; b < b1; ++b) n += (size_t)h->ih[b].Nz * h->ih[b].Q * h->esize;
+    return n;
+}
+
 lbs_status lbs_get_state(lbs_handle h, int inst, void* dst, int to_host)
 {
     if (!h || inst < -1 || inst >= h->ninst) return fail(LBS_ERR_ARG, "invalid handle or instance index");
@@ -1215,25 +1243,68 @@ lbs_status lbs_get_state(lbs_handle h, int inst, void* dst, int to_host)
     std::vector<int> cur(h->ninst);
     CK(cudaMemcpyAsync(cur.data(), h->cur_all, 4 * (size_t)h->ninst, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    lbs_status s = copy_state(h, b0, b1, static_cast<unsigned char*>(dst), true, to_host != 0, cur);
+    lbs_status s = copy_state(h, b0, b1, static_cast<unsigned char*>(dst), 0, state_d_bytes(h, b0, b1), true,
+                              to_host != 0, cur);
     if (s != LBS_OK) return s;
     CK(cudaStreamSynchronize(h->stream));
     return LBS_OK;
 }
 
+// Up to this many groups of instances in a pipelined lbs_set_state
+static const int kSetStateChunks = 4;
+
 lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host)
 {
     if (!h || inst < -1 || inst >= h->ninst) return fail(LBS_ERR_ARG, "invalid handle or instance index");
     if (!src) return fail(LBS_ERR_ARG, "null source");
+    NvtxRange r("lbs_set_state");
     const int b0 = inst < 0 ? 0 : inst, b1 = inst < 0 ? h->ninst : inst + 1;
+    unsigned char* ext = static_cast<unsigned char*>(const_cast<void*>(src));
+    const size_t dtot = state_d_bytes(h, b0, b1);
     // the state goes to F0, and F0 becomes the state buffer of those instances
-    std::vector<int> sel(h->ninst, 0);
-    lbs_status s = copy_state(h, b0, b1, static_cast<unsigned char*>(const_cast<void*>(src)), false,
-                              from_host != 0, sel);
-    if (s != LBS_OK) return s;
+    const std::vector<int> sel(h->ninst, 0);
     CK(cudaMemsetAsync(h->cur_all + b0, 0, 4 * (size_t)(b1 - b0), h->stream));
-    s = analyse(h);
-    if (s != LBS_OK) return s;
+    lbs_status s = h->tiles_full && b1 - b0 >= 2 ? ensure_stream2(h) : LBS_ERR_ARG;
+    if (s != LBS_OK) {
+        // one instance (or a compacted tile list): copy, then analyse the whole batch
+        s = copy_state(h, b0, b1, ext, 0, dtot, false, from_host != 0, sel);
+        if (s == LBS_OK) s = analyse(h);
+        if (s != LBS_OK) return s;
+        return check_status(h);
+    }
+    // Several instances: the copy runs in groups of instances on the handle's stream, and
+    // each group's analysis (stage 0 and its finalisation over the group's tiles and
+    // instances) on the second stream as soon as the group has landed, behind the next
+    // group's copy.  The copy is bound by the host link, so the analysis (a full read of
+    // the state) is hidden but for the last group's.
+    const int K = std::min(kSetStateChunks, b1 - b0);
+    const size_t per = (dtot + K - 1) / K;
+    size_t doff = 0, roff = 0;  // bytes of d and of residuals of the groups before
+    for (int c0 = b0; c0 < b1;) {
+        int c1 = c0;
+        size_t db = 0;
+        do {
+            db += (size_t)h->ih[c1].Nz * h->ih[c1].Q * h->esize;
+            ++c1;
+        } while (c1 < b1 && db < per);
+        s = copy_state(h, c0, c1, ext, doff, dtot + roff, false, from_host != 0, sel);
+        if (s != LBS_OK) return s;
+        doff += db;
+        roff += db / h->esize * 2;
+        CK(cudaEventRecord(h->ev_fork, h->stream));
+        CK(cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));
+        {
+            // the same launches as analyse() (the fused finalisation counts per instance)
+            NvtxRange ra(kStageRange[0]);
+            CK(launch_stage_only(h->fp32, h->reduced, h->V, 0, h->d_inst, h->d_tiles + h->tile_first[c0],
+                                 h->tile_first[c1] - h->tile_first[c0], h->smem, h->fuse & 1, h->stream2));
+            if (!(h->fuse & 1))
+                CK(launch_finalize(h->fp32, 0, h->d_inst + c0, c1 - c0, h->maxNz, h->fin_warp, h->nb, h->stream2));
+        }
+        c0 = c1;
+    }
+    CK(cudaEventRecord(h->ev_join, h->stream2));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     return check_status(h);
 }
 

@@ -111,7 +111,32 @@ __global__ void __launch_bounds__(128) seed_free_molecular(const InstDev* __rest
     }
 }
 
+// The eight profile rows that lbs_moments reports (n, u_x, T, q_x, q_z, P_xx, P_xz, P_zz:
+// rows 0, 1, 4, 5, 7, 8, 12, 10 of the [14][Nz] profiles, one nibble each) of every
+// instance, packed [8][Nz] per instance in instance order, so that a whole-batch read is
+// one device-to-host copy.  The profiles sit back to back (14 Nz doubles per instance),
+// so an instance's offset in out is 8/14 of its offset in prof_all.  Block (b, r) copies
+// row r of instance b.
+__global__ void __launch_bounds__(128) gather_moment_rows(const InstDev* __restrict__ insts,
+                                                          const double* __restrict__ prof_all,
+                                                          double* __restrict__ out)
+{
+    const InstDev& I = insts[blockIdx.x];
+    const int r = blockIdx.y, row = (0xAC875410u >> (4 * r)) & 0xFu;
+    const long before = (long)(I.prof - prof_all) / 14;  // cells of the instances before b
+    const double* __restrict__ src = I.prof + (long)row * I.Nz;
+    double* __restrict__ dst = out + 8 * before + (long)r * I.Nz;
+    for (int c = threadIdx.x; c < I.Nz; c += blockDim.x) dst[c] = src[c];
+}
+
 // ---- host launchers ---------------------------------------------------------
+cudaError_t launch_gather_moments(const InstDev* d_inst, int ninst, const double* prof_all, double* out,
+                                  cudaStream_t st)
+{
+    gather_moment_rows<<<dim3(ninst, 8), 128, 0, st>>>(d_inst, prof_all, out);
+    return cudaGetLastError();
+}
+
 size_t stage_smem_bytes(int fp32, int V, int zn, int G, int stage, int rstride)
 {
     const int KC = kThreads * V;

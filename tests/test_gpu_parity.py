@@ -218,6 +218,78 @@ def test_free_molecular_seed(prec):
     assert np.all(np.isfinite(s.profiles()["T"]))
 
 
+@pytest.mark.parametrize("prec,fuse", [("fp64", 1), ("fp32", 1), ("fp32", 0), ("fp32", 2)])
+def test_whole_batch_state_and_moments(prec, fuse):
+    """Whole-batch state and moments (instance index -1) on a batch of unequal instances:
+    lbs_get_state lays out every d, then every FP32 residual, in instance order, and
+    lbs_moments every instance's [8][Nz] rows, bit for bit as the per-instance calls give
+    them.  lbs_set_state of the whole batch (copied in groups of instances, each group
+    analysed behind the next group's copy, from host and from device memory) restores the
+    state bit for bit and leaves the profiles, and the steps that follow, exactly as a
+    solver restored instance by instance.  A non-finite value in one instance of the
+    buffer is rejected."""
+    import torch
+    P = _lbs()
+    pr = P.LBS_FP64 if prec == "fp64" else P.LBS_FP32
+    ps = [dict(W.C1, Nz=40), RAGGED, dict(W.C1, Kn=1.0, Nz=37), PAIRS, dict(RAGGED, Nz=64, u_w=0.2),
+          dict(W.C1, Kn=0.3, Nz=51)]
+    dt = min(oracle_of(p, None).dt for p in ps)
+    s = solver_of(ps, dt, pr)
+    t = s.tiling()
+    s.set_tiling(t["V"], t["ZT"], fuse)
+    s.step(7)
+    nb = s.state_bytes()
+    buf = np.zeros(nb, np.uint8)
+    s.get_state_all_ptr(buf.ctypes.data)
+    per = [s.get_state(b) for b in range(len(ps))]
+    d = np.concatenate([st.d.view(np.uint8).ravel() for st in per])
+    r = [st.r.view(np.uint8).ravel() for st in per] if pr == P.LBS_FP32 else []
+    assert np.array_equal(buf, np.concatenate([d] + r))
+    mom = np.zeros(8 * sum(p["Nz"] for p in ps))
+    s.moments_all_ptr(mom.ctypes.data)
+    ref = np.concatenate([np.stack(list(s.moments(b).values())).ravel() for b in range(len(ps))])
+    assert np.array_equal(mom, ref)
+    prof0 = [s.profiles(b) for b in range(len(ps))]
+
+    one = solver_of(ps, dt, pr)  # restored instance by instance
+    one.set_tiling(t["V"], t["ZT"], fuse)
+    for b, st in enumerate(per):
+        one.set_state(b, st)
+    s.step(5)
+    s.set_state_all_ptr(buf.ctypes.data, from_host=True)
+    for b in range(len(ps)):
+        assert same_state(s.get_state(b), per[b]), b
+        pa, pb = s.profiles(b), one.profiles(b)
+        assert all(np.array_equal(pa[k], pb[k]) for k in pa), b
+        assert all(np.abs(pa[k] - prof0[b][k]).max() < 2e-6 for k in pa), b  # the moments of that state
+    s.step(3)
+    one.step(3)
+    for b in range(len(ps)):
+        assert same_state(s.get_state(b), one.get_state(b)), b
+
+    dev = torch.from_numpy(buf).cuda()
+    torch.cuda.synchronize()
+    s.set_state_all_ptr(dev.data_ptr(), from_host=False)
+    for b in range(len(ps)):
+        assert same_state(s.get_state(b), per[b]), b
+
+    bad = buf.copy()
+    esize = 4 if pr == P.LBS_FP32 else 8
+    k = (ps[0]["Nz"] * one.info(0)["Q"] + 11) * esize  # an element of instance 1
+    bad[k:k + esize] = np.frombuffer(np.array([np.inf], dtype=np.float32 if esize == 4 else np.float64).tobytes(),
+                                     np.uint8)
+    with pytest.raises(P.LbsError) as e:
+        s.set_state_all_ptr(bad.ctypes.data, from_host=True)
+    assert e.value.status == 3
+    s.clear_status()
+    s.set_state_all_ptr(buf.ctypes.data, from_host=True)
+    s.step(3)
+    for b in range(len(ps)):
+        assert same_state(s.get_state(b), one.get_state(b)), b
+    s.close()
+    one.close()
+
+
 def test_nonfinite_inputs_rejected():
     P = _lbs()
     s = solver_of(W.C1, 0.004, P.LBS_FP64)
