@@ -189,9 +189,9 @@ lbs_status lbs_get_state(lbs_handle h, int inst, void* dst, int to_host);
 /* Resume / warm start: set the distribution of instance inst from src (layout
  * and precision of lbs_get_state; host if from_host, else device) and
  * recompute its moments and wall densities.  inst = -1: every instance from
- * one buffer laid out as lbs_get_state's; the copy then runs in up to four groups of
- * instances, and each group's moments are computed on a second stream while the
- * next group is copied.  LBS_ERR_NONFINITE if the state has non-finite values or
+ * one buffer laid out as lbs_get_state's.  From host memory, a state of 48 MB or more
+ * is copied in two to four groups of instances (at least 24 MB each), and each group's
+ * moments are computed on a second stream while the next group is copied.  LBS_ERR_NONFINITE if the state has non-finite values or
  * n <= 0 or T <= 0 in a cell.  Synchronises the stream. */
 lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host);
 

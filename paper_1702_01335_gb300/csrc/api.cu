@@ -1250,8 +1250,12 @@ lbs_status lbs_get_state(lbs_handle h, int inst, void* dst, int to_host)
     return LBS_OK;
 }
 
-// Up to this many groups of instances in a pipelined lbs_set_state
+// A pipelined lbs_set_state copies in up to four groups of instances, of at least 24 MB
+// each: a group's analysis (a stage-0 launch and a latency-bound finalisation, about
+// 100 us) then hides behind the next group's copy from host memory (about 211 GB/s).
+// Smaller or device-resident states are copied whole and analysed once.
 static const int kSetStateChunks = 4;
+static const size_t kSetStateGroupBytes = size_t(24) << 20;
 
 lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host)
 {
@@ -1264,20 +1268,21 @@ lbs_status lbs_set_state(lbs_handle h, int inst, const void* src, int from_host)
     // the state goes to F0, and F0 becomes the state buffer of those instances
     const std::vector<int> sel(h->ninst, 0);
     CK(cudaMemsetAsync(h->cur_all + b0, 0, 4 * (size_t)(b1 - b0), h->stream));
-    lbs_status s = h->tiles_full && b1 - b0 >= 2 ? ensure_stream2(h) : LBS_ERR_ARG;
+    const size_t total = dtot + (h->fp32 ? dtot / h->esize * 2 : 0);
+    const int K = (int)std::min<size_t>(std::min(kSetStateChunks, b1 - b0), total / kSetStateGroupBytes);
+    lbs_status s = h->tiles_full && from_host && K >= 2 ? ensure_stream2(h) : LBS_ERR_ARG;
     if (s != LBS_OK) {
-        // one instance (or a compacted tile list): copy, then analyse the whole batch
+        // one group (or a compacted tile list): copy, then analyse the whole batch
         s = copy_state(h, b0, b1, ext, 0, dtot, false, from_host != 0, sel);
         if (s == LBS_OK) s = analyse(h);
         if (s != LBS_OK) return s;
         return check_status(h);
     }
-    // Several instances: the copy runs in groups of instances on the handle's stream, and
-    // each group's analysis (stage 0 and its finalisation over the group's tiles and
-    // instances) on the second stream as soon as the group has landed, behind the next
-    // group's copy.  The copy is bound by the host link, so the analysis (a full read of
-    // the state) is hidden but for the last group's.
-    const int K = std::min(kSetStateChunks, b1 - b0);
+    // A large state from host memory: the copy runs in groups of instances on the handle's
+    // stream, and each group's analysis (stage 0 and its finalisation over the group's
+    // tiles and instances) on the second stream as soon as the group has landed, behind
+    // the next group's copy.  The copy is bound by the host link, so the analysis (a full
+    // read of the state) is hidden but for the last group's.
     const size_t per = (dtot + K - 1) / K;
     size_t doff = 0, roff = 0;  // bytes of d and of residuals of the groups before
     for (int c0 = b0; c0 < b1;) {

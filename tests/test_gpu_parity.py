@@ -218,21 +218,25 @@ def test_free_molecular_seed(prec):
     assert np.all(np.isfinite(s.profiles()["T"]))
 
 
-@pytest.mark.parametrize("prec,fuse", [("fp64", 1), ("fp32", 1), ("fp32", 0), ("fp32", 2)])
-def test_whole_batch_state_and_moments(prec, fuse):
+@pytest.mark.parametrize("prec,fuse,big", [("fp64", 1, True), ("fp32", 1, True), ("fp32", 0, True),
+                                           ("fp32", 2, True), ("fp32", 1, False)])
+def test_whole_batch_state_and_moments(prec, fuse, big):
     """Whole-batch state and moments (instance index -1) on a batch of unequal instances:
     lbs_get_state lays out every d, then every FP32 residual, in instance order, and
     lbs_moments every instance's [8][Nz] rows, bit for bit as the per-instance calls give
-    them.  lbs_set_state of the whole batch (copied in groups of instances, each group
-    analysed behind the next group's copy, from host and from device memory) restores the
-    state bit for bit and leaves the profiles, and the steps that follow, exactly as a
-    solver restored instance by instance.  A non-finite value in one instance of the
-    buffer is rejected."""
+    them.  lbs_set_state of the whole batch restores the state bit for bit and leaves the
+    profiles, and the steps that follow, exactly as a solver restored instance by
+    instance: from host memory with five C3-sized instances among the small ones (60 MB
+    in FP32, 80 MB in FP64: copied in two or three groups, each analysed behind the next
+    group's copy), from host memory without them (one copy), and from device memory.  A
+    non-finite value in one instance of the buffer is rejected."""
     import torch
     P = _lbs()
     pr = P.LBS_FP64 if prec == "fp64" else P.LBS_FP32
     ps = [dict(W.C1, Nz=40), RAGGED, dict(W.C1, Kn=1.0, Nz=37), PAIRS, dict(RAGGED, Nz=64, u_w=0.2),
           dict(W.C1, Kn=0.3, Nz=51)]
+    if big:
+        ps = [p for i, q in enumerate(ps) for p in ([q, dict(W.C3, Kn=10.0 * (i + 1))] if i < 5 else [q])]
     dt = min(oracle_of(p, None).dt for p in ps)
     s = solver_of(ps, dt, pr)
     t = s.tiling()
