@@ -250,14 +250,14 @@ def run_small(a):
     st = s.torch_stream()
     upd_step = sum(i.Nz * i.Q for i in inst)
     s.step(a.warmup)
-    torch.cuda.synchronize()
+    barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(0) as clk:
+    with Clocks(local) as clk:
         e0.record(st)
         s.step(a.steps)
         e1.record(st)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = reduce(e0.elapsed_time(e1), "max")
     nprof = max(3, min(500, a.steps // 10))
     k_stage, k_fin, k_step = s.profile_steps(nprof)
     pinned = torch.empty(s.state_bytes(), dtype=torch.uint8, pin_memory=True)
@@ -334,13 +334,43 @@ def run_sweep(a):
     [0.01, 100], u_w in [0.05, 1], half mu ~ T^omega, half Sutherland; Nz 32-512, up to
     16 x 4 x (2 x 48) velocities), every instance at its own CFL time step, in one batch.
     Timed like the main line; then marched to R < 1e-8 per instance (device-side
-    retirement) within a step budget, reporting each instance's steps."""
+    retirement) within a step budget, reporting each instance's steps.
+
+    Under torchrun the 64 instances are sharded over the ranks (paper_1702_01335_gb300.shard:
+    balanced by updates per step, no collective on the data path): the total work is fixed
+    (strong scaling), each rank steps its share, the rate is all instances' updates over the
+    slowest rank's time, and the per-instance steps and residuals are gathered on the host."""
     import torch
     from paper_1702_01335_gb300 import LBS_FP32, LBS_FP64, Instance, Solver
     from paper_1702_01335_gb300.autotune import DEFAULT_CACHE, autotune
-    torch.cuda.set_device(0)
-    ps = W.sweep(64, W.SWEEP_SEED)
-    inst = [Instance(**p) for p in ps]
+    from paper_1702_01335_gb300.shard import gather, shard
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def reduce(x, op):
+        t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "sum": dist.ReduceOp.SUM}[op])
+        return float(t.item())
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ps_all = W.sweep(64, W.SWEEP_SEED)
+    inst_all = [Instance(**p) for p in ps_all]
+    idx = shard(inst_all, rank, world)
+    ps = [ps_all[i] for i in idx]
+    inst = [inst_all[i] for i in idx]
+    upd_total = sum(i.Nz * i.Q for i in inst_all)
     prec = LBS_FP32 if a.precision == "f32" else LBS_FP64
     s = Solver(inst, precision=prec)
     if a.tiling:
@@ -378,36 +408,45 @@ def run_sweep(a):
     nrows = sum(8 * i.Nz for i in inst)
     out_host = torch.empty(nrows, dtype=torch.float64, pin_memory=True)
     e2e_steps = max(3, min(100, a.steps // 30))
-    torch.cuda.synchronize()
+    barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         s.set_state_all_ptr(pinned.data_ptr(), from_host=True)
         s.step(1)
         s.moments_all_ptr(out_host.data_ptr())
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = reduce(time.perf_counter() - t0, "max")
     s.close()
-    # to the steady state from rest, one batch, device-side retirement
+    # to the steady state from rest, one batch per rank, device-side retirement
     budget = 60000
     s = Solver(inst, precision=prec)
     if "V" in tl:
         s.set_tiling(tl["V"], tl["ZT"], tl["fuse"])
-    torch.cuda.synchronize()
+    barrier()
     t0 = time.perf_counter()
     steps = s.run_to_steady(1e-8, max_steps=budget, check_every=500, raise_on_fail=False)
-    wall = time.perf_counter() - t0
+    wall = reduce(time.perf_counter() - t0, "max")
     res = [s.residual(b) for b in range(len(inst))]
-    conv = [r < 1e-8 for r in res]
     s.close()
+    steps = gather([int(x) for x in steps], idx, len(inst_all), dist)
+    res = gather(res, idx, len(inst_all), dist)
+    conv = [r < 1e-8 for r in res]
+    launches = reduce({0: 6, 1: 3, 2: 12}[tl["fuse"]] * a.steps, "sum")
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
     line = {
-        "metric": "cell x velocity updates/s (RK-3 steps)", "value": upd_step * a.steps / (ms * 1e-3),
-        "unit": "updates/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": "cell x velocity updates/s (RK-3 steps)", "value": upd_total * a.steps / (ms * 1e-3),
+        "unit": "updates/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": a.precision, "data": "synthetic",
         "config": {"workload": "C4 sweep: 64 instances, seed 1702, Kn 10^U(-2,2), u_w U(0.05,1), Pr 2/3, "
                                "T^omega / Sutherland (0.27, 0.52), Nz 32-512, Qx 4-16, Qy 4, Qz 4-48, "
                                "N_eq 4, uniform cells, own CFL step each",
-                   "updates_per_step": upd_step,
+                   "updates_per_step": upd_total,
+                   "parallelism": ("instances sharded over %d ranks by updates per step (rank 0: %d "
+                                   "instances)" % (world, len(inst))) if world > 1 else "one batch",
                    "l2": "inputs larger than L2 (d and two increments of %d MiB each)" % (
                        upd_step * (4 if a.precision == "f32" else 8) >> 20),
                    "tiling": {"V": tl["V"], "ZT": tl["ZT"], "fused_finalise": tl["fuse"],
@@ -416,17 +455,17 @@ def run_sweep(a):
                      "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                      "kernel": "stage_kernel", "algorithmic_bytes_per_update_step": bpu,
                      "stage_kernel_ms_per_step": k_stage / nprof, "finalize_ms_per_step": k_fin / nprof},
-        "e2e": {"value": upd_step * e2e_steps / e2e_s, "unit": "updates/s",
-                "h2d_bytes_per_step": sum(i.Nz * i.Q for i in inst) * (6 if a.precision == "f32" else 8),
-                "d2h_bytes_per_step": nrows * 8},
+        "e2e": {"value": upd_total * e2e_steps / e2e_s, "unit": "updates/s",
+                "h2d_bytes_per_step": upd_total * (6 if a.precision == "f32" else 8),
+                "d2h_bytes_per_step": sum(8 * i.Nz for i in inst_all) * 8},
         "to_steady": {"tol": 1e-8, "step_budget": budget, "wall_s": wall, "converged": int(sum(conv)),
                       "steps": [int(x) for x in steps],
-                      "not_converged": [{"inst": b, "Kn": ps[b]["Kn"], "Nz": ps[b]["Nz"], "R": res[b]}
-                                        for b in range(len(inst)) if not conv[b]]},
-        "gpu_launches": {0: 6, 1: 3, 2: 12}[tl["fuse"]] * a.steps,
+                      "not_converged": [{"inst": b, "Kn": ps_all[b]["Kn"], "Nz": ps_all[b]["Nz"], "R": res[b]}
+                                        for b in range(len(inst_all)) if not conv[b]]},
+        "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
-    if not a.no_cpu_baseline:
+    if not a.no_cpu_baseline and world == 1:
         mid = sorted(range(len(ps)), key=lambda b: ps[b]["Nz"] * ps[b]["Qx"] * ps[b]["Qz"])[len(ps) // 2]
         line["cpu_baseline"] = cpu_baseline(ps[mid])
     print(json.dumps(line), flush=True)
