@@ -21,12 +21,14 @@
 //                    weno5_flux - weno_sigma, Table weno), the divergence of
 //                    Eq. (flux), relaxation to n G_x G_y G_z (1 + S) and the
 //                    Shu-Osher combine; it stores F_out and accumulates the raw
-//                    moments of F_out (FP32 within a warp in FP32 mode, FP64
-//                    across warps and chunks).  Tiles that end at a wall also
-//                    reduce the outgoing WENO flux of F_out through the wall.
-//   finalisation     per cell: the FP64 sum of the chunks' partials, n, u, P,
-//                    T, q (Eq. qdef), tau, and the cell record of the next
-//                    stage; per instance: the wall densities n_w (zero net mass
+//                    moments of F_out (in FP32 within the CTA and stored per
+//                    chunk in FP32 in FP32 mode; in FP64 in FP64 mode).  Tiles
+//                    that end at a wall also reduce the outgoing WENO flux of
+//                    F_out through the wall.
+//   finalisation     per cell: the sum of the chunks' partials (double-float in
+//                    FP32 mode, FP64 in FP64 mode), n, u, P, T, q (Eq. qdef),
+//                    tau, and the cell record of the next stage; per
+//                    instance: the wall densities n_w (zero net mass
 //                    flux, Appendix) and, after the third stage, the residual.
 //                    Either a launch of its own (finalize_cells, one thread per
 //                    cell, or finalize_cells_warp, one warp per cell, in
@@ -590,9 +592,10 @@ static __device__ __forceinline__ void state_about(const InstDev& I, double* mom
     for (int a = 0; a < 3; ++a) st.u[a] += ur[a];
 }
 
-// One cell (one thread): FP64 sum of the per-chunk moment partials (written by
-// other CTAs of this launch, hence read past L1), the macroscopic state, the
-// profiles, W for the residual, and the cell record of the next stage.
+// One cell (one thread): the sum of the per-chunk moment partials (written by other
+// CTAs of this launch, hence read past L1; FP32 partials in double-float, FP64 ones in
+// FP64), the macroscopic state, the profiles, W for the residual, and the cell record
+// of the next stage.
 template <typename T, int NB = kMaxN>
 __device__ __noinline__ void finalize_cell(const InstDev& I, int cell, int stage)
 {
