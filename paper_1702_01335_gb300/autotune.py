@@ -120,7 +120,9 @@ def autotune(solver, candidates=CANDIDATES, steps=3, cache_file=None, verbose=Fa
         cur = kernel_hash() + ":"
         disk = {k: v for k, v in disk.items() if k.startswith(cur)}
         disk[key] = res
-        tmp = cache_file + ".tmp"
+        # one temporary file per process: ranks tuning at once each replace the cache
+        # atomically (the last one's entries win)
+        tmp = "%s.%d.tmp" % (cache_file, os.getpid())
         with open(tmp, "w") as f:
             json.dump(disk, f)
         os.replace(tmp, cache_file)
