@@ -262,6 +262,7 @@ def test_autotuner_host_logic(monkeypatch, tmp_path):
     # one scratch solver for the tilings (the invalid one skipped), one for the finalisation layouts
     assert len(r["table"]) == 3 and len(made) == 2
     disk = json.loads(cache.read_text())
+    assert not list(tmp_path.glob("*.tmp"))  # written through a temporary file, then replaced
     key = AT.signature(target)
     assert list(disk) == [key] and key.startswith(AT.kernel_hash() + ":p1:")
     assert key.endswith(":2*16x128,24x128")
