@@ -75,8 +75,10 @@ typedef enum { LBS_VISC_POWER = 0, LBS_VISC_SUTHERLAND = 1 } lbs_visc_law;
  * (without it the state stalls about eps_32 / (lambda dt) short of the steady
  * state, lambda the decay rate of the slowest mode).  The RK stages hold their
  * increments over the step's start state, not stage values, for the same reason.
- * Moment sums across warps, the wall flux balance, the profiles and the residual
- * are FP64 in both modes. */
+ * Moment sums: with FP32 storage, in FP32 within a CTA's velocity chunk and in
+ * double-float (an FP32 pair, about 48 significant bits) across chunks; with FP64
+ * storage, in FP64.  The cell state, the wall flux balance, the profiles and the
+ * residual are FP64 in both modes. */
 typedef enum { LBS_FP64 = 0, LBS_FP32_STORE_FP64_ACC = 1 } lbs_precision;
 
 /* Velocity-set orders.  N_eq is the order of the truncated Hermite expansion
